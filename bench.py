@@ -1,0 +1,286 @@
+"""Benchmark of the WPCD hot path on one GB300 (or N, sharded by sample).
+
+One step = the whole hot path over one batch: parameter sum + eigensolve of
+every (sample, channel), energy plan, SWP boundaries + resolvent + T at the
+needed bins, T at every requested energy, phase interpolation and the np
+total cross section.  Workload: 4096 parameter samples x 15 channels (J <= 4
+plus a T_z = +-1 copy of 1S0), N_WP per channel from {40, 64, 100} (coupled
+80/128/200), 128 lab energies 1..350 MeV, FP64 (seeded synthetic inputs).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2106_00454_gb300 import inputs as W  # noqa: E402
+
+METRIC = "channel-solves/s and p50/p99 latency at <=1e-3 deg phase error vs plain FP64"
+UNIT = "channel-solves/s"
+FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (no measured FP64 peak in the driver's file)
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wpcd", choices=["wpcd", "reference"])
+    ap.add_argument("--samples", type=int, default=4096)
+    ap.add_argument("--exec", default="batched", choices=["batched", "plain"])
+    ap.add_argument("--cpu-samples", type=int, default=24, help="oracle sample size for the CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    lrank = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "wpcd" else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, lrank
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x, device=None):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        loaded = [x for x in sm if x > 0.5 * smax] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(wl, n_samples, steps=1):
+    """Time the FP64 oracle on a bounded sample of the workload (host cores)."""
+    import oracle
+    oracle.build()
+    meshes = [oracle.Mesh(n) for n in wl.nwp]
+    Vts = [oracle.project_channel(m, ch.astuple(), wl.gen, wl.gen_params, wl.n_terms) for m, ch in
+           zip(meshes, wl.channels)]
+    sub = wl.coeffs[:n_samples]
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        _, _, _, rc = oracle.batch([c.astuple() for c in wl.channels], meshes, Vts, sub, wl.e_lab)
+        times.append(time.perf_counter() - t0)
+        assert rc == 0
+    sec = statistics.median(times)
+    return {"value": n_samples * len(wl.channels) / sec, "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"first {n_samples} of {wl.n_samples} samples x {len(wl.channels)} channels, "
+                      f"{len(wl.e_lab)} energies (projection excluded, as on the GPU)"}, sec
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    wl = W.workload_batched(n_samples=args.samples)
+    for _ in range(args.warmup):
+        cpu_baseline(wl, max(1, args.cpu_samples // 4))
+    cb, sec = cpu_baseline(wl, args.cpu_samples, steps=args.steps)
+    line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{wl.name} (oracle on a {args.cpu_samples}-sample slice)",
+                       "samples_per_step": args.cpu_samples, "channels": len(wl.channels), "n_E": len(wl.e_lab)},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def jacobi_algorithmic_flops(wl, S):
+    """(8/3) n^3 per channel-solve: the paper's count for a symmetric eigensolve (Sec. 4.2.1)."""
+    return S * sum((8.0 / 3.0) * (n * (2 if ch.coupled else 1)) ** 3 for n, ch in zip(wl.nwp, wl.channels))
+
+
+def run_wpcd(args, ws, rank, lrank):
+    import torch
+    from paper_2106_00454_gb300 import api, build
+    if rank == 0:
+        build.build()
+    barrier(ws)
+    torch.cuda.set_device(lrank)
+    dev = f"cuda:{lrank}"
+    ctx = api.Context(lrank)
+    if args.exec == "plain":
+        ctx.set_exec(api.EXEC_PLAIN)
+    # weak scaling: every rank owns its own block of samples (independent seeds)
+    wl = W.workload_batched(n_samples=args.samples, seed=W.SEED + 7919 * rank)
+    md = api.Model(ctx, wl)
+    S, nch, nE = wl.n_samples, len(wl.channels), len(wl.e_lab)
+    cf = torch.tensor(wl.coeffs, dtype=torch.float64, device=dev)
+    e = torch.tensor(wl.e_lab, dtype=torch.float64, device=dev)
+    t = torch.empty((S, nch, nE, 2, 2, 2), dtype=torch.float64, device=dev)
+    d = torch.empty((S, nch, nE, 3), dtype=torch.float64, device=dev)
+    s = torch.empty((S, nE), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(lrank)
+
+    def step():
+        ctx.solve(md.vset, cf, S, e, t, d, s)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    # device-timed steps, L2 flushed between them
+    launches0 = ctx.kernel_launches()
+    ctx.profile(True)
+    evs = []
+    barrier(ws)
+    torch.cuda.synchronize()
+    with Clocks(lrank) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+    ctx.sync()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches = ctx.kernel_launches() - launches0
+    ms = statistics.mean(step_ms)
+    ms_max = max_over_ranks(ws, ms, dev)
+    barrier(ws)
+    value = ws * S * nch / (ms_max * 1e-3)
+
+    # end to end through the host entry point: copies in and out inside the timed region
+    th = np.empty((S, nch, nE, 2, 2, 2))
+    dh = np.empty((S, nch, nE, 3))
+    sh = np.empty((S, nE))
+    ctx.solve_host(md.vset, wl.coeffs, S, wl.e_lab, th, dh, sh)
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.solve_host(md.vset, wl.coeffs, S, wl.e_lab, th, dh, sh)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = statistics.mean(e2e_ms)
+    e2e_max = max_over_ranks(ws, e2e, dev)
+    h2d = wl.coeffs.nbytes + wl.e_lab.nbytes
+    d2h = th.nbytes + dh.nbytes + sh.nbytes
+
+    eig_ms, eig_n = prof["eigen"]
+    flops = jacobi_algorithmic_flops(wl, S)  # per step; the step has eig_n/steps launches
+    per_launch_ms = eig_ms / max(eig_n, 1)
+    achieved = flops / (eig_ms / args.steps * 1e-3) / 1e12
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name + "_nwp40-64-100_128E", "samples": S, "channels": nch, "n_E": nE,
+                       "n_wp": wl.nwp, "exec": args.exec, "precision": "fp64",
+                       "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas{ws}"},
+            "roofline": {"kernel": "k_jacobi_f64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "nominal FP64 rate (no measured FP64 figure available)",
+                         "flops_per_step": flops, "launches_per_step": eig_n / args.steps,
+                         "ms_per_launch": per_launch_ms},
+            "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "e2e": {"value": ws * S * nch / (e2e_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            cb, _ = cpu_baseline(wl, args.cpu_samples)
+            line["cpu_baseline"] = cb
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse()
+    ws, rank, lrank = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_wpcd(args, ws, rank, lrank)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * wpcd.h -- C ABI of libwpcd, a GB300 (sm_103a) implementation of the
+ * wave-packet continuum discretisation (WPCD) of the nucleon-nucleon
+ * Lippmann-Schwinger equation (Miller, Ekstrom, Forssen, arXiv:2106.00454).
+ *
+ * Per partial-wave channel and parameter sample the library
+ *   (a) projects the momentum-space potential onto free wave packets (FWP),
+ *   (b) forms H = H0 + V (N_WP x N_WP uncoupled, 2N_WP x 2N_WP coupled) and
+ *       diagonalises it,
+ *   (c) evaluates the on-shell T-matrix at every requested energy through the
+ *       energy-averaged resolvent of the scattering wave packets (SWP), and
+ *   (d) turns T into phase shifts and the np total cross section.
+ *
+ * Conventions (all calls):
+ *   - Every call returns a wpcd_status; nothing throws across the ABI.
+ *   - Pointers named *_dev are device pointers owned by the caller and must
+ *     stay valid until the work queued on the context stream has finished.
+ *     Pointers named *_host are host pointers, read or written before the call
+ *     returns (the *_host entry points synchronise the stream).
+ *   - Handles (mesh, vset, eig ids) are owned by the context and live until
+ *     wpcd_release or wpcd_destroy.
+ *   - Work is queued on the context's CUDA stream; a call returns after
+ *     queueing unless stated otherwise.  Errors that only the device can see
+ *     (an energy outside the mesh, a solve that did not converge) are recorded
+ *     in a device status word and returned by the next wpcd_sync.
+ *   - Units: momenta fm^-1, lab energies MeV, T-matrix fm^2 (partial-wave
+ *     normalisation <k'|k> = delta(k'-k)/(k'k), Sec. 2), angles in degrees,
+ *     cross sections in mb.
+ *   - Kinematics: p^2 = m_N T_lab / 2 with m_N = 938.918309 MeV and
+ *     hbar c = 197.3269804 MeV fm (nonrelativistic; the paper leaves this open).
+ */
+#ifndef WPCD_H
+#define WPCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wpcd_ctx wpcd_ctx; /* opaque; owns all device-resident state */
+
+typedef enum {
+    WPCD_OK = 0,
+    WPCD_ERR_ARG = -1,        /* bad argument (null pointer, size out of range, energy outside the mesh) */
+    WPCD_ERR_NOMEM = -2,      /* device or host allocation failed */
+    WPCD_ERR_BUDGET = -3,     /* the request would exceed the context's HBM budget */
+    WPCD_ERR_NOCONVERGE = -4, /* an eigensolve hit its sweep cap (per-solve status says which) */
+    WPCD_ERR_TIMEOUT = -5,    /* a bounded wait ran out */
+    WPCD_ERR_CUDA = -6,       /* a CUDA runtime call failed */
+    WPCD_ERR_NOTREADY = -7,   /* serving: the ticket is still in flight */
+    WPCD_ERR_HANDLE = -8      /* unknown or released handle / ticket */
+} wpcd_status;
+
+typedef enum { WPCD_PREC_FP64 = 0, WPCD_PREC_MIXED = 1 } wpcd_precision;
+
+/* Resolvent used for the on-shell T (App. B).  FREE_BIN: the SWP resolvent
+ * averaged over the free bin that holds the on-shell energy (the averaging of
+ * Sec. 3.2, "resolvent energy averaging"). */
+typedef enum { WPCD_AVG_FREE_BIN = 0 } wpcd_resolvent;
+
+/* Partial-wave channel.  Uncoupled: l = lp.  Coupled (K = 2): l = J-1,
+ * lp = J+1 and the channel is the 2x2 block pair on degenerate FWP copies
+ * (Sec. 3.1).  tz = 0 is np; only tz = 0 channels enter the np cross section. */
+typedef struct { int s, J, l, lp, coupled, tz; } wpcd_channel;
+
+/* Potential generators for wpcd_project. */
+enum {
+    WPCD_GEN_FINE = -1,     /* caller-supplied fine-grid values (v_fine_dev) */
+    WPCD_GEN_YAMAGUCHI = 0, /* params {lambda (fm^2), beta (fm^-1)}: V = lambda g(p')g(p), g = 1/(p^2+beta^2); 1 term */
+    WPCD_GEN_YUKAWA = 1     /* 19 params (masses m1..m3, regulator Lambda, 14 V0 strengths, 1S0 tz!=0 contact); 15 terms */
+};
+
+/* Execution modes (wpcd_set_option key WPCD_OPT_EXEC). */
+enum { WPCD_EXEC_BATCHED = 0, WPCD_EXEC_PLAIN = 1 };
+enum { WPCD_OPT_EXEC = 1 };
+
+/* ---- context --------------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context may hold (0 = no cap).  cuda_stream: a cudaStream_t on
+ * that device (NULL = the legacy default stream); the context does not own it.
+ * Errors: WPCD_ERR_ARG (null out pointer, bad device), WPCD_ERR_CUDA. */
+wpcd_status wpcd_create(wpcd_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream);
+
+/* Wait for the stream, free every handle and the context.  NULL is ignored. */
+void wpcd_destroy(wpcd_ctx *ctx);
+
+/* Static, human-readable text for a status code. */
+const char *wpcd_strerror(wpcd_status st);
+
+/* Set an execution option (see WPCD_OPT_*).  Errors: WPCD_ERR_ARG. */
+wpcd_status wpcd_set_option(wpcd_ctx *ctx, int key, int value);
+
+/* Synchronise the context stream and return (then clear) the first error
+ * recorded by device code since the last wpcd_sync, else WPCD_OK. */
+wpcd_status wpcd_sync(wpcd_ctx *ctx);
+
+/* Device bytes currently held by the context. */
+size_t wpcd_bytes_in_use(const wpcd_ctx *ctx);
+
+/* ---- (a0) free-wave-packet mesh: Sec. 3.2 step 1 ------------------------------------------------
+ * Builds N+1 momentum boundaries k_0 = 0 < ... < k_N and n_quad Gauss-Legendre
+ * points per bin on the device.  kind 0: tan^t map on a uniform angle grid that
+ * ends at kmax_fm (k_j = alpha tan^t(j theta_max / N), theta_max =
+ * atan((kmax/alpha)^(1/t))); kind 1: the paper's Chebyshev distribution
+ * k_j = alpha tan^t((2j-1) pi / (4N)), k_0 = 0 (kmax ignored).
+ * wp_kind 0: momentum packets f(k) = 1, N_i = dk_i; 1: energy packets
+ * f(k) = sqrt(k/mu), N_i = dE_i (Sec. 3.1, definition of the free wave packet).
+ * Constraints: 4 <= n_wp <= 512, 1 <= n_quad <= 16, alpha, t > 0.
+ * Errors: WPCD_ERR_ARG, WPCD_ERR_NOMEM, WPCD_ERR_BUDGET, WPCD_ERR_CUDA. */
+wpcd_status wpcd_mesh(wpcd_ctx *ctx, int n_wp, int kind, double alpha_fm, double t, double kmax_fm,
+                      int n_quad, int wp_kind, int *mesh_id);
+
+/* Copy a mesh to the host (synchronises): kb_host[n_wp+1], kq_host/wq_host[n_wp*n_quad]
+ * (any of them may be NULL).  Errors: WPCD_ERR_HANDLE. */
+wpcd_status wpcd_mesh_get(wpcd_ctx *ctx, int mesh_id, double *kb_host, double *kq_host, double *wq_host);
+
+/* ---- (a1) projection of the potential terms: Sec. 3.2, Eq. "WP potential matrix identity" ------
+ *   V_ij = (N_i N_j)^-1/2 int_{D_i} int_{D_j} k'k dk'dk f(k') f(k) v(k', k)
+ * for every term t of the potential (t = 0 is V0, t >= 1 the terms that the
+ * per-sample coefficients multiply), evaluated with the mesh's fine rule.
+ * The partial-wave projection of a built-in generator uses a 96-point
+ * Gauss-Legendre rule in the scattering angle.  Each channel c has its own
+ * mesh (mesh_ids[c]); its matrix is n x n, n = K N_WP, l-blocks ordered
+ * (l = J-1, l = J+1) for coupled channels.  Result: a vset handle holding
+ * the FP64 matrices [term][n][n] per channel, resident on the device.
+ * gen_params_host: the generator's parameters (see WPCD_GEN_*).
+ * v_fine_dev (WPCD_GEN_FINE only): per channel c, term t, the fine-grid values
+ * v(k_a, k_b) as a [K*NQ][K*NQ] row-major FP64 block (NQ = n_wp*n_quad),
+ * channels one after another, terms inner: offset(c, t) = sum_{c'<c}
+ * n_terms (K' NQ')^2 + t (K NQ)^2.  Read during the call's device work.
+ * Errors: WPCD_ERR_ARG (n_ch < 1, unknown generator, n_terms out of range
+ * 1..16, a generator that does not define the channel), WPCD_ERR_HANDLE,
+ * WPCD_ERR_NOMEM, WPCD_ERR_BUDGET, WPCD_ERR_CUDA. */
+wpcd_status wpcd_project(wpcd_ctx *ctx, const int *mesh_ids, const wpcd_channel *channels, int n_ch,
+                         int generator_id, const double *gen_params_host, int n_gen_params,
+                         const double *v_fine_dev, int n_terms, int *vset_id);
+
+/* Copy the projected matrices of one channel to the host (synchronises):
+ * out_host[n_terms][n][n].  Errors: WPCD_ERR_HANDLE, WPCD_ERR_ARG. */
+wpcd_status wpcd_vset_get(wpcd_ctx *ctx, int vset_id, int channel, double *out_host);
+
+/* ---- (a2, a3) parameter sum and eigendecomposition: Sec. 3.2 step 2, Eq. "eigendecomposition
+ * Hamiltonian" -----------------------------------------------------------------------------------
+ * For every sample s and channel c: H = diag(H0) + V0 + sum_{a>=1} c[s][a-1] V_a
+ * (H0_ii = <x_i|h0|x_i> exactly, repeated on both l-blocks of a coupled
+ * channel), then H = C D C^T with eigenvalues ascending.  coeffs_dev:
+ * [n_samples][n_terms-1] FP64 (may be NULL when n_terms == 1).  The eigenpairs
+ * stay on the device under the returned eig handle.  prec: WPCD_PREC_FP64.
+ * Per-solve convergence status: wpcd_diag_status.
+ * Errors: WPCD_ERR_ARG, WPCD_ERR_HANDLE, WPCD_ERR_NOMEM, WPCD_ERR_BUDGET, WPCD_ERR_CUDA. */
+wpcd_status wpcd_diag(wpcd_ctx *ctx, int vset_id, const double *coeffs_dev, int n_samples,
+                      wpcd_precision prec, int *eig_id);
+
+/* Per-solve status into status_dev[n_samples][n_ch] (int32): the number of
+ * Jacobi sweeps taken, or -1 if the sweep cap was hit.  Queued on the stream. */
+wpcd_status wpcd_diag_status(wpcd_ctx *ctx, int eig_id, int *status_dev);
+
+/* Copy the eigenpairs of one solve to the host (synchronises):
+ * eps_host[n], C_host[n][n] row-major (column s = eigenvector s). */
+wpcd_status wpcd_eig_get(wpcd_ctx *ctx, int eig_id, int sample, int channel, double *eps_host, double *C_host);
+
+/* ---- (a4-a7) on-shell T: Sec. 3.2 steps 3-5, App. B -----------------------------------------------
+ * For every sample, channel and requested energy: the SWP boundaries of
+ * Eq. "pseudostate wave packet boundaries", the energy-averaged resolvent of
+ * App. B averaged over the free bin D_i holding p(E), and
+ *   T_ab(i) = V_(a,i),(b,i) + sum_s (VC)_(a,i),s gbar_s (VC)_(b,i),s,
+ * converted to the continuum at q = the bin midpoint (Eq. "operator in cont and
+ * disc representation").  e_lab_dev: [n_E] MeV, ascending, each inside the
+ * channel meshes.  t_out_dev: complex128 (re, im interleaved)
+ * [n_samples][n_ch][n_E][2][2] fm^2 (uncoupled channels fill [0][0], zeros
+ * elsewhere).  Errors: WPCD_ERR_ARG, WPCD_ERR_HANDLE, WPCD_ERR_NOMEM, WPCD_ERR_CUDA;
+ * an energy outside a mesh is reported by wpcd_sync as WPCD_ERR_ARG. */
+wpcd_status wpcd_tmatrix(wpcd_ctx *ctx, int eig_id, const double *e_lab_dev, int n_E, wpcd_resolvent res,
+                         double *t_out_dev);
+
+/* ---- (a7, a8) phase shifts and total cross section: App. A, Sec. 5.1.1 ------------------------------
+ * Phase shifts at the bin midpoints (S = 1 - 2 pi i mu p T; Stapp for coupled
+ * channels), interpolated linearly in p between consecutive midpoints to each
+ * requested energy (Eq. "linear interpolation"), and the np total cross section
+ * sigma = pi/(2p^2) sum_ch (2J+1) sum_l Re(1 - S_ll) from the interpolated
+ * parameters.  delta_dev: [n_samples][n_ch][n_E][3] degrees (delta or delta_-,
+ * delta_+, eps_J; zeros where undefined); sigma_dev: [n_samples][n_E] mb.
+ * Either output may be NULL.  Errors as wpcd_tmatrix. */
+wpcd_status wpcd_observables(wpcd_ctx *ctx, int eig_id, const double *e_lab_dev, int n_E, double *delta_dev,
+                             double *sigma_dev);
+
+/* ---- the whole hot path in one call --------------------------------------------------------------
+ * wpcd_diag + wpcd_tmatrix + wpcd_observables for one batch, with the
+ * eigenpairs kept in context scratch instead of a handle.  Outputs may be NULL. */
+wpcd_status wpcd_solve(wpcd_ctx *ctx, int vset_id, const double *coeffs_dev, int n_samples,
+                       const double *e_lab_dev, int n_E, wpcd_precision prec, wpcd_resolvent res,
+                       double *t_out_dev, double *delta_dev, double *sigma_dev);
+
+/* Same as wpcd_solve with every buffer on the host: inputs are copied to the
+ * device and outputs back inside the call, which synchronises and returns the
+ * device status as wpcd_sync would. */
+wpcd_status wpcd_solve_host(wpcd_ctx *ctx, int vset_id, const double *coeffs_host, int n_samples,
+                            const double *e_lab_host, int n_E, wpcd_precision prec, wpcd_resolvent res,
+                            double *t_out_host, double *delta_host, double *sigma_host);
+
+/* Free a mesh, vset or eig handle.  Errors: WPCD_ERR_HANDLE. */
+wpcd_status wpcd_release(wpcd_ctx *ctx, int id);
+
+/* ---- tracing ---------------------------------------------------------------------------------
+ * Kernel phases for the per-launch event timing of wpcd_profile. */
+enum {
+    WPCD_PHASE_MESH = 0,        /* Gauss-Legendre rules and meshes */
+    WPCD_PHASE_PROJECT = 1,     /* projection of the potential terms */
+    WPCD_PHASE_EIGEN = 2,       /* parameter sum + eigensolve */
+    WPCD_PHASE_PLAN = 3,        /* energy -> bin plan */
+    WPCD_PHASE_TMATRIX = 4,     /* SWP boundaries, resolvent, T, phases at the bins */
+    WPCD_PHASE_GATHER = 5,      /* T at the requested energies */
+    WPCD_PHASE_OBSERVABLES = 6, /* interpolation and cross section */
+    WPCD_PHASE_COUNT = 7
+};
+
+/* Number of kernels this context has launched since creation (host count). */
+unsigned long long wpcd_kernel_launches(const wpcd_ctx *ctx);
+
+/* Turn per-launch CUDA-event timing on (1) or off (0); either call clears the
+ * accumulated totals.  Timing adds two events per launch on the context stream. */
+wpcd_status wpcd_profile(wpcd_ctx *ctx, int enable);
+
+/* Synchronise and return the summed device time (ms) and the launch count of
+ * one phase since profiling was enabled.  Errors: WPCD_ERR_ARG. */
+wpcd_status wpcd_profile_read(wpcd_ctx *ctx, int phase, double *ms_total, long *launches);
+
+/* Number of channels and matrix size of channel c in a vset. */
+wpcd_status wpcd_vset_info(wpcd_ctx *ctx, int vset_id, int *n_ch, int *n_terms, int channel, int *n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WPCD_H */

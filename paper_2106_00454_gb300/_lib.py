@@ -1,0 +1,82 @@
+"""ctypes loader for libwpcd.so (the C ABI of include/wpcd.h).
+
+The library is built in place by ``paper_2106_00454_gb300.build.build()``.
+There is no fallback: if the shared library is missing or fails to load,
+every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libwpcd.so")
+
+# Every entry point declared in include/wpcd.h.
+EXPORTED = [
+    "wpcd_create", "wpcd_destroy", "wpcd_strerror", "wpcd_set_option", "wpcd_sync", "wpcd_bytes_in_use",
+    "wpcd_mesh", "wpcd_mesh_get", "wpcd_project", "wpcd_vset_get", "wpcd_vset_info", "wpcd_diag",
+    "wpcd_diag_status", "wpcd_eig_get", "wpcd_tmatrix", "wpcd_observables", "wpcd_solve", "wpcd_solve_host",
+    "wpcd_release", "wpcd_kernel_launches", "wpcd_profile", "wpcd_profile_read",
+]
+
+
+class wpcd_channel(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_int), ("J", ctypes.c_int), ("l", ctypes.c_int), ("lp", ctypes.c_int),
+                ("coupled", ctypes.c_int), ("tz", ctypes.c_int)]
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_ip = ctypes.POINTER(ctypes.c_int)
+_sz = ctypes.c_size_t
+_SIG = {
+    "wpcd_create": (_i, [ctypes.POINTER(_vp), _i, _sz, _vp]),
+    "wpcd_destroy": (None, [_vp]),
+    "wpcd_strerror": (ctypes.c_char_p, [_i]),
+    "wpcd_set_option": (_i, [_vp, _i, _i]),
+    "wpcd_sync": (_i, [_vp]),
+    "wpcd_bytes_in_use": (_sz, [_vp]),
+    "wpcd_mesh": (_i, [_vp, _i, _i, _d, _d, _d, _i, _i, _ip]),
+    "wpcd_mesh_get": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "wpcd_project": (_i, [_vp, _ip, ctypes.POINTER(wpcd_channel), _i, _i, _vp, _i, _vp, _i, _ip]),
+    "wpcd_vset_get": (_i, [_vp, _i, _i, _vp]),
+    "wpcd_vset_info": (_i, [_vp, _i, _ip, _ip, _i, _ip]),
+    "wpcd_diag": (_i, [_vp, _i, _vp, _i, _i, _ip]),
+    "wpcd_diag_status": (_i, [_vp, _i, _vp]),
+    "wpcd_eig_get": (_i, [_vp, _i, _i, _i, _vp, _vp]),
+    "wpcd_tmatrix": (_i, [_vp, _i, _vp, _i, _i, _vp]),
+    "wpcd_observables": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
+    "wpcd_solve": (_i, [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp, _vp, _vp]),
+    "wpcd_solve_host": (_i, [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp, _vp, _vp]),
+    "wpcd_release": (_i, [_vp, _i]),
+    "wpcd_kernel_launches": (ctypes.c_ulonglong, [_vp]),
+    "wpcd_profile": (_i, [_vp, _i]),
+    "wpcd_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long)]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Load the compiled library (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2106_00454_gb300.build.build()")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIG.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    """Names from EXPORTED that the shared library exports (no device needed)."""
+    lib = load()
+    return [n for n in EXPORTED if hasattr(lib, n)]

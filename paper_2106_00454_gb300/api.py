@@ -1,0 +1,190 @@
+"""Python binding of the C ABI (argument marshalling only).
+
+Device buffers are torch tensors (float64, on the context's device); the
+context stream is a torch CUDA stream.  Every computation runs in libwpcd's
+kernels; this module only converts arguments and raises on error codes.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from . import inputs as W
+
+WPCD_OK = 0
+WPCD_ERR_NOTREADY = -7
+PREC_FP64, PREC_MIXED = 0, 1
+AVG_FREE_BIN = 0
+EXEC_BATCHED, EXEC_PLAIN = 0, 1
+OPT_EXEC = 1
+
+
+class WpcdError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.load().wpcd_strerror(code).decode()
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+def _ck(code: int, where: str):
+    if code != WPCD_OK:
+        raise WpcdError(code, where)
+
+
+def _ptr(t):
+    """Device (or host numpy) pointer of a contiguous float64/int32 buffer, or None."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags.c_contiguous
+        return ctypes.c_void_p(t.ctypes.data)
+    assert t.is_contiguous(), "buffers must be contiguous"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One libwpcd context bound to a CUDA device and a torch stream."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = _lib.load()
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = ctypes.c_void_p()
+        _ck(self.lib.wpcd_create(ctypes.byref(h), device, hbm_budget_bytes, ctypes.c_void_p(self.stream.cuda_stream)),
+            "wpcd_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.lib.wpcd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ options / sync
+    def set_exec(self, mode: int):
+        _ck(self.lib.wpcd_set_option(self.h, OPT_EXEC, mode), "wpcd_set_option")
+
+    def sync(self):
+        _ck(self.lib.wpcd_sync(self.h), "wpcd_sync")
+
+    def sync_status(self) -> int:
+        return self.lib.wpcd_sync(self.h)
+
+    def bytes_in_use(self) -> int:
+        return self.lib.wpcd_bytes_in_use(self.h)
+
+    PHASES = ["mesh", "project", "eigen", "plan", "tmatrix", "gather", "observables"]
+
+    def kernel_launches(self) -> int:
+        return int(self.lib.wpcd_kernel_launches(self.h))
+
+    def profile(self, enable: bool):
+        _ck(self.lib.wpcd_profile(self.h, 1 if enable else 0), "wpcd_profile")
+
+    def profile_read(self) -> dict:
+        out = {}
+        for k, name in enumerate(self.PHASES):
+            ms, n = ctypes.c_double(), ctypes.c_long()
+            _ck(self.lib.wpcd_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n)), "wpcd_profile_read")
+            out[name] = (ms.value, n.value)
+        return out
+
+    def release(self, hid: int):
+        _ck(self.lib.wpcd_release(self.h, hid), "wpcd_release")
+
+    # ------------------------------------------------------------------ mesh / projection
+    def mesh(self, n_wp, kind=W.MESH_KIND_CAPPED, alpha=W.MESH_ALPHA_FM, t=W.MESH_T, kmax=W.MESH_KMAX_FM,
+             n_quad=W.MESH_Q, wp_kind=W.WP_MOMENTUM) -> int:
+        mid = ctypes.c_int()
+        _ck(self.lib.wpcd_mesh(self.h, n_wp, kind, alpha, t, kmax, n_quad, wp_kind, ctypes.byref(mid)), "wpcd_mesh")
+        return mid.value
+
+    def mesh_get(self, mesh_id, n_wp, n_quad):
+        kb = np.zeros(n_wp + 1)
+        kq = np.zeros(n_wp * n_quad)
+        wq = np.zeros(n_wp * n_quad)
+        _ck(self.lib.wpcd_mesh_get(self.h, mesh_id, _ptr(kb), _ptr(kq), _ptr(wq)), "wpcd_mesh_get")
+        return kb, kq, wq
+
+    def project(self, mesh_ids, channels, gen, gen_params, n_terms, v_fine=None) -> int:
+        n = len(channels)
+        arr = (_lib.wpcd_channel * n)(*[_lib.wpcd_channel(*c.astuple()) if hasattr(c, "astuple")
+                                        else _lib.wpcd_channel(*c) for c in channels])
+        mids = (ctypes.c_int * n)(*mesh_ids)
+        gp = None if gen_params is None else np.ascontiguousarray(gen_params, dtype=np.float64)
+        vid = ctypes.c_int()
+        _ck(self.lib.wpcd_project(self.h, mids, arr, n, gen, _ptr(gp), 0 if gp is None else gp.size,
+                                  _ptr(v_fine), n_terms, ctypes.byref(vid)), "wpcd_project")
+        return vid.value
+
+    def vset_info(self, vset_id, channel=0):
+        nch, nterm, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _ck(self.lib.wpcd_vset_info(self.h, vset_id, ctypes.byref(nch), ctypes.byref(nterm), channel,
+                                    ctypes.byref(n)), "wpcd_vset_info")
+        return nch.value, nterm.value, n.value
+
+    def vset_get(self, vset_id, channel):
+        _, nterm, n = self.vset_info(vset_id, channel)
+        out = np.zeros((nterm, n, n))
+        _ck(self.lib.wpcd_vset_get(self.h, vset_id, channel, _ptr(out)), "wpcd_vset_get")
+        return out
+
+    # ------------------------------------------------------------------ hot path
+    def diag(self, vset_id, coeffs, n_samples, prec=PREC_FP64) -> int:
+        eid = ctypes.c_int()
+        _ck(self.lib.wpcd_diag(self.h, vset_id, _ptr(coeffs), n_samples, prec, ctypes.byref(eid)), "wpcd_diag")
+        return eid.value
+
+    def diag_status(self, eig_id, out):
+        _ck(self.lib.wpcd_diag_status(self.h, eig_id, _ptr(out)), "wpcd_diag_status")
+
+    def eig_get(self, eig_id, sample, channel, n):
+        eps = np.zeros(n)
+        C = np.zeros((n, n))
+        _ck(self.lib.wpcd_eig_get(self.h, eig_id, sample, channel, _ptr(eps), _ptr(C)), "wpcd_eig_get")
+        return eps, C
+
+    def tmatrix(self, eig_id, e_lab, t_out):
+        _ck(self.lib.wpcd_tmatrix(self.h, eig_id, _ptr(e_lab), e_lab.numel(), AVG_FREE_BIN, _ptr(t_out)),
+            "wpcd_tmatrix")
+
+    def observables(self, eig_id, e_lab, delta=None, sigma=None):
+        _ck(self.lib.wpcd_observables(self.h, eig_id, _ptr(e_lab), e_lab.numel(), _ptr(delta), _ptr(sigma)),
+            "wpcd_observables")
+
+    def solve(self, vset_id, coeffs, n_samples, e_lab, t_out=None, delta=None, sigma=None, prec=PREC_FP64):
+        _ck(self.lib.wpcd_solve(self.h, vset_id, _ptr(coeffs), n_samples, _ptr(e_lab), e_lab.numel(), prec,
+                                AVG_FREE_BIN, _ptr(t_out), _ptr(delta), _ptr(sigma)), "wpcd_solve")
+
+    def solve_host(self, vset_id, coeffs, n_samples, e_lab, t_out=None, delta=None, sigma=None, prec=PREC_FP64):
+        e_lab = np.ascontiguousarray(e_lab, dtype=np.float64)
+        coeffs = None if coeffs is None else np.ascontiguousarray(coeffs, dtype=np.float64)
+        _ck(self.lib.wpcd_solve_host(self.h, vset_id, _ptr(coeffs), n_samples, _ptr(e_lab), e_lab.size, prec,
+                                     AVG_FREE_BIN, _ptr(t_out), _ptr(delta), _ptr(sigma)), "wpcd_solve_host")
+
+
+class Model:
+    """Meshes + projected potential for one workload's channel set."""
+
+    def __init__(self, ctx: Context, wl: W.Workload, v_fine=None):
+        self.ctx = ctx
+        self.wl = wl
+        self.mesh_of_n = {}
+        for n in sorted(set(wl.nwp)):
+            self.mesh_of_n[n] = ctx.mesh(n, wl.mesh_kind, wl.alpha, wl.t, wl.kmax, wl.Q, wl.wp_kind)
+        mids = [self.mesh_of_n[n] for n in wl.nwp]
+        self.vset = ctx.project(mids, wl.channels, wl.gen if v_fine is None else -1, wl.gen_params, wl.n_terms,
+                                v_fine)
+
+    @property
+    def n_ch(self):
+        return len(self.wl.channels)

@@ -1,0 +1,344 @@
+// mesh_project.cu -- (a0) free-wave-packet mesh and (a1) projection of the
+// potential terms onto the wave-packet basis (Sec. 3.2 step 1 and Eq. "WP
+// potential matrix identity").  FP64 on the CUDA cores.
+#include <math.h>
+
+#include "wpcd_internal.cuh"
+
+namespace wpcd {
+
+// ---------------------------------------------------------------------------------------------
+// Gauss-Legendre rule on [-1, 1]: one thread per node pair, Newton iteration on
+// P_n from the three-term recurrence.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_gauss_legendre(int n, double *x, double *w)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int m = (n + 1) / 2;
+    if (i >= m) return;
+    double z = cos(kPi * (i + 0.75) / (n + 0.5));
+    double pcur = z, pm1 = 1.0, dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+        pm1 = 1.0;
+        pcur = z;
+        for (int j = 2; j <= n; ++j) {
+            double pn = ((2.0 * j - 1.0) * z * pcur - (j - 1.0) * pm1) / j;
+            pm1 = pcur;
+            pcur = pn;
+        }
+        dp = n * (z * pcur - pm1) / (z * z - 1.0);
+        double dz = pcur / dp;
+        z -= dz;
+        if (fabs(dz) < 1e-16) break;
+    }
+    pm1 = 1.0;
+    pcur = z;
+    for (int j = 2; j <= n; ++j) {
+        double pn = ((2.0 * j - 1.0) * z * pcur - (j - 1.0) * pm1) / j;
+        pm1 = pcur;
+        pcur = pn;
+    }
+    dp = n * (z * pcur - pm1) / (z * z - 1.0);
+    double wi = 2.0 / ((1.0 - z * z) * dp * dp);
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = wi;
+    w[n - 1 - i] = wi;
+    if ((n & 1) && i == m - 1) x[i] = 0.0;
+}
+
+cudaError_t launch_gauss_legendre(int n, double *x, double *w, cudaStream_t st)
+{
+    int m = (n + 1) / 2;
+    k_gauss_legendre<<<(m + 63) / 64, 64, 0, st>>>(n, x, w);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Mesh: N+1 boundaries, Q-point rule per bin, and the exact diagonal of h0 in the
+// packet basis, <x_i|h0|x_i> = (1/N_i) int_{D_i} dk f(k)^2 k^2/(2 mu).
+// One block; thread j handles boundary j and bin j.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_mesh(int N, int kind, double alpha, double t, double kmax, int Q, int wp_kind, const double *glx,
+                       const double *glw, double *kb, double *kq, double *wq, double *h0)
+{
+    extern __shared__ double sk[];  // N+1
+    for (int j = threadIdx.x; j <= N; j += blockDim.x) {
+        double v;
+        if (j == 0) {
+            v = 0.0;
+        } else if (kind == 0) {
+            double thmax = atan(pow(kmax / alpha, 1.0 / t));
+            v = (j == N) ? kmax : alpha * pow(tan(j * thmax / N), t);
+        } else {
+            v = alpha * pow(tan((2.0 * j - 1.0) * kPi / (4.0 * N)), t);
+        }
+        sk[j] = v;
+        kb[j] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double a = sk[i], b = sk[i + 1];
+        for (int q = 0; q < Q; ++q) {
+            kq[i * Q + q] = 0.5 * (a + b) + 0.5 * (b - a) * glx[q];
+            wq[i * Q + q] = 0.5 * (b - a) * glw[q];
+        }
+        if (wp_kind == 0) {
+            h0[i] = (b * b * b - a * a * a) / (3.0 * (b - a)) / (2.0 * kMu);
+        } else {
+            h0[i] = 0.5 * (a * a + b * b) / (2.0 * kMu);
+        }
+    }
+}
+
+cudaError_t launch_mesh(int N, int kind, double alpha, double t, double kmax, int Q, int wp_kind,
+                        const double *glx, const double *glw, double *kb, double *kq, double *wq, double *h0,
+                        cudaStream_t st)
+{
+    k_mesh<<<1, 256, (N + 1) * sizeof(double), st>>>(N, kind, alpha, t, kmax, Q, wp_kind, glx, glw, kb, kq, wq, h0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Projection.  Every CTA owns one pair of bins (i <= j) of one mesh and all the
+// channels that use that mesh; each thread one fine pair (a in D_i, b in D_j).
+// It evaluates v_t(k_a, k_b) for every term, multiplies by
+//   omega_a omega_b,  omega_a = w_a k_a f(k_a) / sqrt(N_i),
+// and the CTA sums over its Q x Q pairs.  The matrix element and its mirror
+// V[(b,j),(a,i)] = V[(a,i),(b,j)] are written together (v^{l'l}(p',p) =
+// v^{ll'}(p,p')).
+// ---------------------------------------------------------------------------------------------
+constexpr int kLmaxReg = 10;  // angle integrals kept in registers: L = 0..10 (J <= 8)
+
+__device__ __forceinline__ double wp_f(int wp_kind, double k) { return wp_kind == 0 ? 1.0 : sqrt(k / kMu); }
+__device__ __forceinline__ double wp_norm(int wp_kind, double a, double b)
+{
+    return wp_kind == 0 ? (b - a) : (b * b - a * a) / (2.0 * kMu);
+}
+
+__device__ __forceinline__ double ls_factor(int s, int J, int l)
+{
+    return 0.5 * (J * (J + 1.0) - l * (l + 1.0) - s * (s + 1.0));
+}
+
+__device__ __forceinline__ double s12_factor(int s, int J, int lp, int l)
+{
+    if (s != 1) return 0.0;
+    if (lp == l) {
+        if (l == J) return 2.0;
+        if (l == J - 1) return -2.0 * (J - 1.0) / (2.0 * J + 1.0);
+        if (l == J + 1) return -2.0 * (J + 2.0) / (2.0 * J + 1.0);
+        return 0.0;
+    }
+    if ((lp == J - 1 && l == J + 1) || (lp == J + 1 && l == J - 1)) return 6.0 * sqrt(J * (J + 1.0)) / (2.0 * J + 1.0);
+    return 0.0;
+}
+
+// Sum over the CTA (blockDim <= 1024, multiple of 32).  Every thread gets the total.
+__device__ __forceinline__ double cta_sum(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double tot = 0.0;
+    for (int k = 0; k < nw; ++k) tot += red[k];
+    return tot;
+}
+
+template <int GEN>
+__global__ void __launch_bounds__(256) k_project(const ChanDev *chans, const int *group, int n_group, int N, int Q,
+                                                 int Lmax, const double *gp, const double *angx, const double *angw,
+                                                 int n_terms)
+{
+    // decode the bin pair (i <= j) from the linear block index over the upper triangle
+    int b = blockIdx.x;
+    int j = (int)((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
+    while ((j + 1) * (j + 2) / 2 <= b) ++j;
+    while (j * (j + 1) / 2 > b) --j;
+    int i = b - j * (j + 1) / 2;
+    if (j >= N) return;
+
+    __shared__ double wpl[kAngleQ][kLmaxReg + 1];  // w_x P_L(x)
+    __shared__ double ax[kAngleQ];
+    __shared__ double red[8];
+    const int Lm = (Lmax < kLmaxReg) ? Lmax : kLmaxReg;
+    if (GEN == WPCD_GEN_YUKAWA) {
+        for (int x = threadIdx.x; x < kAngleQ; x += blockDim.x) {
+            double xv = angx[x], p0 = 1.0, p1 = xv;
+            ax[x] = xv;
+            wpl[x][0] = angw[x];
+            if (Lm >= 1) wpl[x][1] = angw[x] * xv;
+            for (int L = 2; L <= Lm; ++L) {
+                double p2 = ((2.0 * L - 1.0) * xv * p1 - (L - 1.0) * p0) / L;
+                p0 = p1;
+                p1 = p2;
+                wpl[x][L] = angw[x] * p2;
+            }
+        }
+        __syncthreads();
+    }
+
+    const ChanDev c0 = chans[group[0]];
+    const int qa = threadIdx.x / Q, qb = threadIdx.x % Q;
+    const bool live = threadIdx.x < Q * Q;
+    const int a = i * Q + (live ? qa : 0), bb = j * Q + (live ? qb : 0);
+    const double pp = c0.kq[a], p = c0.kq[bb];
+    double om = 0.0;
+    if (live) {
+        om = c0.wq[a] * pp * wp_f(c0.wp_kind, pp) / sqrt(wp_norm(c0.wp_kind, c0.kb[i], c0.kb[i + 1]));
+        om *= c0.wq[bb] * p * wp_f(c0.wp_kind, p) / sqrt(wp_norm(c0.wp_kind, c0.kb[j], c0.kb[j + 1]));
+    }
+
+    double I1[kLmaxReg + 1], I2[kLmaxReg + 1], I3[kLmaxReg + 1];
+    double R = 0.0;
+    if (GEN == WPCD_GEN_YUKAWA) {
+        const double m1 = gp[0], m2 = gp[1], m3 = gp[2], Lam = gp[3];
+#pragma unroll
+        for (int L = 0; L <= kLmaxReg; ++L) I1[L] = I2[L] = I3[L] = 0.0;
+        const double A0 = pp * pp + p * p, B = 2.0 * pp * p;
+        for (int x = 0; x < kAngleQ; ++x) {
+            double d = A0 - B * ax[x];
+            double F1 = 1.0 / (d + m1 * m1), F2 = 1.0 / (d + m2 * m2), F3 = 1.0 / (d + m3 * m3);
+#pragma unroll
+            for (int L = 0; L <= kLmaxReg; ++L) {
+                if (L <= Lm) {
+                    double wv = wpl[x][L];
+                    I1[L] = fma(wv, F1, I1[L]);
+                    I2[L] = fma(wv, F2, I2[L]);
+                    I3[L] = fma(wv, F3, I3[L]);
+                }
+            }
+        }
+#pragma unroll
+        for (int L = 0; L <= kLmaxReg; ++L) {
+            I1[L] *= 2.0 * kPi;
+            I2[L] *= 2.0 * kPi;
+            I3[L] *= 2.0 * kPi;
+        }
+        R = exp(-(pp * pp + p * p) / (Lam * Lam));
+    }
+
+    for (int g = 0; g < n_group; ++g) {
+        const int cidx = group[g];
+        const ChanDev ch = chans[cidx];
+        const int K = ch.K, n = ch.n;
+        for (int al = 0; al < K; ++al)
+            for (int be = 0; be < K; ++be) {
+                const int lp = ch.coupled ? (al == 0 ? ch.J - 1 : ch.J + 1) : ch.l;
+                const int l = ch.coupled ? (be == 0 ? ch.J - 1 : ch.J + 1) : ch.l;
+                double tv[kMaxTerms];
+#pragma unroll
+                for (int t = 0; t < kMaxTerms; ++t) tv[t] = 0.0;
+                if (GEN == WPCD_GEN_YAMAGUCHI) {
+                    if (lp == 0 && l == 0) tv[0] = gp[0] / ((pp * pp + gp[1] * gp[1]) * (p * p + gp[1] * gp[1]));
+                } else {
+                    const int s = ch.s, J = ch.J;
+                    double u[kYukTerms];
+#pragma unroll
+                    for (int k = 0; k < kYukTerms; ++k) u[k] = 0.0;
+                    const bool diag = (lp == l);
+                    if (diag) {
+                        u[0] = I1[l];
+                        u[1] = (2.0 * s * (s + 1.0) - 3.0) * I1[l];
+                        u[2] = I2[l];
+                        double ilm1 = (l >= 1) ? I2[l - 1] : 0.0;
+                        u[3] = ls_factor(s, J, l) * pp * p * (I2[l + 1] - ilm1) / (2.0 * l + 1.0);
+                    }
+                    u[4] = s12_factor(s, J, lp, l) * I3[(l + lp) / 2];
+                    if (diag && l == 0 && s == 0) { u[5] = 1.0; u[7] = p * p + pp * pp; }
+                    if (diag && l == 0 && s == 1) { u[6] = 1.0; u[8] = p * p + pp * pp; }
+                    if (diag && l == 1 && s == 1 && J == 0) u[9] = pp * p;
+                    if (diag && l == 1 && s == 0 && J == 1) u[10] = pp * p;
+                    if (diag && l == 1 && s == 1 && J == 1) u[11] = pp * p;
+                    if (diag && l == 1 && s == 1 && J == 2) u[12] = pp * p;
+                    if (s == 1 && J == 1 && lp == 2 && l == 0) u[13] = pp * pp;
+                    if (s == 1 && J == 1 && lp == 0 && l == 2) u[13] = p * p;
+                    double v0 = 0.0;
+#pragma unroll
+                    for (int k = 0; k < kYukTerms; ++k) {
+                        u[k] *= R;
+                        v0 = fma(gp[4 + k], u[k], v0);
+                    }
+                    if (s == 0 && l == 0 && lp == 0 && ch.tz != 0) v0 += gp[18] * R;
+                    tv[0] = v0;
+#pragma unroll
+                    for (int k = 0; k < kYukTerms; ++k)
+                        if (k + 1 < kMaxTerms) tv[k + 1] = u[k];
+                }
+                for (int t = 0; t < n_terms; ++t) {
+                    double v = cta_sum(live ? om * tv[t] : 0.0, red);
+                    if (threadIdx.x == 0) {
+                        double *Vt = const_cast<double *>(ch.V) + (size_t)t * n * n;
+                        Vt[(size_t)(al * N + i) * n + (be * N + j)] = v;
+                        Vt[(size_t)(be * N + j) * n + (al * N + i)] = v;
+                    }
+                }
+            }
+    }
+}
+
+static int proj_threads(int Q) { return ((Q * Q + 31) / 32) * 32; }
+
+cudaError_t launch_project_yukawa(const ChanDev *chans_dev, const int *group_dev, int n_group, int N, int Q, int Lmax,
+                                  const double *gp_dev, const double *angx, const double *angw, int n_terms,
+                                  cudaStream_t st)
+{
+    int nblk = N * (N + 1) / 2;
+    k_project<WPCD_GEN_YUKAWA><<<nblk, proj_threads(Q), 0, st>>>(chans_dev, group_dev, n_group, N, Q, Lmax, gp_dev,
+                                                                 angx, angw, n_terms);
+    return cudaGetLastError();
+}
+
+// Yamaguchi parameters travel in the same device parameter buffer as the Yukawa set.
+cudaError_t launch_project_yamaguchi_gp(const ChanDev *chans_dev, const int *group_dev, int n_group, int N, int Q,
+                                        const double *gp_dev, cudaStream_t st)
+{
+    int nblk = N * (N + 1) / 2;
+    k_project<WPCD_GEN_YAMAGUCHI><<<nblk, proj_threads(Q), 0, st>>>(chans_dev, group_dev, n_group, N, Q, 0, gp_dev,
+                                                                    nullptr, nullptr, 1);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Caller-supplied fine-grid values: the same bin reduction, over all (i, j) and
+// l-blocks of one channel.  vfine: [n_terms][K*NQ][K*NQ].
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_project_fine(const ChanDev *chans, int c, const double *vfine, int n_terms)
+{
+    const ChanDev ch = chans[c];
+    const int N = ch.N, Q = ch.Q, K = ch.K, n = ch.n, NQ = N * Q;
+    const int i = blockIdx.x, j = blockIdx.y;
+    __shared__ double red[8];
+    const int qa = threadIdx.x / Q, qb = threadIdx.x % Q;
+    const bool live = threadIdx.x < Q * Q;
+    const int a = i * Q + (live ? qa : 0), b = j * Q + (live ? qb : 0);
+    double om = 0.0;
+    if (live) {
+        om = ch.wq[a] * ch.kq[a] * wp_f(ch.wp_kind, ch.kq[a]) / sqrt(wp_norm(ch.wp_kind, ch.kb[i], ch.kb[i + 1]));
+        om *= ch.wq[b] * ch.kq[b] * wp_f(ch.wp_kind, ch.kq[b]) / sqrt(wp_norm(ch.wp_kind, ch.kb[j], ch.kb[j + 1]));
+    }
+    const size_t KNQ = (size_t)K * NQ;
+    for (int t = 0; t < n_terms; ++t)
+        for (int al = 0; al < K; ++al)
+            for (int be = 0; be < K; ++be) {
+                double v = 0.0;
+                if (live) v = om * vfine[(size_t)t * KNQ * KNQ + (size_t)(al * NQ + a) * KNQ + (be * NQ + b)];
+                v = cta_sum(v, red);
+                if (threadIdx.x == 0) {
+                    double *Vt = const_cast<double *>(ch.V) + (size_t)t * n * n;
+                    Vt[(size_t)(al * N + i) * n + (be * N + j)] = v;
+                }
+            }
+}
+
+cudaError_t launch_project_fine(const ChanDev *chans_dev, int c, const ChanDev &ch_host, const double *vfine,
+                                int n_terms, cudaStream_t st)
+{
+    dim3 grid(ch_host.N, ch_host.N);
+    k_project_fine<<<grid, proj_threads(ch_host.Q), 0, st>>>(chans_dev, c, vfine, n_terms);
+    return cudaGetLastError();
+}
+
+}  // namespace wpcd

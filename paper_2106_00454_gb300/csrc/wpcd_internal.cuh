@@ -1,0 +1,114 @@
+// wpcd_internal.cuh -- types, constants and launch helpers shared by the
+// CUDA translation units of libwpcd (sm_103a).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/wpcd.h"
+
+namespace wpcd {
+
+// Kinematics (the paper leaves the T_lab <-> p relation open): nonrelativistic
+// p^2 = m_N T_lab / 2 with the np reduced-mass nucleon mass.
+constexpr double kHbarc = 197.3269804;                // MeV fm
+constexpr double kMn = 938.918309;                    // MeV, 2 m_p m_n/(m_p+m_n)
+constexpr double kMu = 0.5 * kMn / kHbarc;            // reduced mass, fm^-1
+constexpr double kPi = 3.14159265358979323846;
+
+constexpr int kMaxNwp = 512;     // largest N_WP per channel
+constexpr int kMaxQ = 16;        // largest fine points per bin
+constexpr int kAngleQ = 96;      // Gauss-Legendre points in the scattering angle
+constexpr int kMaxTerms = 16;    // potential terms per channel (V0 + 15)
+constexpr int kYukTerms = 14;    // unit terms of the Yukawa/contact generator
+constexpr int kYukParams = 19;
+constexpr int kMaxJ = 16;
+
+// Device error codes recorded in the context status word (first one wins).
+enum DevErr : int { kDevOk = 0, kDevEnergyOutside = 1, kDevNoConverge = 2, kDevBranch = 3, kDevBadSize = 4 };
+
+// One channel of a projected potential set, as the kernels see it.
+struct ChanDev {
+    int s, J, l, lp, coupled, tz;
+    int N;              // N_WP of its mesh
+    int K;              // 1 or 2 l-blocks
+    int n;              // K * N
+    int Q;              // fine points per bin
+    int wp_kind;        // 0 momentum, 1 energy packets
+    int pad_;
+    const double *kb;   // mesh boundaries [N+1]
+    const double *kq;   // fine nodes [N*Q]
+    const double *wq;   // fine weights [N*Q]
+    const double *h0;   // <x_i|h0|x_i> [N]
+    const double *V;    // projected terms [n_terms][n][n]
+    long long eps_off;  // offset of this channel's eigenvalue block [S][n] in an eig buffer
+    long long c_off;    // offset of this channel's eigenvector block [S][n][n]
+};
+
+// Energy plan of one channel for one energy list.
+struct PlanDev {
+    int *bin;      // [n_ch][n_E] free bin holding p(E)
+    int *brk;      // [n_ch][n_E] lower index j of the midpoint segment used to interpolate
+    int *cnt;      // [n_ch] number of distinct bins whose T is needed
+    int *list;     // [n_ch][maxN] those bins, ascending
+    double *pE;    // [n_E] c.m. momentum of each energy
+};
+
+// Bytes of dynamic shared memory this launch was given.
+__device__ __forceinline__ unsigned dyn_smem_bytes()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return r;
+}
+
+// Shared-memory layouts (doubles) of the kernels, used by kernel and launcher alike.
+__host__ __device__ inline size_t tbin_smem_doubles(int n)  // n = K * N of the channel
+{
+    // eps n, branch members 2n, branch boundaries 2(n+1), lo/hi 2n, V rows 2n, R 2n, reduction 6 x 32
+    return (size_t)11 * n + 2 + 6 * 32;
+}
+
+__device__ __forceinline__ void record_error(int *err, int code)
+{
+    if (err) atomicCAS(err, 0, code);
+}
+
+// Packed upper-triangle index (i <= j), column-major: element (i, j) at j(j+1)/2 + i.
+__device__ __forceinline__ int pk(int i, int j)
+{
+    return (i <= j) ? (j * (j + 1) / 2 + i) : (i * (i + 1) / 2 + j);
+}
+
+}  // namespace wpcd
+
+// ---- host-side launch interfaces (defined in the .cu files) ----------------------------------
+namespace wpcd {
+
+cudaError_t launch_gauss_legendre(int n, double *x, double *w, cudaStream_t st);
+cudaError_t launch_mesh(int N, int kind, double alpha, double t, double kmax, int Q, int wp_kind,
+                        const double *glx, const double *glw, double *kb, double *kq, double *wq, double *h0,
+                        cudaStream_t st);
+cudaError_t launch_project_yukawa(const ChanDev *chans_dev, const int *group_dev, int n_group, int N, int Q,
+                                  int Lmax, const double *gp_dev, const double *angx, const double *angw,
+                                  int n_terms, cudaStream_t st);
+cudaError_t launch_project_yamaguchi_gp(const ChanDev *chans_dev, const int *group_dev, int n_group, int N, int Q,
+                                        const double *gp_dev, cudaStream_t st);
+cudaError_t launch_project_fine(const ChanDev *chans_dev, int c, const ChanDev &ch_host, const double *vfine,
+                                int n_terms, cudaStream_t st);
+size_t jacobi_smem_bytes(int n, bool c_in_smem);
+bool jacobi_c_in_smem(int n);
+cudaError_t launch_jacobi_f64(const ChanDev *chans_dev, const int *work_ch_dev, int n_work_ch, int n_samples,
+                              int sample0, int n_terms, const double *coeffs, int n, double *eps_all,
+                              double *C_all, int *status_all, int n_ch_total, int *err, cudaStream_t st);
+cudaError_t launch_plan(const ChanDev *chans_dev, int n_ch, int maxN, const double *e_lab, int n_E, PlanDev plan,
+                        int *err, cudaStream_t st);
+cudaError_t launch_tbin(const ChanDev *chans_dev, int n_ch, int n_samples, int n_terms, const double *coeffs,
+                        const double *eps_all, const double *C_all, PlanDev plan, int maxN, double *tbin,
+                        double *phbin, int *err, cudaStream_t st);
+cudaError_t launch_gather_t(const ChanDev *chans_dev, int n_ch, int n_samples, int n_E, int maxN, PlanDev plan,
+                            const double *tbin, double *t_out, cudaStream_t st);
+cudaError_t launch_observables(const ChanDev *chans_dev, int n_ch, int n_samples, int n_E, int maxN, PlanDev plan,
+                               const double *phbin, double *delta, double *sigma, cudaStream_t st);
+
+}  // namespace wpcd
