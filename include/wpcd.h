@@ -231,6 +231,40 @@ wpcd_status wpcd_profile_read(wpcd_ctx *ctx, int phase, double *ms_total, long *
 /* Number of channels and matrix size of channel c in a vset. */
 wpcd_status wpcd_vset_info(wpcd_ctx *ctx, int vset_id, int *n_ch, int *n_terms, int channel, int *n);
 
+/* ---- the per-channel hot path without device allocation -------------------------------------
+ * No counterpart in the paper: this entry point exists for callers that cannot
+ * call cudaMalloc -- an application that owns all device memory through its own
+ * pool and forbids libraries from allocating, or a latency-critical loop that
+ * cannot take cudaMalloc's implicit device synchronisation.
+ *
+ * For one channel and n_samples parameter samples it runs what wpcd_solve runs
+ * for that channel: builds the mesh (same arguments as wpcd_mesh), forms
+ * H = diag(H0) + V0 + sum_a c_a V_a, diagonalises it (FP64 Jacobi), and
+ * writes T at every requested energy (t_out_dev, layout of wpcd_tmatrix with
+ * n_ch = 1) and the interpolated phase shifts (delta_dev, layout of
+ * wpcd_observables with n_ch = 1; no cross section, which sums channels).
+ * V_dev: the channel's projected terms [n_terms][n][n] FP64 (n = K n_wp), e.g.
+ * from wpcd_vset_get; coeffs_dev: [n_samples][n_terms-1] (NULL if n_terms == 1).
+ * Either output may be NULL, not both.  status_dev (optional, caller-zeroed
+ * int on the device) receives the first device-side error code (1 = an energy
+ * outside the mesh, 2 = no convergence).  Work is queued on cuda_stream (NULL =
+ * legacy default stream) and the call returns without synchronising.
+ *
+ * It allocates nothing: every intermediate lives in one file-scope device
+ * array of 16 MiB, held by every GPU that loads the library until exit.  A
+ * problem whose intermediates do not fit (roughly n_samples * (K n_wp)^2 * 8
+ * bytes plus small terms) is rejected with WPCD_ERR_ARG.  The first call on
+ * each device looks up the array's device address with that device current;
+ * make that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU race on it and must be serialised by
+ * the caller (one stream, or events).
+ * Errors: WPCD_ERR_ARG, WPCD_ERR_CUDA. */
+wpcd_status wpcd_channel_solve_noalloc(int n_wp, int mesh_kind, double alpha_fm, double t, double kmax_fm,
+                                       int n_quad, int wp_kind, wpcd_channel channel, const double *V_dev,
+                                       int n_terms, const double *coeffs_dev, int n_samples,
+                                       const double *e_lab_dev, int n_E, double *t_out_dev, double *delta_dev,
+                                       int *status_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

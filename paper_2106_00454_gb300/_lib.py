@@ -18,6 +18,7 @@ EXPORTED = [
     "wpcd_mesh", "wpcd_mesh_get", "wpcd_project", "wpcd_vset_get", "wpcd_vset_info", "wpcd_diag",
     "wpcd_diag_status", "wpcd_eig_get", "wpcd_tmatrix", "wpcd_observables", "wpcd_solve", "wpcd_solve_host",
     "wpcd_release", "wpcd_kernel_launches", "wpcd_profile", "wpcd_profile_read",
+    "wpcd_channel_solve_noalloc",
 ]
 
 
@@ -54,6 +55,8 @@ _SIG = {
     "wpcd_kernel_launches": (ctypes.c_ulonglong, [_vp]),
     "wpcd_profile": (_i, [_vp, _i]),
     "wpcd_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long)]),
+    "wpcd_channel_solve_noalloc": (_i, [_i, _i, _d, _d, _d, _i, _i, wpcd_channel, _vp, _i, _vp, _i, _vp, _i, _vp,
+                                        _vp, _vp, _vp]),
 }
 
 _lock = threading.Lock()
