@@ -31,6 +31,7 @@ from paper_2106_00454_gb300 import inputs as W  # noqa: E402
 METRIC = "channel-solves/s and p50/p99 latency at <=1e-3 deg phase error vs plain FP64"
 UNIT = "channel-solves/s"
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (no measured FP64 peak in the driver's file)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA lanes x clock
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 
 
@@ -42,8 +43,15 @@ def parse():
     ap.add_argument("--impl", default="wpcd", choices=["wpcd", "reference"])
     ap.add_argument("--samples", type=int, default=4096)
     ap.add_argument("--exec", default="batched", choices=["batched", "plain"])
+    ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--check-samples", type=int, default=64,
+                    help="samples re-solved in FP64 to state the mixed path's phase error")
     ap.add_argument("--cpu-samples", type=int, default=24, help="oracle sample size for the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=5.0,
+                    help="length of the Poisson request stream for the latency figures (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-nwp", default="32,64,128")
     return ap.parse_args()
 
 
@@ -164,6 +172,52 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def serve_latency(args, lrank, prec):
+    """Open-loop Poisson stream through wpcd_submit / wpcd_poll (continuous batching)."""
+    from paper_2106_00454_gb300 import api
+    nwp = tuple(int(x) for x in args.serve_nwp.split(","))
+    reqs = W.serving_requests(duration_s=args.serve_seconds, rate_hz=args.serve_rate, nwp_choices=nwp)
+    chs = W.np_channels(4, extra_1s0_tz=True)
+    ctx = api.Context(lrank)
+    ctx.serve_start(chs, W.GEN_YUKAWA, W.YUKAWA_PARAMS, W.N_TERMS_YUKAWA, list(nwp), max_batch=256, n_slots=4)
+    # warm the slots (allocations) with a short burst before the timed stream
+    warm = [ctx.submit(r.coeffs, r.e_lab, r.n_wp, prec) for r in reqs[:64]]
+    for t in warm:
+        ctx.wait(t)
+        ctx.release_result(t)
+    lat, pending, refused = [], [], 0
+    t0 = time.perf_counter()
+    for r in reqs:
+        while time.perf_counter() - t0 < r.arrival_s:
+            pass
+        out = ctx.submit(r.coeffs, r.e_lab, r.n_wp, prec, raise_on_error=False)
+        if out < 0:
+            refused += 1
+            continue
+        pending.append(out)
+        while pending:
+            res = ctx.poll(pending[0])
+            if res is None:
+                break
+            lat.append(res.latency_us)
+            ctx.release_result(pending.pop(0))
+    for t in pending:
+        res = ctx.wait(t, 600000)
+        lat.append(res.latency_us)
+        ctx.release_result(t)
+    wall = time.perf_counter() - t0
+    stats = ctx.serve_stats()
+    ctx.serve_stop()
+    ctx.close()
+    lat = np.array(lat)
+    return {"requests": len(reqs), "completed": int(lat.size), "refused": refused, "offered_rate_hz": args.serve_rate,
+            "n_wp": list(nwp), "channels": len(chs), "wall_s": wall, "achieved_req_per_s": lat.size / wall,
+            "channel_solves_per_s": lat.size * len(chs) / wall,
+            "p50_ms": float(np.percentile(lat, 50) / 1e3) if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99) / 1e3) if lat.size else None,
+            "mean_batch": stats["completed"] / max(stats["batches"], 1), "precision": args.prec}
+
+
 def jacobi_algorithmic_flops(wl, S):
     """(8/3) n^3 per channel-solve: the paper's count for a symmetric eigensolve (Sec. 4.2.1)."""
     return S * sum((8.0 / 3.0) * (n * (2 if ch.coupled else 1)) ** 3 for n, ch in zip(wl.nwp, wl.channels))
@@ -192,8 +246,10 @@ def run_wpcd(args, ws, rank, lrank):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(lrank)
 
+    prec = api.PREC_MIXED if args.prec == "mixed" else api.PREC_FP64
+
     def step():
-        ctx.solve(md.vset, cf, S, e, t, d, s)
+        ctx.solve(md.vset, cf, S, e, t, d, s, prec=prec)
 
     for _ in range(args.warmup):
         step()
@@ -227,42 +283,80 @@ def run_wpcd(args, ws, rank, lrank):
     th = np.empty((S, nch, nE, 2, 2, 2))
     dh = np.empty((S, nch, nE, 3))
     sh = np.empty((S, nE))
-    ctx.solve_host(md.vset, wl.coeffs, S, wl.e_lab, th, dh, sh)
+    ctx.solve_host(md.vset, wl.coeffs, S, wl.e_lab, th, dh, sh, prec=prec)
     e2e_ms = []
     for _ in range(max(1, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.solve_host(md.vset, wl.coeffs, S, wl.e_lab, th, dh, sh)
+        ctx.solve_host(md.vset, wl.coeffs, S, wl.e_lab, th, dh, sh, prec=prec)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e = statistics.mean(e2e_ms)
     e2e_max = max_over_ranks(ws, e2e, dev)
     h2d = wl.coeffs.nbytes + wl.e_lab.nbytes
     d2h = th.nbytes + dh.nbytes + sh.nbytes
 
+    # the mixed path's phase / cross-section error against plain FP64 on the GPU
+    accuracy = None
+    if prec == api.PREC_MIXED and args.check_samples > 0:
+        k = min(args.check_samples, S)
+        d64 = torch.empty((k, nch, nE, 3), dtype=torch.float64, device=dev)
+        s64 = torch.empty((k, nE), dtype=torch.float64, device=dev)
+        ctx.solve(md.vset, cf[:k].contiguous(), k, e, None, d64, s64, prec=api.PREC_FP64)
+        ctx.sync()
+        dm, d6 = d[:k].cpu().numpy(), d64.cpu().numpy()
+        comp = np.array([[1, 1 if ch.coupled else 0, 1 if ch.coupled else 0] for ch in wl.channels], dtype=bool)
+        diff = np.abs((dm - d6 + 90.0) % 180.0 - 90.0)
+        diff[..., 2] = np.abs(dm[..., 2] - d6[..., 2])
+        diff = diff * comp[None, :, None, :]
+        accuracy = {"samples_checked": k, "max_phase_err_deg": float(diff.max()),
+                    "max_sigma_err_mb": float(np.abs(s[:k].cpu().numpy() - s64.cpu().numpy()).max()),
+                    "reference": "FP64 path on the same GPU"}
+
+    sum_n3 = sum((n * (2 if ch.coupled else 1)) ** 3 for n, ch in zip(wl.nwp, wl.channels))
     eig_ms, eig_n = prof["eigen"]
-    flops = jacobi_algorithmic_flops(wl, S)  # per step; the step has eig_n/steps launches
-    per_launch_ms = eig_ms / max(eig_n, 1)
-    achieved = flops / (eig_ms / args.steps * 1e-3) / 1e12
+    ref_ms, ref_n = prof["refine"]
+    jac = {"kernel": "k_jacobi_f64" if prec == api.PREC_FP64 else "k_jacobi_mixed", "bound": "alu",
+           "flops_per_step": S * (8.0 / 3.0) * sum_n3,
+           "flops_note": "(8/3) n^3 per channel-solve, the paper's symmetric-eigensolve count (Sec. 4.2.1)",
+           "ms_per_step": eig_ms / args.steps, "launches_per_step": eig_n / args.steps,
+           "peak": FP64_PEAK_TFLOPS if prec == api.PREC_FP64 else FP32_PEAK_TFLOPS,
+           "peak_source": ("nominal GB300 FP64 rate (measured 1.19 TFLOP/s with a DFMA probe)" if prec == api.PREC_FP64
+                           else "FP32 FMA rate from unit counts: 152 SM x 128 lanes x 2 flop x 2.07 GHz")}
+    ref = None
+    if ref_n:
+        ref = {"kernel": "k_bgemm64 (FP64 refinement products)", "bound": "alu",
+               "flops_per_step": S * 18.0 * sum_n3,
+               "flops_note": "two refinement iterations of 4 n^3 products plus the final H X: 18 n^3 flop",
+               "ms_per_step": ref_ms / args.steps, "launches_per_step": ref_n / args.steps,
+               "peak": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64 rate"}
+    for r in (jac, ref):
+        if r:
+            r["achieved"] = r["flops_per_step"] / (r["ms_per_step"] * 1e-3) / 1e12
+            r["unit"] = "TFLOP/s"
+            r["frac"] = r["achieved"] / r["peak"]
+            r["traffic"] = None
+    dominant, secondary = (ref, jac) if (ref and ref["ms_per_step"] > jac["ms_per_step"]) else (jac, ref)
     if rank == 0:
         clocks = clk.summary()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if prec == api.PREC_FP64 else "f32+f64", "data": "synthetic",
             "config": {"workload": wl.name + "_nwp40-64-100_128E", "samples": S, "channels": nch, "n_E": nE,
-                       "n_wp": wl.nwp, "exec": args.exec, "precision": "fp64",
+                       "n_wp": wl.nwp, "exec": args.exec, "precision": args.prec,
                        "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas{ws}"},
-            "roofline": {"kernel": "k_jacobi_f64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                         "peak_source": "nominal FP64 rate (no measured FP64 figure available)",
-                         "flops_per_step": flops, "launches_per_step": eig_n / args.steps,
-                         "ms_per_launch": per_launch_ms},
+            "roofline": dominant,
+            "roofline_secondary": secondary,
             "phases_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "e2e": {"value": ws * S * nch / (e2e_max * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_max},
             "gpu_launches": launches,
+            "autotune": ctx.tuning(),
+            "accuracy_vs_fp64": accuracy,
             "clocks": clocks,
         }
+        if args.serve_seconds > 0:
+            line["latency"] = serve_latency(args, lrank, prec)
         if not args.no_cpu_baseline:
             cb, _ = cpu_baseline(wl, args.cpu_samples)
             line["cpu_baseline"] = cb

@@ -53,6 +53,12 @@ typedef enum {
     WPCD_ERR_HANDLE = -8      /* unknown or released handle / ticket */
 } wpcd_status;
 
+/* Arithmetic of the eigensolve.  FP64: H assembled and diagonalised in FP64
+ * (parallel Jacobi).  MIXED: H diagonalised in FP32 (the same Jacobi with a
+ * relative rotation threshold), then two FP64 refinement iterations of the
+ * eigenpairs (Ogita-Aishima: Y = HX, S = X^T Y, G = X^T X, X <- X(I + E)) as
+ * batched FP64 products; everything after the eigensolve (resolvent logs, T,
+ * S, phases) is FP64 on both paths. */
 typedef enum { WPCD_PREC_FP64 = 0, WPCD_PREC_MIXED = 1 } wpcd_precision;
 
 /* Resolvent used for the on-shell T (App. B).  FREE_BIN: the SWP resolvent
@@ -72,9 +78,17 @@ enum {
     WPCD_GEN_YUKAWA = 1     /* 19 params (masses m1..m3, regulator Lambda, 14 V0 strengths, 1S0 tz!=0 contact); 15 terms */
 };
 
-/* Execution modes (wpcd_set_option key WPCD_OPT_EXEC). */
+/* Options (wpcd_set_option).  WPCD_OPT_EXEC: one launch per size bucket
+ * (BATCHED) or one launch per (sample, channel) solve (PLAIN, the baseline
+ * execution).  WPCD_OPT_REFINE: engine of the mixed path's FP64 refinement
+ * products -- TENSOR (BF16 tensor cores with Ozaki splitting, FP64-accurate) or
+ * FP64 (FP64 CUDA cores).  WPCD_OPT_AUTOTUNE (1 = on, the default): on the first
+ * batched eigensolve of each (matrix size, precision) the context times CTA
+ * sizes 64/128/256/512 on about two full waves of that bucket and keeps the
+ * fastest (wpcd_tuning reports the choices); 0 = fixed 256 threads. */
 enum { WPCD_EXEC_BATCHED = 0, WPCD_EXEC_PLAIN = 1 };
-enum { WPCD_OPT_EXEC = 1 };
+enum { WPCD_REFINE_TENSOR = 0, WPCD_REFINE_FP64 = 1 };
+enum { WPCD_OPT_EXEC = 1, WPCD_OPT_REFINE = 2, WPCD_OPT_AUTOTUNE = 3 };
 
 /* ---- context --------------------------------------------------------------------------------- */
 
@@ -148,7 +162,8 @@ wpcd_status wpcd_vset_get(wpcd_ctx *ctx, int vset_id, int channel, double *out_h
  * (H0_ii = <x_i|h0|x_i> exactly, repeated on both l-blocks of a coupled
  * channel), then H = C D C^T with eigenvalues ascending.  coeffs_dev:
  * [n_samples][n_terms-1] FP64 (may be NULL when n_terms == 1).  The eigenpairs
- * stay on the device under the returned eig handle.  prec: WPCD_PREC_FP64.
+ * stay on the device under the returned eig handle.  prec: WPCD_PREC_FP64 or
+ * WPCD_PREC_MIXED (see wpcd_precision).
  * Per-solve convergence status: wpcd_diag_status.
  * Errors: WPCD_ERR_ARG, WPCD_ERR_HANDLE, WPCD_ERR_NOMEM, WPCD_ERR_BUDGET, WPCD_ERR_CUDA. */
 wpcd_status wpcd_diag(wpcd_ctx *ctx, int vset_id, const double *coeffs_dev, int n_samples,
@@ -214,8 +229,28 @@ enum {
     WPCD_PHASE_TMATRIX = 4,     /* SWP boundaries, resolvent, T, phases at the bins */
     WPCD_PHASE_GATHER = 5,      /* T at the requested energies */
     WPCD_PHASE_OBSERVABLES = 6, /* interpolation and cross section */
-    WPCD_PHASE_COUNT = 7
+    WPCD_PHASE_REFINE = 7,      /* FP64 refinement of the mixed path's eigenpairs */
+    WPCD_PHASE_COUNT = 8
 };
+
+/* Batched square products C_b = op(A_b) B_b (op(A) = A^T if trans_a) for `items`
+ * n x n row-major FP64 matrices stored back to back, queued on the context
+ * stream -- the refinement products of the mixed path, exposed for reuse and
+ * testing.  engine WPCD_REFINE_TENSOR: each row of op(A) and column of B is
+ * scaled by a power of two, rounded to 48 bits and split into six 8-bit
+ * digits (exact in BF16); digit products are summed exactly in FP32 on the
+ * tensor cores (k <= 256 per sum) and combined in FP64 (Ozaki, Ogita, Oishi,
+ * Rump, "Error-free transformations of matrix multiplication", 2012).  Error
+ * <~ 2^-49 (max_k|op(A)_ik| sum_k|B_kj| + sum_k|op(A)_ik| max_k|B_kj|).
+ * engine WPCD_REFINE_FP64: FP64 FMA.
+ * n <= 1024.  Errors: WPCD_ERR_ARG, WPCD_ERR_NOMEM, WPCD_ERR_CUDA. */
+wpcd_status wpcd_batched_dgemm(wpcd_ctx *ctx, int n, int items, int trans_a, const double *A_dev,
+                               const double *B_dev, double *C_dev, int engine);
+
+/* The autotuner's table: up to max_entries (n, precision, chosen CTA size) and,
+ * in ms_out[4 k + j], the measured time per solve of candidate j (64, 128, 256,
+ * 512 threads; negative = not run).  Returns the number of entries. */
+int wpcd_tuning(wpcd_ctx *ctx, int max_entries, int *n_out, int *prec_out, int *threads_out, float *ms_out);
 
 /* Number of kernels this context has launched since creation (host count). */
 unsigned long long wpcd_kernel_launches(const wpcd_ctx *ctx);
@@ -230,6 +265,59 @@ wpcd_status wpcd_profile_read(wpcd_ctx *ctx, int phase, double *ms_total, long *
 
 /* Number of channels and matrix size of channel c in a vset. */
 wpcd_status wpcd_vset_info(wpcd_ctx *ctx, int vset_id, int *n_ch, int *n_terms, int channel, int *n);
+
+/* ---- serving: continuous batching -----------------------------------------------------------
+ * wpcd_serve_start builds, for every N_WP in n_wp_list, the default mesh
+ * (tan^2 map to 8 fm^-1, 8 points per bin, momentum packets) and the projected
+ * potential of the channel set, keeps them resident, and starts a worker
+ * thread with n_slots executors (each its own CUDA stream and workspaces).
+ * Requests queue FIFO; whenever a slot is free the worker takes the oldest
+ * request and every queued request with the same (N_WP, precision), up to
+ * max_batch, and runs the whole hot path for that batch on the slot's stream
+ * (each request keeps its own energy list), so batches overlap on the device
+ * and new requests join as slots free up.  Admission: wpcd_submit refuses with
+ * WPCD_ERR_BUDGET when max_queue requests wait, or when the context has an HBM
+ * budget and the queued requests' working memory would exceed what is left.
+ * Results (delta [n_ch][n_E][3] deg, sigma [n_E] mb, T [n_ch][n_E][2][2]
+ * complex, host memory) belong to the context until wpcd_release_result;
+ * latency_us is submit -> results ready on the host.  No counterpart in the
+ * paper (its GPU code ran one prediction at a time). */
+typedef struct {
+    const double *coeffs; /* [n_terms] host: the sample's coefficients (n_terms = model terms - 1) */
+    int n_terms;
+    const double *e_lab;  /* [n_E] host, MeV */
+    int n_E;
+    int n_wp;             /* one of the served N_WP */
+    wpcd_precision prec;
+} wpcd_request;
+
+typedef struct {
+    wpcd_status status;
+    int n_E, n_ch;
+    const double *delta;
+    const double *sigma;
+    const double *T;
+    double latency_us;
+} wpcd_result;
+
+wpcd_status wpcd_serve_start(wpcd_ctx *ctx, const wpcd_channel *channels, int n_ch, int generator_id,
+                             const double *gen_params_host, int n_gen_params, int n_terms, const int *n_wp_list,
+                             int n_nwp, int max_batch, int n_slots, int max_queue);
+/* Drain the queue, stop the worker and free the serving state. */
+wpcd_status wpcd_serve_stop(wpcd_ctx *ctx);
+/* Copy a request (the caller may reuse its buffers afterwards).  Errors:
+ * WPCD_ERR_ARG (no server, unserved N_WP, bad energies, a matrix larger than
+ * the precision's eigensolver holds), WPCD_ERR_BUDGET (admission refused). */
+wpcd_status wpcd_submit(wpcd_ctx *ctx, const wpcd_request *req, uint64_t *ticket);
+/* WPCD_OK and the result, WPCD_ERR_NOTREADY while in flight, WPCD_ERR_HANDLE for an unknown ticket. */
+wpcd_status wpcd_poll(wpcd_ctx *ctx, uint64_t ticket, wpcd_result *out);
+/* As wpcd_poll, blocking up to timeout_ms; WPCD_ERR_TIMEOUT if still in flight. */
+wpcd_status wpcd_wait(wpcd_ctx *ctx, uint64_t ticket, int timeout_ms, wpcd_result *out);
+/* Free a finished request's results (no-op while it is in flight). */
+void wpcd_release_result(wpcd_ctx *ctx, uint64_t ticket);
+/* Requests finished, batches launched, requests waiting. */
+wpcd_status wpcd_serve_stats(wpcd_ctx *ctx, unsigned long long *completed, unsigned long long *batches,
+                             unsigned long long *queued);
 
 /* ---- the per-channel hot path without device allocation -------------------------------------
  * No counterpart in the paper: this entry point exists for callers that cannot

@@ -18,13 +18,26 @@ EXPORTED = [
     "wpcd_mesh", "wpcd_mesh_get", "wpcd_project", "wpcd_vset_get", "wpcd_vset_info", "wpcd_diag",
     "wpcd_diag_status", "wpcd_eig_get", "wpcd_tmatrix", "wpcd_observables", "wpcd_solve", "wpcd_solve_host",
     "wpcd_release", "wpcd_kernel_launches", "wpcd_profile", "wpcd_profile_read",
-    "wpcd_channel_solve_noalloc",
+    "wpcd_channel_solve_noalloc", "wpcd_serve_start", "wpcd_serve_stop", "wpcd_submit", "wpcd_poll", "wpcd_wait",
+    "wpcd_release_result", "wpcd_serve_stats", "wpcd_batched_dgemm", "wpcd_tuning",
 ]
 
 
 class wpcd_channel(ctypes.Structure):
     _fields_ = [("s", ctypes.c_int), ("J", ctypes.c_int), ("l", ctypes.c_int), ("lp", ctypes.c_int),
                 ("coupled", ctypes.c_int), ("tz", ctypes.c_int)]
+
+
+class wpcd_request(ctypes.Structure):
+    _fields_ = [("coeffs", ctypes.POINTER(ctypes.c_double)), ("n_terms", ctypes.c_int),
+                ("e_lab", ctypes.POINTER(ctypes.c_double)), ("n_E", ctypes.c_int), ("n_wp", ctypes.c_int),
+                ("prec", ctypes.c_int)]
+
+
+class wpcd_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("n_E", ctypes.c_int), ("n_ch", ctypes.c_int),
+                ("delta", ctypes.POINTER(ctypes.c_double)), ("sigma", ctypes.POINTER(ctypes.c_double)),
+                ("T", ctypes.POINTER(ctypes.c_double)), ("latency_us", ctypes.c_double)]
 
 
 _vp = ctypes.c_void_p
@@ -57,6 +70,16 @@ _SIG = {
     "wpcd_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long)]),
     "wpcd_channel_solve_noalloc": (_i, [_i, _i, _d, _d, _d, _i, _i, wpcd_channel, _vp, _i, _vp, _i, _vp, _i, _vp,
                                         _vp, _vp, _vp]),
+    "wpcd_serve_start": (_i, [_vp, ctypes.POINTER(wpcd_channel), _i, _i, _vp, _i, _i, _ip, _i, _i, _i, _i]),
+    "wpcd_serve_stop": (_i, [_vp]),
+    "wpcd_submit": (_i, [_vp, ctypes.POINTER(wpcd_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "wpcd_poll": (_i, [_vp, ctypes.c_uint64, ctypes.POINTER(wpcd_result)]),
+    "wpcd_wait": (_i, [_vp, ctypes.c_uint64, _i, ctypes.POINTER(wpcd_result)]),
+    "wpcd_release_result": (None, [_vp, ctypes.c_uint64]),
+    "wpcd_batched_dgemm": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp, _i]),
+    "wpcd_tuning": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
+    "wpcd_serve_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong),
+                              ctypes.POINTER(ctypes.c_ulonglong)]),
 }
 
 _lock = threading.Lock()

@@ -18,7 +18,8 @@ WPCD_ERR_NOTREADY = -7
 PREC_FP64, PREC_MIXED = 0, 1
 AVG_FREE_BIN = 0
 EXEC_BATCHED, EXEC_PLAIN = 0, 1
-OPT_EXEC = 1
+REFINE_TENSOR, REFINE_FP64 = 0, 1
+OPT_EXEC, OPT_REFINE, OPT_AUTOTUNE = 1, 2, 3
 
 
 class WpcdError(RuntimeError):
@@ -73,6 +74,29 @@ class Context:
     def set_exec(self, mode: int):
         _ck(self.lib.wpcd_set_option(self.h, OPT_EXEC, mode), "wpcd_set_option")
 
+    def set_refine_engine(self, engine: int):
+        _ck(self.lib.wpcd_set_option(self.h, OPT_REFINE, engine), "wpcd_set_option")
+
+    def batched_dgemm(self, A, B, C, trans_a=False, engine=REFINE_TENSOR):
+        """C[b] = op(A[b]) @ B[b] for (items, n, n) float64 device tensors."""
+        items, n, _ = A.shape
+        _ck(self.lib.wpcd_batched_dgemm(self.h, n, items, 1 if trans_a else 0, _ptr(A), _ptr(B), _ptr(C), engine),
+            "wpcd_batched_dgemm")
+
+    def set_autotune(self, on: bool):
+        _ck(self.lib.wpcd_set_option(self.h, OPT_AUTOTUNE, 1 if on else 0), "wpcd_set_option")
+
+    def tuning(self) -> list:
+        m = 64
+        n = np.zeros(m, dtype=np.int32)
+        p = np.zeros(m, dtype=np.int32)
+        t = np.zeros(m, dtype=np.int32)
+        ms = np.zeros(4 * m, dtype=np.float32)
+        k = self.lib.wpcd_tuning(self.h, m, _ptr(n), _ptr(p), _ptr(t), _ptr(ms))
+        return [{"n": int(n[i]), "precision": ("fp64", "mixed")[int(p[i])], "threads": int(t[i]),
+                 "ms_per_solve": {c: float(ms[4 * i + j]) for j, c in enumerate((64, 128, 256, 512))}}
+                for i in range(k)]
+
     def sync(self):
         _ck(self.lib.wpcd_sync(self.h), "wpcd_sync")
 
@@ -82,7 +106,7 @@ class Context:
     def bytes_in_use(self) -> int:
         return self.lib.wpcd_bytes_in_use(self.h)
 
-    PHASES = ["mesh", "project", "eigen", "plan", "tmatrix", "gather", "observables"]
+    PHASES = ["mesh", "project", "eigen", "plan", "tmatrix", "gather", "observables", "refine"]
 
     def kernel_launches(self) -> int:
         return int(self.lib.wpcd_kernel_launches(self.h))
@@ -139,7 +163,7 @@ class Context:
         return out
 
     # ------------------------------------------------------------------ hot path
-    def diag(self, vset_id, coeffs, n_samples, prec=PREC_FP64) -> int:
+    def diag(self, vset_id, coeffs, n_samples, prec=PREC_FP64) -> int:  # noqa: D401
         eid = ctypes.c_int()
         _ck(self.lib.wpcd_diag(self.h, vset_id, _ptr(coeffs), n_samples, prec, ctypes.byref(eid)), "wpcd_diag")
         return eid.value
@@ -170,6 +194,75 @@ class Context:
         coeffs = None if coeffs is None else np.ascontiguousarray(coeffs, dtype=np.float64)
         _ck(self.lib.wpcd_solve_host(self.h, vset_id, _ptr(coeffs), n_samples, _ptr(e_lab), e_lab.size, prec,
                                      AVG_FREE_BIN, _ptr(t_out), _ptr(delta), _ptr(sigma)), "wpcd_solve_host")
+
+
+class ServedResult:
+    """One finished request: delta [n_ch, n_E, 3] deg, sigma [n_E] mb, T [n_ch, n_E, 2, 2] complex."""
+
+    def __init__(self, r):
+        nch, nE = r.n_ch, r.n_E
+        self.status = r.status
+        self.latency_us = r.latency_us
+        self.delta = np.ctypeslib.as_array(r.delta, shape=(nch * nE * 3,)).reshape(nch, nE, 3).copy()
+        self.sigma = np.ctypeslib.as_array(r.sigma, shape=(nE,)).copy()
+        t = np.ctypeslib.as_array(r.T, shape=(nch * nE * 8,)).copy()
+        self.T = t.view(np.complex128).reshape(nch, nE, 2, 2)
+
+
+def _serve_methods():
+    def serve_start(self, channels, gen, gen_params, n_terms, n_wp_list, max_batch=64, n_slots=4,
+                    max_queue=1 << 16):
+        n = len(channels)
+        arr = (_lib.wpcd_channel * n)(*[_lib.wpcd_channel(*c.astuple()) for c in channels])
+        gp = np.ascontiguousarray(gen_params, dtype=np.float64)
+        nw = (ctypes.c_int * len(n_wp_list))(*n_wp_list)
+        _ck(self.lib.wpcd_serve_start(self.h, arr, n, gen, _ptr(gp), gp.size, n_terms, nw, len(n_wp_list),
+                                      max_batch, n_slots, max_queue), "wpcd_serve_start")
+        self._n_terms = n_terms
+
+    def submit(self, coeffs, e_lab, n_wp, prec=PREC_FP64, raise_on_error=True):
+        e = np.ascontiguousarray(e_lab, dtype=np.float64)
+        c = None if coeffs is None else np.ascontiguousarray(coeffs, dtype=np.float64)
+        rq = _lib.wpcd_request(
+            None if c is None else c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0 if c is None else c.size,
+            e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), e.size, n_wp, prec)
+        t = ctypes.c_uint64()
+        code = self.lib.wpcd_submit(self.h, ctypes.byref(rq), ctypes.byref(t))
+        if code != WPCD_OK:
+            if raise_on_error:
+                raise WpcdError(code, "wpcd_submit")
+            return code
+        return t.value
+
+    def poll(self, ticket):
+        r = _lib.wpcd_result()
+        code = self.lib.wpcd_poll(self.h, ticket, ctypes.byref(r))
+        if code == WPCD_ERR_NOTREADY:
+            return None
+        _ck(code, "wpcd_poll")
+        return ServedResult(r)
+
+    def wait(self, ticket, timeout_ms=60000):
+        r = _lib.wpcd_result()
+        _ck(self.lib.wpcd_wait(self.h, ticket, timeout_ms, ctypes.byref(r)), "wpcd_wait")
+        return ServedResult(r)
+
+    def release_result(self, ticket):
+        self.lib.wpcd_release_result(self.h, ticket)
+
+    def serve_stop(self):
+        _ck(self.lib.wpcd_serve_stop(self.h), "wpcd_serve_stop")
+
+    def serve_stats(self):
+        a, b, q = ctypes.c_ulonglong(), ctypes.c_ulonglong(), ctypes.c_ulonglong()
+        _ck(self.lib.wpcd_serve_stats(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(q)), "wpcd_serve_stats")
+        return {"completed": a.value, "batches": b.value, "queued": q.value}
+
+    for f in (serve_start, submit, poll, wait, release_result, serve_stop, serve_stats):
+        setattr(Context, f.__name__, f)
+
+
+_serve_methods()
 
 
 class Model:

@@ -19,7 +19,7 @@
 
 namespace wpcd {
 
-constexpr int kJacThreads = 256;
+constexpr int kJacMaxThreads = 512;  // launch bound; the launch picks 64..512
 constexpr int kMaxSweeps = 40;
 constexpr size_t kSmemCap = 200 * 1024;
 
@@ -66,7 +66,7 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 }
 
 template <bool C_SMEM>
-__global__ void __launch_bounds__(kJacThreads) k_jacobi_f64(const ChanDev *chans, const int *work_ch, int n_work_ch,
+__global__ void __launch_bounds__(kJacMaxThreads) k_jacobi_f64(const ChanDev *chans, const int *work_ch, int n_work_ch,
                                                              int sample0, int n_terms, const double *coeffs,
                                                              double *eps_all, double *C_all, int *status_all,
                                                              int n_ch_total, int *err)
@@ -246,22 +246,38 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi_f64(const ChanDev *chans
 
 cudaError_t launch_jacobi_f64(const ChanDev *chans_dev, const int *work_ch_dev, int n_work_ch, int n_samples,
                               int sample0, int n_terms, const double *coeffs, int n, double *eps_all, double *C_all,
-                              int *status_all, int n_ch_total, int *err, cudaStream_t st)
+                              int *status_all, int n_ch_total, int *err, cudaStream_t st, int threads)
 {
+    if (threads < 32 || threads > kJacMaxThreads || (threads & 31)) return cudaErrorInvalidValue;
     bool cs = jacobi_c_in_smem(n);
     size_t smem = jacobi_smem_bytes(n, cs);
-    if (!cs && (size_t)8 * 8 * n > packed_len(n) * 8) return cudaErrorInvalidValue;  // row buffers must fit in A
+    if (!cs && (size_t)(threads / 32) * n > packed_len(n)) return cudaErrorInvalidValue;  // row buffers fit in A
     dim3 grid((unsigned)(n_samples * n_work_ch));
     if (cs) {
         cudaFuncSetAttribute(k_jacobi_f64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_jacobi_f64<true><<<grid, kJacThreads, smem, st>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
+        k_jacobi_f64<true><<<grid, threads, smem, st>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
                                                             coeffs, eps_all, C_all, status_all, n_ch_total, err);
     } else {
         cudaFuncSetAttribute(k_jacobi_f64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_jacobi_f64<false><<<grid, kJacThreads, smem, st>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
+        k_jacobi_f64<false><<<grid, threads, smem, st>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
                                                              coeffs, eps_all, C_all, status_all, n_ch_total, err);
     }
     return cudaGetLastError();
+}
+
+int jacobi_f64_occupancy(int n, int threads)
+{
+    const bool cs = jacobi_c_in_smem(n);
+    const size_t smem = jacobi_smem_bytes(n, cs);
+    int blocks = 0;
+    if (cs) {
+        cudaFuncSetAttribute(k_jacobi_f64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_jacobi_f64<true>, threads, smem);
+    } else {
+        cudaFuncSetAttribute(k_jacobi_f64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_jacobi_f64<false>, threads, smem);
+    }
+    return blocks;
 }
 
 }  // namespace wpcd

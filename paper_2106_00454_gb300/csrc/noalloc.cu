@@ -128,7 +128,7 @@ extern "C" wpcd_status wpcd_channel_solve_noalloc(int n_wp, int mesh_kind, doubl
     cd.eps_off = 0;
     cd.c_off = 0;
 
-    PlanDev plan;
+    PlanDev plan{};  // one plan shared by all samples
     plan.bin = reinterpret_cast<int *>(base + o_bin);
     plan.brk = reinterpret_cast<int *>(base + o_brk);
     plan.cnt = reinterpret_cast<int *>(base + o_cnt);

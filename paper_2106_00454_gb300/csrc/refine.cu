@@ -1,0 +1,286 @@
+// refine.cu -- FP64 refinement of approximate eigenpairs (mixed path).
+//
+// The FP32 eigensolve leaves eigenvectors X whose errors reach ~1e-4 inside
+// the closely spaced low-energy part of the spectrum.  Each refinement
+// iteration (Ogita & Aishima, "Iterative refinement for symmetric eigenvalue
+// decomposition", 2018) computes in FP64
+//     Y = H X,  S = X^T Y,  G = X^T X,  R = I - G,
+//     lambda_i = S_ii / G_ii,
+//     E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)   if |lambda_j - lambda_i| > delta,
+//     E_ij = R_ij / 2                                         otherwise (and on the diagonal),
+//     delta = 2 (||S - diag(lambda)||_F + max|lambda| ||R||_F),
+//     X <- X (I + E),
+// which squares the eigenvector error.  After the last iteration every
+// eigenvalue is the FP64 Rayleigh quotient of its refined vector,
+// lambda_i = (X^T H X)_ii / (X^T X)_ii.  The four products are batched FP64
+// GEMMs over every (sample, channel) item of one chunk of a size bucket; the
+// working matrices of item b sit contiguously at b * n^2 in scratch buffers,
+// and the final sort writes the eigenpairs into the eigen-buffer layout
+// (channel offset + sample * n^2).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "wpcd_internal.cuh"
+
+namespace wpcd {
+
+// H = diag(H0) + V0 + sum_a c_a V_a in FP64, full n x n.
+__global__ void k_assemble_h64(const ChanDev *chans, const int *work, int nw, int sample0, int n, int n_terms,
+                               const double *coeffs, double *H_all)
+{
+    const int b = blockIdx.y;
+    const int wc = b % nw, smp = sample0 + b / nw;
+    const ChanDev ch = chans[work[wc]];
+    double *H = H_all + (size_t)b * n * n;
+    const double *cf = coeffs ? coeffs + (size_t)smp * (n_terms - 1) : nullptr;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+        double v = ch.V[e];
+        for (int a = 1; a < n_terms; ++a) v = fma(cf[a - 1], ch.V[(size_t)a * n * n + e], v);
+        const int i = e / n, j = e - i * n;
+        if (i == j) v += ch.h0[i % ch.N];
+        H[e] = v;
+    }
+}
+
+// Batched C = op(A) B (n x n, row-major), op(A) = A^T when TA.  64 x 64 output
+// tile per CTA, 16-deep k steps through shared memory, 4 x 4 outputs per thread.
+constexpr int kBM = 64, kBK = 16;
+
+template <bool TA>
+__global__ void __launch_bounds__(256) k_bgemm64(int n, const double *A_all, const double *B_all, double *C_all)
+{
+    __shared__ double As[kBK][kBM];
+    __shared__ double Bs[kBK][kBM];
+    const size_t off = (size_t)blockIdx.z * n * n;
+    const double *A = A_all + off, *B = B_all + off;
+    double *C = C_all + off;
+    const int row0 = blockIdx.y * kBM, col0 = blockIdx.x * kBM;
+    const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < n; k0 += kBK) {
+        // op(A) tile [rows row0.., k k0..] stored k-major; B tile [k, cols] stored k-major
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = tid + u * 256;  // 0..1023
+            int kk, r;
+            if (TA) {  // op(A)[r][k] = A[k][r]: read along r (coalesced)
+                kk = e / kBM;
+                r = e % kBM;
+            } else {   // A[r][k]: read along k
+                r = e / kBK;
+                kk = e % kBK;
+            }
+            const int gr = row0 + r, gk = k0 + kk;
+            double v = 0.0;
+            if (gr < n && gk < n) v = TA ? A[(size_t)gk * n + gr] : A[(size_t)gr * n + gk];
+            As[kk][r] = v;
+            const int bk = e / kBM, bc = e % kBM;
+            const int gbk = k0 + bk, gbc = col0 + bc;
+            Bs[bk][bc] = (gbk < n && gbc < n) ? B[(size_t)gbk * n + gbc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kBK; ++kk) {
+            double a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gr = row0 + ty * 4 + i;
+        if (gr >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gc = col0 + tx * 4 + j;
+            if (gc < n) C[(size_t)gr * n + gc] = acc[i][j];
+        }
+    }
+}
+
+// One CTA per item: lambda, the threshold delta, and I + E written over G.
+__global__ void __launch_bounds__(256) k_oa_update(int n, const double *H_all, const double *S_all, double *G_all,
+                                                   double *lam_all)
+{
+    extern __shared__ double lam[];  // n
+    __shared__ double red[32];
+    const int b = blockIdx.x;
+    const size_t off = (size_t)b * n * n;
+    const double *H = H_all + off, *S = S_all + off;
+    double *G = G_all + off;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = S[(size_t)i * n + i] / G[(size_t)i * n + i];
+    __syncthreads();
+    double sd = 0.0, hh = 0.0, rr = 0.0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e - i * n;
+        const double s = S[e] - (i == j ? lam[i] : 0.0);
+        const double r = (i == j ? 1.0 : 0.0) - G[e];
+        sd += s * s;
+        rr += r * r;
+    }
+    sd = cta_sum64(sd, red);
+    rr = cta_sum64(rr, red);
+    // ||H||_2 estimated by the largest |lambda| (Frobenius norms bound the other two)
+    double lmax = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lmax = fmax(lmax, fabs(lam[i]));
+    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lmax;
+    __syncthreads();
+    lmax = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lmax = fmax(lmax, red[w]);
+    (void)hh;
+    const double delta = 2.0 * (sqrt(sd) + lmax * sqrt(rr));
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int i = e / n, j = e - i * n;
+        const double r = (i == j ? 1.0 : 0.0) - G[e];
+        double E;
+        if (i == j) {
+            E = 0.5 * r;
+        } else {
+            const double dl = lam[j] - lam[i];
+            E = (fabs(dl) > delta) ? (S[e] + lam[j] * r) / dl : 0.5 * r;
+        }
+        G[e] = (i == j ? 1.0 : 0.0) + E;
+    }
+    double *lo = lam_all + (size_t)b * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lo[i] = lam[i];
+}
+
+// lambda_i = (X_i . Y_i) / (X_i . X_i) with Y = H X, columns i; one CTA per item.
+__global__ void __launch_bounds__(256) k_rayleigh(int n, const double *X_all, const double *Y_all, double *lam_all)
+{
+    const size_t off = (size_t)blockIdx.x * n * n;
+    const double *X = X_all + off, *Y = Y_all + off;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double num = 0.0, den = 0.0;
+        for (int r = 0; r < n; ++r) {
+            const double x = X[(size_t)r * n + i];
+            num = fma(x, Y[(size_t)r * n + i], num);
+            den = fma(x, x, den);
+        }
+        lam_all[(size_t)blockIdx.x * n + i] = num / den;
+    }
+}
+
+// Sort the eigenvalues ascending and write them, with the columns of X
+// permuted alike, into the eigen-buffer layout of their (sample, channel).
+__global__ void __launch_bounds__(256) k_sort_eig(const ChanDev *chans, const int *work, int nw, int sample0, int n,
+                                                  const double *lam_s, const double *X_s, double *eps_all,
+                                                  double *X_all)
+{
+    extern __shared__ double sm[];
+    double *lam = sm;                               // n
+    int *rank = reinterpret_cast<int *>(lam + n);   // n
+    const int b = blockIdx.x;
+    const int wc = b % nw, smp = sample0 + b / nw;
+    const ChanDev ch = chans[work[wc]];
+    const double *Xs = X_s + (size_t)b * n * n;
+    double *X = X_all + ch.c_off + (size_t)smp * n * n;
+    double *eps = eps_all + ch.eps_off + (size_t)smp * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = lam_s[(size_t)b * n + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double ei = lam[i];
+        int r = 0;
+        for (int j = 0; j < n; ++j) r += (lam[j] < ei) || (lam[j] == ei && j < i);
+        rank[i] = r;
+        eps[r] = ei;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int row = e / n, c = e - row * n;
+        X[(size_t)row * n + rank[c]] = Xs[e];
+    }
+}
+
+size_t sort_eig_smem(int n) { return (size_t)n * 8 + (size_t)n * 4; }
+
+size_t refine_scratch_per_item(int n, int engine)
+{
+    size_t b = (size_t)5 * n * n * 8 + (size_t)n * 8;  // X, H, Y, W1, W2, lambda
+    if (engine == 0) b += 2 * oz_slice_elems(n) * 2 + (size_t)2 * n * 4 + 512;
+    return b;
+}
+
+// Refine the eigenpairs of `items` = n_samples * nw items of one bucket chunk.
+// scratch: refine_scratch_per_item(n, engine) bytes per item, carved here.
+// Xs (first n^2 doubles of each item's block) holds the FP32-solve
+// eigenvectors as FP64 on entry.  iters must be even.
+cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_samples, int sample0, int n,
+                          int n_terms, const double *coeffs, void *scratch, double *eps_all, double *X_all,
+                          int iters, int engine, cudaStream_t st)
+{
+    if (iters < 0 || (iters & 1)) return cudaErrorInvalidValue;
+    const int items = n_samples * nw;
+    const size_t nn = (size_t)items * n * n;
+    double *Xs = static_cast<double *>(scratch);
+    double *H = Xs + nn, *Y = H + nn, *W1 = Y + nn, *W2 = W1 + nn, *lam = W2 + nn;
+    // slices start on a 256-byte boundary (16-byte vector loads)
+    const uintptr_t sa_addr = (reinterpret_cast<uintptr_t>(lam + (size_t)items * n) + 255) & ~(uintptr_t)255;
+    __nv_bfloat16 *sa = reinterpret_cast<__nv_bfloat16 *>(sa_addr);
+    __nv_bfloat16 *sb = sa + (size_t)items * oz_slice_elems(n);
+    int *ea = reinterpret_cast<int *>(sb + (size_t)items * oz_slice_elems(n));
+    int *eb = ea + (size_t)items * n;
+    const int tiles = (n + kBM - 1) / kBM;
+    const dim3 gg(tiles, tiles, items);
+    auto gemm = [&](bool ta, const double *A, const double *B, double *C) {
+        if (engine == 0) return launch_oz_gemm(n, items, ta, A, B, C, sa, sb, ea, eb, st);
+        if (ta) k_bgemm64<true><<<gg, 256, 0, st>>>(n, A, B, C);
+        else k_bgemm64<false><<<gg, 256, 0, st>>>(n, A, B, C);
+        return cudaGetLastError();
+    };
+    const int ab = (n * n + 255) / 256 < 64 ? (n * n + 255) / 256 : 64;
+    k_assemble_h64<<<dim3(ab, items), 256, 0, st>>>(chans, work, nw, sample0, n, n_terms, coeffs, H);
+    double *x = Xs, *xn = Y;
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+        if ((e = gemm(false, H, x, xn))) break;   // Y = H X
+        if ((e = gemm(true, x, xn, W1))) break;   // S = X^T Y
+        if ((e = gemm(true, x, x, W2))) break;    // G = X^T X
+        k_oa_update<<<items, 256, (size_t)n * 8, st>>>(n, H, W1, W2, lam);
+        if ((e = gemm(false, x, W2, xn))) break;  // X (I + E)
+        double *t = x;
+        x = xn;
+        xn = t;
+    }
+    if (e != cudaSuccess) return e;
+    if (iters > 0) {
+        if ((e = gemm(false, H, x, xn))) return e;  // Y = H X for the Rayleigh quotients
+        k_rayleigh<<<items, 256, 0, st>>>(n, x, xn, lam);
+    }
+    k_sort_eig<<<items, 256, sort_eig_smem(n), st>>>(chans, work, nw, sample0, n, lam, Xs, eps_all, X_all);
+    return cudaGetLastError();
+}
+
+// Batched products through either engine (exposed for tests and callers).
+cudaError_t launch_batched_dgemm(int n, int items, bool ta, const double *A, const double *B, double *C,
+                                 void *scratch, int engine, cudaStream_t st)
+{
+    if (engine == 0) {
+        __nv_bfloat16 *sa = static_cast<__nv_bfloat16 *>(scratch);
+        __nv_bfloat16 *sb = sa + (size_t)items * oz_slice_elems(n);
+        int *ea = reinterpret_cast<int *>(sb + (size_t)items * oz_slice_elems(n));
+        return launch_oz_gemm(n, items, ta, A, B, C, sa, sb, ea, ea + (size_t)items * n, st);
+    }
+    const int tiles = (n + kBM - 1) / kBM;
+    const dim3 gg(tiles, tiles, items);
+    if (ta) k_bgemm64<true><<<gg, 256, 0, st>>>(n, A, B, C);
+    else k_bgemm64<false><<<gg, 256, 0, st>>>(n, A, B, C);
+    return cudaGetLastError();
+}
+
+size_t batched_dgemm_scratch(int n, int items) { return (size_t)items * (2 * oz_slice_elems(n) * 2 + 2 * n * 4) + 512; }
+
+}  // namespace wpcd

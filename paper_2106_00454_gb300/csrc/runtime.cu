@@ -3,10 +3,16 @@
 // Every numerical step runs in the kernels of the other translation units;
 // this file only allocates, validates, orders launches and copies.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "wpcd_internal.cuh"
@@ -18,6 +24,9 @@ size_t tbin_smem_bytes(int nmax);
 using namespace wpcd;
 
 namespace {
+
+constexpr size_t kRefineScratchBytes = (size_t)8 << 30;  // mixed path: refinement scratch per bucket chunk
+constexpr int kRefineIters = 2;                            // FP64 refinement iterations (even)
 
 struct MeshH {
     int N = 0, Q = 0, kind = 0, wp_kind = 0;
@@ -38,11 +47,28 @@ struct VSetH {
 };
 
 struct EigH {
-    int vset_id = -1, n_samples = 0;
+    int vset_id = -1, n_samples = 0, prec = WPCD_PREC_FP64;
     double *eps = nullptr, *C = nullptr, *coeffs = nullptr;
+    // (the mixed path leaves refined FP64 eigenpairs in eps / C as well)
     int *status = nullptr;
     ChanDev *cd_dev = nullptr;  // vset channels with this eig's offsets
-    size_t eps_len = 0, c_len = 0, coeff_len = 0;
+    size_t eps_len = 0, c_len = 0, coeff_len = 0, status_len = 0, cd_len = 0;
+};
+
+// Grow-only device buffer.
+struct Buf {
+    void *p = nullptr;
+    size_t n = 0;
+};
+
+// One executor: a stream, its device status word and its workspaces.  The
+// synchronous API runs on the context's own executor; each serving slot has
+// one of its own so that batches overlap on the device.
+struct Exec {
+    cudaStream_t stream = nullptr;
+    int *err = nullptr;
+    Buf ws_plan_i, ws_plan_d, ws_tbin, ws_phbin, ws_ref, ws_in, ws_out;
+    EigH eig;
 };
 
 enum Kind { kMesh = 1, kVSet = 2, kEig = 3 };
@@ -65,20 +91,26 @@ struct wpcd_ctx {
     int next_id = 1;
     std::mutex mu;
     int exec_mode = WPCD_EXEC_BATCHED;
+    int refine_engine = WPCD_REFINE_TENSOR;
+    int autotune = 1;
+    int n_sm = 0;
+    struct Tuned {
+        int threads;
+        float ms[4];
+    };
+    std::map<std::pair<int, int>, Tuned> tuned;  // (n, precision) -> eigensolver CTA size
+    std::mutex tmu;
     int *err_dev = nullptr;
+    std::mutex amu;  // device-memory accounting (shared with the serving thread)
+    std::mutex pmu;  // profiling records
     // Gauss-Legendre rules cached on the device, keyed by order
     std::map<int, std::pair<double *, double *>> gl;
-    // grow-only workspaces
-    struct Buf {
-        void *p = nullptr;
-        size_t n = 0;
-    };
-    Buf ws_plan_i, ws_plan_d, ws_tbin, ws_phbin, ws_in, ws_out;
+    Exec main;  // executor of the synchronous API (the caller's stream)
     void *pin_in = nullptr, *pin_out = nullptr;
     size_t pin_in_n = 0, pin_out_n = 0;
-    EigH scratch_eig;  // eigenpairs of wpcd_solve
+    struct Server *server = nullptr;
     // tracing: kernels launched, and (when enabled) CUDA events around each launch
-    unsigned long long launches = 0;
+    std::atomic<unsigned long long> launches{0};
     bool prof = false;
     struct Rec {
         int phase;
@@ -99,6 +131,7 @@ namespace {
 
 wpcd_status dmalloc(wpcd_ctx *c, void **p, size_t bytes)
 {
+    std::lock_guard<std::mutex> lk(c->amu);
     if (bytes == 0) bytes = 8;
     if (c->budget && c->in_use + bytes > c->budget) return WPCD_ERR_BUDGET;
     if (cudaMalloc(p, bytes) != cudaSuccess) {
@@ -113,6 +146,7 @@ wpcd_status dmalloc(wpcd_ctx *c, void **p, size_t bytes)
 void dfree(wpcd_ctx *c, void *p)
 {
     if (!p) return;
+    std::lock_guard<std::mutex> lk(c->amu);
     auto it = c->sizes.find(p);
     if (it != c->sizes.end()) {
         c->in_use -= it->second;
@@ -130,21 +164,24 @@ wpcd_status dalloc(wpcd_ctx *c, T **p, size_t count)
 // Counts one kernel launch of `phase`; with profiling on, brackets it with events.
 struct Launch {
     wpcd_ctx *c;
+    cudaStream_t st;
     wpcd_ctx::Rec r{};
-    Launch(wpcd_ctx *cc, int phase) : c(cc)
+    bool on;
+    Launch(wpcd_ctx *cc, const Exec &X, int phase) : c(cc), st(X.stream), on(cc->prof)
     {
         ++c->launches;
         r.phase = phase;
-        if (c->prof) {
+        if (on) {
             cudaEventCreate(&r.a);
             cudaEventCreate(&r.b);
-            cudaEventRecord(r.a, c->stream);
+            cudaEventRecord(r.a, st);
         }
     }
     ~Launch()
     {
-        if (c->prof) {
-            cudaEventRecord(r.b, c->stream);
+        if (on) {
+            cudaEventRecord(r.b, st);
+            std::lock_guard<std::mutex> lk(c->pmu);
             c->recs.push_back(r);
         }
     }
@@ -152,9 +189,10 @@ struct Launch {
 
 void prof_collect(wpcd_ctx *c)
 {
+    std::lock_guard<std::mutex> lk(c->pmu);
     if (c->recs.empty()) return;
-    cudaStreamSynchronize(c->stream);
     for (auto &r : c->recs) {
+        cudaEventSynchronize(r.b);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, r.a, r.b);
         c->prof_ms[r.phase] += ms;
@@ -165,11 +203,11 @@ void prof_collect(wpcd_ctx *c)
     c->recs.clear();
 }
 
-wpcd_status ws_reserve(wpcd_ctx *c, wpcd_ctx::Buf &b, size_t bytes)
+wpcd_status ws_reserve(wpcd_ctx *c, const Exec &X, Buf &b, size_t bytes)
 {
     if (b.n >= bytes) return WPCD_OK;
     if (b.p) {
-        cudaStreamSynchronize(c->stream);
+        cudaStreamSynchronize(X.stream);
         dfree(c, b.p);
         b.p = nullptr;
         b.n = 0;
@@ -196,8 +234,8 @@ wpcd_status gl_rule(wpcd_ctx *c, int n, double **x, double **w)
         return st;
     }
     {
-        Launch L(c, WPCD_PHASE_MESH);
-        CK(launch_gauss_legendre(n, dx, dw, c->stream));
+        Launch L(c, c->main, WPCD_PHASE_MESH);
+        CK(launch_gauss_legendre(n, dx, dw, c->main.stream));
     }
     c->gl[n] = {dx, dw};
     *x = dx;
@@ -238,9 +276,65 @@ void free_mesh(wpcd_ctx *c, MeshH &m)
     dfree(c, m.h0);
 }
 
+// Autotuner of the eigensolver's CTA size.  On the first batched use of a
+// (matrix size, precision) it times each candidate on about two full waves of
+// the bucket's own solves (occupancy from the CUDA occupancy calculator) and
+// keeps the fastest; the tuning launches write the same outputs the real
+// launch then overwrites.  Returns the CTA size, or -1 on a CUDA error.
+template <class F>
+int pick_threads(wpcd_ctx *c, Exec &X, int n, int prec, int nw, int nsmp, F launch)
+{
+    static const int cand[4] = {64, 128, 256, 512};
+    if (!c->autotune || c->exec_mode != WPCD_EXEC_BATCHED) return 256;
+    const auto key = std::make_pair(n, prec);
+    {
+        std::lock_guard<std::mutex> lk(c->tmu);
+        auto it = c->tuned.find(key);
+        if (it != c->tuned.end()) return it->second.threads;
+    }
+    if (!c->n_sm) cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    wpcd_ctx::Tuned t{256, {-1.f, -1.f, -1.f, -1.f}};
+    float best = 1e30f;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    for (int k = 0; k < 4; ++k) {
+        const int th = cand[k];
+        if (prec == WPCD_PREC_FP64 && !jacobi_c_in_smem(n) && (th / 32) * n > n * (n + 1) / 2) continue;
+        const int occ = prec == WPCD_PREC_FP64 ? jacobi_f64_occupancy(n, th) : jacobi_mixed_occupancy(n, th);
+        if (occ < 1) continue;
+        const int ns = std::max(1, std::min(nsmp, (2 * c->n_sm * occ + nw - 1) / nw));
+        cudaEventRecord(a, X.stream);
+        if (launch(th, ns) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaEventRecord(b, X.stream);
+        if (cudaEventSynchronize(b) != cudaSuccess) {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            return -1;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        const float per = ms / (float)(ns * nw);  // time per solve
+        t.ms[k] = per;
+        if (per < best) {
+            best = per;
+            t.threads = th;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    std::lock_guard<std::mutex> lk(c->tmu);
+    c->tuned[key] = t;
+    return t.threads;
+}
+
 // Allocate (or reuse) eigenpair storage for `S` samples of vset v and run the
 // parameter sum + eigensolve.
-wpcd_status run_diag(wpcd_ctx *c, VSetH &v, int vset_id, const double *coeffs, int S, EigH &e)
+wpcd_status run_diag(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, const double *coeffs, int S, int prec, EigH &e,
+                     bool coeffs_on_device = true)
 {
     size_t eps_len = 0, c_len = 0;
     std::vector<ChanDev> cd = v.cd;
@@ -252,9 +346,10 @@ wpcd_status run_diag(wpcd_ctx *c, VSetH &v, int vset_id, const double *coeffs, i
     }
     const size_t coeff_len = (size_t)S * std::max(v.n_terms - 1, 1);
     wpcd_status st = WPCD_OK;
-    if (e.eps_len < eps_len || e.c_len < c_len || e.coeff_len < coeff_len || e.n_samples != S ||
-        e.vset_id != vset_id || !e.cd_dev) {
-        cudaStreamSynchronize(c->stream);
+    // grow-only storage: a smaller batch or another set with as many channels reuses it
+    if (e.eps_len < eps_len || e.c_len < c_len || e.coeff_len < coeff_len || e.status_len < (size_t)S * v.n_ch ||
+        e.cd_len < (size_t)v.n_ch) {
+        cudaStreamSynchronize(X.stream);
         free_eig(c, e);
         if ((st = dalloc(c, &e.eps, eps_len))) return st;
         if ((st = dalloc(c, &e.C, c_len))) return st;
@@ -264,57 +359,126 @@ wpcd_status run_diag(wpcd_ctx *c, VSetH &v, int vset_id, const double *coeffs, i
         e.eps_len = eps_len;
         e.c_len = c_len;
         e.coeff_len = coeff_len;
+        e.status_len = (size_t)S * v.n_ch;
+        e.cd_len = (size_t)v.n_ch;
     }
     e.vset_id = vset_id;
     e.n_samples = S;
-    CK(cudaMemcpyAsync(e.cd_dev, cd.data(), sizeof(ChanDev) * v.n_ch, cudaMemcpyHostToDevice, c->stream));
+    e.prec = prec;
+    CK(cudaMemcpyAsync(e.cd_dev, cd.data(), sizeof(ChanDev) * v.n_ch, cudaMemcpyHostToDevice, X.stream));
     if (v.n_terms > 1) {
-        CK(cudaMemcpyAsync(e.coeffs, coeffs, sizeof(double) * S * (v.n_terms - 1), cudaMemcpyDeviceToDevice,
-                           c->stream));
+        CK(cudaMemcpyAsync(e.coeffs, coeffs, sizeof(double) * S * (v.n_terms - 1),
+                           coeffs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, X.stream));
     }
     const double *cf = v.n_terms > 1 ? e.coeffs : nullptr;
+    // FP64: one Jacobi launch per size bucket (largest first), or per solve in plain mode.
+    // MIXED: per bucket, in sample chunks sized to the refinement scratch, an FP32
+    // Jacobi launch followed by two FP64 refinement iterations.
+    auto run_bucket = [&](const int *work, int nw, int nsmp, int smp0, int n) -> wpcd_status {
+        const int threads = pick_threads(c, X, n, prec, nw, nsmp, [&](int th, int ns) {
+            if (prec == WPCD_PREC_FP64)
+                return launch_jacobi_f64(e.cd_dev, work, nw, ns, smp0, v.n_terms, cf, n, e.eps, e.C, e.status, v.n_ch,
+                                         X.err, X.stream, th);
+            // the FP32 solve alone, into the start of the refinement scratch
+            const bool cs = jacobi_mixed_smem_bytes(n, true) <= 200 * 1024;
+            const size_t per = refine_scratch_per_item(n, c->refine_engine) + (cs ? 0 : (size_t)n * n * 4) + 256;
+            if (ws_reserve(c, X, X.ws_ref, per * nw * ns)) return cudaErrorMemoryAllocation;
+            unsigned char *base = static_cast<unsigned char *>(X.ws_ref.p);
+            double *Xs = reinterpret_cast<double *>(base);
+            return launch_jacobi_mixed(e.cd_dev, work, nw, ns, smp0, v.n_terms, cf, n, Xs + (size_t)5 * ns * nw * n * n,
+                                       Xs, reinterpret_cast<float *>(base + refine_scratch_per_item(n, c->refine_engine) * nw * ns),
+                                       e.status, v.n_ch, X.err, X.stream, th);
+        });
+        if (threads < 0) return WPCD_ERR_CUDA;
+        if (prec == WPCD_PREC_FP64) {
+            Launch L(c, X, WPCD_PHASE_EIGEN);
+            CK(launch_jacobi_f64(e.cd_dev, work, nw, nsmp, smp0, v.n_terms, cf, n, e.eps, e.C, e.status, v.n_ch,
+                                 X.err, X.stream, threads));
+            return WPCD_OK;
+        }
+        const bool c_smem = jacobi_mixed_smem_bytes(n, true) <= 200 * 1024;
+        const size_t ref_item = refine_scratch_per_item(n, c->refine_engine);
+        const size_t per_item = ref_item + (c_smem ? 0 : (size_t)n * n * 4) + 256;
+        int chunk = (int)std::max<size_t>(1, kRefineScratchBytes / (per_item * nw));
+        chunk = std::min(chunk, nsmp);
+        wpcd_status st2 = ws_reserve(c, X, X.ws_ref, per_item * nw * chunk);
+        if (st2) return st2;
+        unsigned char *base = static_cast<unsigned char *>(X.ws_ref.p);
+        double *Xs = reinterpret_cast<double *>(base);  // first block of the refinement scratch
+        double *lam = Xs + (size_t)5 * chunk * nw * n * n;
+        float *Cf = reinterpret_cast<float *>(base + ref_item * nw * chunk);
+        for (int s0 = 0; s0 < nsmp; s0 += chunk) {
+            const int ns = std::min(chunk, nsmp - s0);
+            {
+                Launch L(c, X, WPCD_PHASE_EIGEN);
+                CK(launch_jacobi_mixed(e.cd_dev, work, nw, ns, smp0 + s0, v.n_terms, cf, n, lam, Xs, Cf, e.status,
+                                       v.n_ch, X.err, X.stream, threads));
+            }
+            Launch L(c, X, WPCD_PHASE_REFINE);
+            CK(launch_refine(e.cd_dev, work, nw, ns, smp0 + s0, n, v.n_terms, cf, base, e.eps, e.C, kRefineIters,
+                             c->refine_engine, X.stream));
+        }
+        return WPCD_OK;
+    };
     if (c->exec_mode == WPCD_EXEC_PLAIN) {
         // one solve per launch: the baseline execution on the same GPU
         for (int s = 0; s < S; ++s)
             for (int k = 0; k < v.n_ch; ++k)
-                CK((Launch(c, WPCD_PHASE_EIGEN), launch_jacobi_f64(e.cd_dev, v.ident_dev + k, 1, 1, s, v.n_terms, cf, cd[k].n, e.eps, e.C, e.status,
-                                     v.n_ch, c->err_dev, c->stream)));
+                if ((st = run_bucket(v.ident_dev + k, 1, 1, s, cd[k].n))) return st;
     } else {
-        // one launch per size bucket, largest first
-        for (auto it = v.buckets.rbegin(); it != v.buckets.rend(); ++it) {
-            const int n = it->first;
-            const int nw = (int)it->second.size();
-            Launch L(c, WPCD_PHASE_EIGEN);
-            CK(launch_jacobi_f64(e.cd_dev, v.bucket_dev[n], nw, S, 0, v.n_terms, cf, n, e.eps, e.C, e.status, v.n_ch,
-                                 c->err_dev, c->stream));
-        }
+        for (auto it = v.buckets.rbegin(); it != v.buckets.rend(); ++it)
+            if ((st = run_bucket(v.bucket_dev[it->first], (int)it->second.size(), S, 0, it->first))) return st;
     }
     return WPCD_OK;
 }
 
-// Energy plan + T at the needed bins into the context workspaces.
-wpcd_status run_tbin(wpcd_ctx *c, VSetH &v, EigH &e, const double *e_lab, int n_E, PlanDev &plan)
+// Energy plan + T at the needed bins into the executor's workspaces.  With
+// n_E_s (device, per-sample list lengths) every sample has its own energy
+// list at e_lab + s * n_E; otherwise one list serves all samples.
+wpcd_status run_tbin(wpcd_ctx *c, Exec &X, VSetH &v, EigH &e, const double *e_lab, int n_E, const int *n_E_s,
+                     PlanDev &plan)
 {
     const int nch = v.n_ch, maxN = v.maxN, S = e.n_samples;
+    const int P = n_E_s ? S : 1;
     wpcd_status st;
-    const size_t ni = (size_t)2 * nch * n_E + nch + (size_t)nch * maxN;
-    if ((st = ws_reserve(c, c->ws_plan_i, ni * sizeof(int)))) return st;
-    if ((st = ws_reserve(c, c->ws_plan_d, (size_t)n_E * sizeof(double)))) return st;
-    if ((st = ws_reserve(c, c->ws_tbin, (size_t)S * nch * maxN * 8 * sizeof(double)))) return st;
-    if ((st = ws_reserve(c, c->ws_phbin, (size_t)S * nch * maxN * 3 * sizeof(double)))) return st;
-    int *pi = static_cast<int *>(c->ws_plan_i.p);
+    const size_t ni = (size_t)P * (2 * (size_t)nch * n_E + nch + (size_t)nch * maxN);
+    if ((st = ws_reserve(c, X, X.ws_plan_i, ni * sizeof(int)))) return st;
+    if ((st = ws_reserve(c, X, X.ws_plan_d, (size_t)P * n_E * sizeof(double)))) return st;
+    if ((st = ws_reserve(c, X, X.ws_tbin, (size_t)S * nch * maxN * 8 * sizeof(double)))) return st;
+    if ((st = ws_reserve(c, X, X.ws_phbin, (size_t)S * nch * maxN * 3 * sizeof(double)))) return st;
+    int *pi = static_cast<int *>(X.ws_plan_i.p);
     plan.bin = pi;
-    plan.brk = pi + (size_t)nch * n_E;
-    plan.cnt = plan.brk + (size_t)nch * n_E;
-    plan.list = plan.cnt + nch;
-    plan.pE = static_cast<double *>(c->ws_plan_d.p);
+    plan.brk = pi + (size_t)P * nch * n_E;
+    plan.cnt = plan.brk + (size_t)P * nch * n_E;
+    plan.list = plan.cnt + (size_t)P * nch;
+    plan.pE = static_cast<double *>(X.ws_plan_d.p);
+    plan.per_sample = n_E_s ? 1 : 0;
+    plan.n_E_s = n_E_s;
     {
-        Launch L(c, WPCD_PHASE_PLAN);
-        CK(launch_plan(e.cd_dev, nch, maxN, e_lab, n_E, plan, c->err_dev, c->stream));
+        Launch L(c, X, WPCD_PHASE_PLAN);
+        CK(launch_plan(e.cd_dev, nch, maxN, e_lab, n_E, plan, X.err, X.stream, P));
     }
-    Launch L(c, WPCD_PHASE_TMATRIX);
-    CK(launch_tbin(e.cd_dev, nch, S, v.n_terms, v.n_terms > 1 ? e.coeffs : nullptr, e.eps, e.C, plan, maxN,
-                   static_cast<double *>(c->ws_tbin.p), static_cast<double *>(c->ws_phbin.p), c->err_dev, c->stream));
+    Launch L(c, X, WPCD_PHASE_TMATRIX);
+    const double *cf = v.n_terms > 1 ? e.coeffs : nullptr;
+    double *tb = static_cast<double *>(X.ws_tbin.p), *pb = static_cast<double *>(X.ws_phbin.p);
+    CK(launch_tbin(e.cd_dev, nch, S, v.n_terms, cf, e.eps, e.C, plan, maxN, tb, pb, X.err, X.stream));
+    return WPCD_OK;
+}
+
+// T at the energies and/or phases + cross sections, after run_tbin.
+wpcd_status run_outputs(wpcd_ctx *c, Exec &X, VSetH &v, EigH &e, int n_E, PlanDev &plan, double *t_out,
+                        double *delta, double *sigma)
+{
+    if (t_out) {
+        Launch L(c, X, WPCD_PHASE_GATHER);
+        CK(launch_gather_t(e.cd_dev, v.n_ch, e.n_samples, n_E, v.maxN, plan, static_cast<double *>(X.ws_tbin.p),
+                           t_out, X.stream));
+    }
+    if (delta || sigma) {
+        Launch L(c, X, WPCD_PHASE_OBSERVABLES);
+        CK(launch_observables(e.cd_dev, v.n_ch, e.n_samples, n_E, v.maxN, plan, static_cast<double *>(X.ws_phbin.p),
+                              delta, sigma, X.stream));
+    }
     return WPCD_OK;
 }
 
@@ -325,6 +489,9 @@ wpcd_status check_energies(const double *e_lab, int n_E)
 }
 
 }  // namespace
+
+void serve_shutdown(wpcd_ctx *c);
+bool serve_owns(wpcd_ctx *c, int id);
 
 // ============================================================================================ ABI
 extern "C" {
@@ -358,12 +525,13 @@ wpcd_status wpcd_create(wpcd_ctx **out, int device, size_t hbm_budget_bytes, voi
     auto *c = new (std::nothrow) wpcd_ctx();
     if (!c) return WPCD_ERR_NOMEM;
     c->device = device;
-    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->main.stream = static_cast<cudaStream_t>(cuda_stream);
     c->budget = hbm_budget_bytes;
-    if (dalloc(c, &c->err_dev, 1) != WPCD_OK || cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream) != cudaSuccess) {
+    if (dalloc(c, &c->err_dev, 1) != WPCD_OK || cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->main.stream) != cudaSuccess) {
         delete c;
         return WPCD_ERR_CUDA;
     }
+    c->main.err = c->err_dev;
     *out = c;
     return WPCD_OK;
 }
@@ -372,18 +540,20 @@ void wpcd_destroy(wpcd_ctx *c)
 {
     if (!c) return;
     cudaSetDevice(c->device);
-    cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->main.stream);
     for (auto &kv : c->handles) {
         if (kv.second.mesh) free_mesh(c, *kv.second.mesh);
         if (kv.second.vset) free_vset(c, *kv.second.vset);
         if (kv.second.eig) free_eig(c, *kv.second.eig);
     }
-    free_eig(c, c->scratch_eig);
+    serve_shutdown(c);
+    free_eig(c, c->main.eig);
     for (auto &kv : c->gl) {
         dfree(c, kv.second.first);
         dfree(c, kv.second.second);
     }
-    for (auto *b : {&c->ws_plan_i, &c->ws_plan_d, &c->ws_tbin, &c->ws_phbin, &c->ws_in, &c->ws_out}) dfree(c, b->p);
+    Exec &M = c->main;
+    for (auto *b : {&M.ws_plan_i, &M.ws_plan_d, &M.ws_tbin, &M.ws_phbin, &M.ws_in, &M.ws_out, &M.ws_ref}) dfree(c, b->p);
     if (c->pin_in) cudaFreeHost(c->pin_in);
     if (c->pin_out) cudaFreeHost(c->pin_out);
     dfree(c, c->err_dev);
@@ -397,6 +567,18 @@ wpcd_status wpcd_set_option(wpcd_ctx *c, int key, int value)
         c->exec_mode = value;
         return WPCD_OK;
     }
+    if (key == WPCD_OPT_REFINE && (value == WPCD_REFINE_TENSOR || value == WPCD_REFINE_FP64)) {
+        c->refine_engine = value;
+        return WPCD_OK;
+    }
+    if (key == WPCD_OPT_AUTOTUNE && (value == 0 || value == 1)) {
+        c->autotune = value;
+        if (!value) {
+            std::lock_guard<std::mutex> lk(c->tmu);
+            c->tuned.clear();
+        }
+        return WPCD_OK;
+    }
     return WPCD_ERR_ARG;
 }
 
@@ -406,9 +588,9 @@ wpcd_status wpcd_sync(wpcd_ctx *c)
     std::lock_guard<std::mutex> lk(c->mu);
     CK(cudaSetDevice(c->device));
     int h = 0;
-    CK(cudaMemcpyAsync(&h, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    if (h != 0) CK(cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream));
+    CK(cudaMemcpyAsync(&h, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->main.stream));
+    CK(cudaStreamSynchronize(c->main.stream));
+    if (h != 0) CK(cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->main.stream));
     switch (h) {
     case kDevOk: return WPCD_OK;
     case kDevEnergyOutside: return WPCD_ERR_ARG;
@@ -444,8 +626,8 @@ wpcd_status wpcd_mesh(wpcd_ctx *c, int n_wp, int kind, double alpha, double t, d
         free_mesh(c, *m);
         return st;
     }
-    Launch L(c, WPCD_PHASE_MESH);
-    CK(launch_mesh(n_wp, kind, alpha, t, kmax, n_quad, wp_kind, glx, glw, m->kb, m->kq, m->wq, m->h0, c->stream));
+    Launch L(c, c->main, WPCD_PHASE_MESH);
+    CK(launch_mesh(n_wp, kind, alpha, t, kmax, n_quad, wp_kind, glx, glw, m->kb, m->kq, m->wq, m->h0, c->main.stream));
     int id = c->next_id++;
     Handle h;
     h.kind = kMesh;
@@ -463,10 +645,10 @@ wpcd_status wpcd_mesh_get(wpcd_ctx *c, int mesh_id, double *kb, double *kq, doub
     if (!h) return WPCD_ERR_HANDLE;
     CK(cudaSetDevice(c->device));
     MeshH &m = *h->mesh;
-    if (kb) CK(cudaMemcpyAsync(kb, m.kb, sizeof(double) * (m.N + 1), cudaMemcpyDeviceToHost, c->stream));
-    if (kq) CK(cudaMemcpyAsync(kq, m.kq, sizeof(double) * m.N * m.Q, cudaMemcpyDeviceToHost, c->stream));
-    if (wq) CK(cudaMemcpyAsync(wq, m.wq, sizeof(double) * m.N * m.Q, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    if (kb) CK(cudaMemcpyAsync(kb, m.kb, sizeof(double) * (m.N + 1), cudaMemcpyDeviceToHost, c->main.stream));
+    if (kq) CK(cudaMemcpyAsync(kq, m.kq, sizeof(double) * m.N * m.Q, cudaMemcpyDeviceToHost, c->main.stream));
+    if (wq) CK(cudaMemcpyAsync(wq, m.wq, sizeof(double) * m.N * m.Q, cudaMemcpyDeviceToHost, c->main.stream));
+    CK(cudaStreamSynchronize(c->main.stream));
     return WPCD_OK;
 }
 
@@ -537,8 +719,8 @@ wpcd_status wpcd_project(wpcd_ctx *c, const int *mesh_ids, const wpcd_channel *c
         ident[k] = k;
         v->buckets[v->cd[k].n].push_back(k);
     }
-    CK(cudaMemcpyAsync(v->cd_dev, v->cd.data(), sizeof(ChanDev) * n_ch, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(v->ident_dev, ident.data(), sizeof(int) * n_ch, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(v->cd_dev, v->cd.data(), sizeof(ChanDev) * n_ch, cudaMemcpyHostToDevice, c->main.stream));
+    CK(cudaMemcpyAsync(v->ident_dev, ident.data(), sizeof(int) * n_ch, cudaMemcpyHostToDevice, c->main.stream));
     for (auto &kv : v->buckets) {
         int *p;
         if ((st = dalloc(c, &p, kv.second.size()))) {
@@ -546,14 +728,14 @@ wpcd_status wpcd_project(wpcd_ctx *c, const int *mesh_ids, const wpcd_channel *c
             return st;
         }
         v->bucket_dev[kv.first] = p;
-        CK(cudaMemcpyAsync(p, kv.second.data(), sizeof(int) * kv.second.size(), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(p, kv.second.data(), sizeof(int) * kv.second.size(), cudaMemcpyHostToDevice, c->main.stream));
     }
     if (gen == WPCD_GEN_FINE) {
         size_t off = 0;
         for (int k = 0; k < n_ch; ++k) {
             const ChanDev &d = v->cd[k];
-            Launch L(c, WPCD_PHASE_PROJECT);
-            CK(launch_project_fine(v->cd_dev, k, d, v_fine_dev + off, n_terms, c->stream));
+            Launch L(c, c->main, WPCD_PHASE_PROJECT);
+            CK(launch_project_fine(v->cd_dev, k, d, v_fine_dev + off, n_terms, c->main.stream));
             const size_t knq = (size_t)d.K * d.N * d.Q;
             off += (size_t)n_terms * knq * knq;
         }
@@ -564,7 +746,7 @@ wpcd_status wpcd_project(wpcd_ctx *c, const int *mesh_ids, const wpcd_channel *c
             free_vset(c, *v);
             return st;
         }
-        CK(cudaMemcpyAsync(gp_dev, gp_host, sizeof(double) * n_gp, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(gp_dev, gp_host, sizeof(double) * n_gp, cudaMemcpyHostToDevice, c->main.stream));
         double *angx = nullptr, *angw = nullptr;
         if (gen == WPCD_GEN_YUKAWA && (st = gl_rule(c, kAngleQ, &angx, &angw))) return st;
         // group the channels by mesh; one launch per mesh
@@ -576,16 +758,16 @@ wpcd_status wpcd_project(wpcd_ctx *c, const int *mesh_ids, const wpcd_channel *c
             if ((st = dalloc(c, &gd, kv.second.size()))) return st;
             gdevs.push_back(gd);
             CK(cudaMemcpyAsync(gd, kv.second.data(), sizeof(int) * kv.second.size(), cudaMemcpyHostToDevice,
-                               c->stream));
+                               c->main.stream));
             const ChanDev &d0 = v->cd[kv.second[0]];
-            Launch L(c, WPCD_PHASE_PROJECT);
+            Launch L(c, c->main, WPCD_PHASE_PROJECT);
             if (gen == WPCD_GEN_YUKAWA)
                 CK(launch_project_yukawa(v->cd_dev, gd, (int)kv.second.size(), d0.N, d0.Q, maxJ + 2, gp_dev, angx, angw,
-                                         n_terms, c->stream));
+                                         n_terms, c->main.stream));
             else
-                CK(launch_project_yamaguchi_gp(v->cd_dev, gd, (int)kv.second.size(), d0.N, d0.Q, gp_dev, c->stream));
+                CK(launch_project_yamaguchi_gp(v->cd_dev, gd, (int)kv.second.size(), d0.N, d0.Q, gp_dev, c->main.stream));
         }
-        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaStreamSynchronize(c->main.stream));
         for (int *gd : gdevs) dfree(c, gd);
         dfree(c, gp_dev);
     }
@@ -624,15 +806,15 @@ wpcd_status wpcd_vset_get(wpcd_ctx *c, int vset_id, int channel, double *out)
     if (channel < 0 || channel >= v.n_ch) return WPCD_ERR_ARG;
     CK(cudaSetDevice(c->device));
     const ChanDev &d = v.cd[channel];
-    CK(cudaMemcpyAsync(out, d.V, sizeof(double) * v.n_terms * d.n * d.n, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(out, d.V, sizeof(double) * v.n_terms * d.n * d.n, cudaMemcpyDeviceToHost, c->main.stream));
+    CK(cudaStreamSynchronize(c->main.stream));
     return WPCD_OK;
 }
 
 wpcd_status wpcd_diag(wpcd_ctx *c, int vset_id, const double *coeffs_dev, int n_samples, wpcd_precision prec,
                       int *eig_id)
 {
-    if (!c || !eig_id || n_samples < 1 || prec != WPCD_PREC_FP64) return WPCD_ERR_ARG;
+    if (!c || !eig_id || n_samples < 1 || (prec != WPCD_PREC_FP64 && prec != WPCD_PREC_MIXED)) return WPCD_ERR_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
     Handle *h = find(c, vset_id, kVSet);
     if (!h) return WPCD_ERR_HANDLE;
@@ -640,7 +822,7 @@ wpcd_status wpcd_diag(wpcd_ctx *c, int vset_id, const double *coeffs_dev, int n_
     if (v.n_terms > 1 && !coeffs_dev) return WPCD_ERR_ARG;
     CK(cudaSetDevice(c->device));
     auto e = std::make_unique<EigH>();
-    wpcd_status st = run_diag(c, v, vset_id, coeffs_dev, n_samples, *e);
+    wpcd_status st = run_diag(c, c->main, v, vset_id, coeffs_dev, n_samples, prec, *e);
     if (st) {
         free_eig(c, *e);
         return st;
@@ -665,7 +847,7 @@ wpcd_status wpcd_diag_status(wpcd_ctx *c, int eig_id, int *status_dev)
     if (!hv) return WPCD_ERR_HANDLE;
     CK(cudaSetDevice(c->device));
     CK(cudaMemcpyAsync(status_dev, e.status, sizeof(int) * e.n_samples * hv->vset->n_ch, cudaMemcpyDeviceToDevice,
-                       c->stream));
+                       c->main.stream));
     return WPCD_OK;
 }
 
@@ -689,27 +871,21 @@ wpcd_status wpcd_eig_get(wpcd_ctx *c, int eig_id, int sample, int channel, doubl
     const int n = v.cd[channel].n;
     if (eps_host)
         CK(cudaMemcpyAsync(eps_host, e.eps + eo + (size_t)sample * n, sizeof(double) * n, cudaMemcpyDeviceToHost,
-                           c->stream));
+                           c->main.stream));
     if (C_host)
         CK(cudaMemcpyAsync(C_host, e.C + co + (size_t)sample * n * n, sizeof(double) * n * n, cudaMemcpyDeviceToHost,
-                           c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+                           c->main.stream));
+    CK(cudaStreamSynchronize(c->main.stream));
     return WPCD_OK;
 }
 
 static wpcd_status tmatrix_impl(wpcd_ctx *c, VSetH &v, EigH &e, const double *e_lab, int n_E, double *t_out,
                                 double *delta, double *sigma)
 {
-    PlanDev plan;
-    wpcd_status st = run_tbin(c, v, e, e_lab, n_E, plan);
+    PlanDev plan{};
+    wpcd_status st = run_tbin(c, c->main, v, e, e_lab, n_E, nullptr, plan);
     if (st) return st;
-    if (t_out)
-        CK((Launch(c, WPCD_PHASE_GATHER), launch_gather_t(e.cd_dev, v.n_ch, e.n_samples, n_E, v.maxN, plan, static_cast<double *>(c->ws_tbin.p), t_out,
-                           c->stream)));
-    if (delta || sigma)
-        CK((Launch(c, WPCD_PHASE_OBSERVABLES), launch_observables(e.cd_dev, v.n_ch, e.n_samples, n_E, v.maxN, plan, static_cast<double *>(c->ws_phbin.p),
-                              delta, sigma, c->stream)));
-    return WPCD_OK;
+    return run_outputs(c, c->main, v, e, n_E, plan, t_out, delta, sigma);
 }
 
 wpcd_status wpcd_tmatrix(wpcd_ctx *c, int eig_id, const double *e_lab, int n_E, wpcd_resolvent res, double *t_out)
@@ -739,7 +915,8 @@ wpcd_status wpcd_observables(wpcd_ctx *c, int eig_id, const double *e_lab, int n
 wpcd_status wpcd_solve(wpcd_ctx *c, int vset_id, const double *coeffs, int S, const double *e_lab, int n_E,
                        wpcd_precision prec, wpcd_resolvent res, double *t_out, double *delta, double *sigma)
 {
-    if (!c || S < 1 || prec != WPCD_PREC_FP64 || res != WPCD_AVG_FREE_BIN || check_energies(e_lab, n_E))
+    if (!c || S < 1 || (prec != WPCD_PREC_FP64 && prec != WPCD_PREC_MIXED) || res != WPCD_AVG_FREE_BIN ||
+        check_energies(e_lab, n_E))
         return WPCD_ERR_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
     Handle *hv = find(c, vset_id, kVSet);
@@ -747,9 +924,9 @@ wpcd_status wpcd_solve(wpcd_ctx *c, int vset_id, const double *coeffs, int S, co
     VSetH &v = *hv->vset;
     if (v.n_terms > 1 && !coeffs) return WPCD_ERR_ARG;
     CK(cudaSetDevice(c->device));
-    wpcd_status st = run_diag(c, v, vset_id, coeffs, S, c->scratch_eig);
+    wpcd_status st = run_diag(c, c->main, v, vset_id, coeffs, S, prec, c->main.eig);
     if (st) return st;
-    return tmatrix_impl(c, v, c->scratch_eig, e_lab, n_E, t_out, delta, sigma);
+    return tmatrix_impl(c, v, c->main.eig, e_lab, n_E, t_out, delta, sigma);
 }
 
 wpcd_status wpcd_solve_host(wpcd_ctx *c, int vset_id, const double *coeffs_h, int S, const double *e_lab_h, int n_E,
@@ -769,7 +946,7 @@ wpcd_status wpcd_solve_host(wpcd_ctx *c, int vset_id, const double *coeffs_h, in
     {
         std::lock_guard<std::mutex> lk(c->mu);
         CK(cudaSetDevice(c->device));
-        if ((st = ws_reserve(c, c->ws_in, in_bytes)) || (st = ws_reserve(c, c->ws_out, out_bytes))) return st;
+        if ((st = ws_reserve(c, c->main, c->main.ws_in, in_bytes)) || (st = ws_reserve(c, c->main, c->main.ws_out, out_bytes))) return st;
         if (c->pin_in_n < in_bytes) {
             if (c->pin_in) cudaFreeHost(c->pin_in);
             CK(cudaMallocHost(&c->pin_in, in_bytes));
@@ -780,20 +957,20 @@ wpcd_status wpcd_solve_host(wpcd_ctx *c, int vset_id, const double *coeffs_h, in
             CK(cudaMallocHost(&c->pin_out, out_bytes));
             c->pin_out_n = out_bytes;
         }
-        din = static_cast<double *>(c->ws_in.p);
-        dout = static_cast<double *>(c->ws_out.p);
+        din = static_cast<double *>(c->main.ws_in.p);
+        dout = static_cast<double *>(c->main.ws_out.p);
         hin = static_cast<double *>(c->pin_in);
         hout = static_cast<double *>(c->pin_out);
         if (nc) memcpy(hin, coeffs_h, nc * sizeof(double));
         memcpy(hin + nc, e_lab_h, n_E * sizeof(double));
-        CK(cudaMemcpyAsync(din, hin, in_bytes, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(din, hin, in_bytes, cudaMemcpyHostToDevice, c->main.stream));
     }
     st = wpcd_solve(c, vset_id, nc ? din : nullptr, S, din + nc, n_E, prec, res, t_h ? dout : nullptr,
                     delta_h ? dout + nt : nullptr, sigma_h ? dout + nt + nd : nullptr);
     if (st) return st;
     {
         std::lock_guard<std::mutex> lk(c->mu);
-        if (out_bytes) CK(cudaMemcpyAsync(hout, dout, out_bytes, cudaMemcpyDeviceToHost, c->stream));
+        if (out_bytes) CK(cudaMemcpyAsync(hout, dout, out_bytes, cudaMemcpyDeviceToHost, c->main.stream));
     }
     st = wpcd_sync(c);
     if (t_h) memcpy(t_h, hout, nt * sizeof(double));
@@ -802,7 +979,39 @@ wpcd_status wpcd_solve_host(wpcd_ctx *c, int vset_id, const double *coeffs_h, in
     return st;
 }
 
-unsigned long long wpcd_kernel_launches(const wpcd_ctx *c) { return c ? c->launches : 0; }
+wpcd_status wpcd_batched_dgemm(wpcd_ctx *c, int n, int items, int trans_a, const double *A_dev, const double *B_dev,
+                                double *C_dev, int engine)
+{
+    if (!c || n < 1 || n > 2 * kMaxNwp || items < 1 || !A_dev || !B_dev || !C_dev ||
+        (engine != WPCD_REFINE_TENSOR && engine != WPCD_REFINE_FP64))
+        return WPCD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaSetDevice(c->device));
+    wpcd_status st = ws_reserve(c, c->main, c->main.ws_ref, batched_dgemm_scratch(n, items));
+    if (st) return st;
+    Launch L(c, c->main, WPCD_PHASE_REFINE);
+    CK(launch_batched_dgemm(n, items, trans_a != 0, A_dev, B_dev, C_dev, c->main.ws_ref.p, engine, c->main.stream));
+    return WPCD_OK;
+}
+
+int wpcd_tuning(wpcd_ctx *c, int max_entries, int *n_out, int *prec_out, int *threads_out, float *ms_out)
+{
+    if (!c) return 0;
+    std::lock_guard<std::mutex> lk(c->tmu);
+    int k = 0;
+    for (auto &kv : c->tuned) {
+        if (k >= max_entries) break;
+        if (n_out) n_out[k] = kv.first.first;
+        if (prec_out) prec_out[k] = kv.first.second;
+        if (threads_out) threads_out[k] = kv.second.threads;
+        if (ms_out)
+            for (int j = 0; j < 4; ++j) ms_out[4 * k + j] = kv.second.ms[j];
+        ++k;
+    }
+    return k;
+}
+
+unsigned long long wpcd_kernel_launches(const wpcd_ctx *c) { return c ? c->launches.load() : 0ULL; }
 
 wpcd_status wpcd_profile(wpcd_ctx *c, int enable)
 {
@@ -832,15 +1041,431 @@ wpcd_status wpcd_profile_read(wpcd_ctx *c, int phase, double *ms_total, long *la
 wpcd_status wpcd_release(wpcd_ctx *c, int id)
 {
     if (!c) return WPCD_ERR_ARG;
+    if (serve_owns(c, id)) return WPCD_ERR_ARG;  // meshes and sets of a running server stay
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->handles.find(id);
     if (it == c->handles.end()) return WPCD_ERR_HANDLE;
     cudaSetDevice(c->device);
-    cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->main.stream);
     if (it->second.mesh) free_mesh(c, *it->second.mesh);
     if (it->second.vset) free_vset(c, *it->second.vset);
     if (it->second.eig) free_eig(c, *it->second.eig);
     c->handles.erase(it);
+    return WPCD_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================================ serving
+//
+// Continuous batching.  Requests (one parameter sample, its own energy list,
+// an N_WP among the served ones) enter a FIFO queue.  A worker thread owns
+// n_slots executors, each with its own CUDA stream and workspaces.  Whenever a
+// slot is free and requests wait, the worker takes the oldest request and
+// every other queued request with the same (N_WP, precision), up to
+// max_batch, and queues one batch on that slot's stream: inputs H2D, the
+// eigensolve of every (sample, channel), per-sample energy plans, T, phases and
+// cross sections, outputs D2H, and a host callback that marks the slot done.
+// Batches on different slots overlap on the device; new requests join the next
+// free slot while others run.  Results belong to the context until
+// wpcd_release_result.
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+    uint64_t ticket = 0;
+    int model = 0, prec = 0, n_E = 0;
+    std::vector<double> coeffs, e_lab;
+    Clock::time_point t_submit;
+    int state = 0;  // 0 queued, 1 running, 2 done
+    wpcd_status status = WPCD_OK;
+    std::vector<double> T, delta, sigma;
+    double latency_us = 0.0;
+    size_t bytes = 0;
+};
+
+struct Slot {
+    Exec X;
+    std::vector<std::shared_ptr<Req>> reqs;
+    std::atomic<int> done{0};
+    bool busy = false;
+    double *pin_in = nullptr, *pin_out = nullptr;
+    size_t pin_in_n = 0, pin_out_n = 0;
+    int S = 0, nE = 0;
+    size_t nt = 0, nd = 0, ns = 0;
+};
+
+struct ModelS {
+    int n_wp = 0, vset_id = -1;
+    std::vector<int> mesh_ids;
+    VSetH *v = nullptr;
+};
+
+}  // namespace
+
+struct Server {
+    wpcd_ctx *c = nullptr;
+    std::vector<ModelS> models;
+    int n_ch = 0, n_terms = 0, max_batch = 64;
+    size_t max_queue = 1 << 16;
+    std::vector<std::unique_ptr<Slot>> slots;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<std::shared_ptr<Req>> queue;
+    std::unordered_map<uint64_t, std::shared_ptr<Req>> table;
+    uint64_t next_ticket = 1;
+    size_t queued_bytes = 0;
+    std::thread worker;
+    bool stop = false;
+    uint64_t completed = 0, batches = 0, batched_requests = 0;
+};
+
+namespace {
+
+void CUDART_CB slot_done_cb(void *arg)
+{
+    Slot *sl = static_cast<Slot *>(arg);
+    sl->done.store(1);
+}
+
+size_t request_bytes(const ModelS &m, int prec)
+{
+    size_t b = 0;
+    for (const ChanDev &d : m.v->cd) b += (size_t)d.n * d.n * 8 * (prec == WPCD_PREC_MIXED ? 6 : 1) + (size_t)d.n * 8;
+    return b + (size_t)m.v->n_ch * m.v->maxN * 11 * 8;
+}
+
+// Queue one batch on a slot.  Returns a status for every request of the batch.
+wpcd_status launch_batch(Server *sv, Slot &sl)
+{
+    wpcd_ctx *c = sv->c;
+    Exec &X = sl.X;
+    const Req &r0 = *sl.reqs[0];
+    ModelS &m = sv->models[r0.model];
+    VSetH &v = *m.v;
+    const int S = (int)sl.reqs.size(), nt1 = std::max(v.n_terms - 1, 1);
+    int nE = 0;
+    for (auto &r : sl.reqs) nE = std::max(nE, r->n_E);
+    sl.S = S;
+    sl.nE = nE;
+    const size_t in_d = (size_t)S * nt1 + (size_t)S * nE;
+    const size_t in_bytes = in_d * 8 + (size_t)S * 4;
+    sl.nt = (size_t)S * v.n_ch * nE * 8;
+    sl.nd = (size_t)S * v.n_ch * nE * 3;
+    sl.ns = (size_t)S * nE;
+    const size_t out_bytes = (sl.nt + sl.nd + sl.ns) * 8 + 8;
+    wpcd_status st;
+    if ((st = ws_reserve(c, X, X.ws_in, in_bytes)) || (st = ws_reserve(c, X, X.ws_out, out_bytes))) return st;
+    if (sl.pin_in_n < in_bytes) {
+        if (sl.pin_in) cudaFreeHost(sl.pin_in);
+        sl.pin_in = nullptr;
+        CK(cudaMallocHost(&sl.pin_in, in_bytes));
+        sl.pin_in_n = in_bytes;
+    }
+    if (sl.pin_out_n < out_bytes) {
+        if (sl.pin_out) cudaFreeHost(sl.pin_out);
+        sl.pin_out = nullptr;
+        CK(cudaMallocHost(&sl.pin_out, out_bytes));
+        sl.pin_out_n = out_bytes;
+    }
+    double *hc = sl.pin_in, *he = hc + (size_t)S * nt1;
+    int *hn = reinterpret_cast<int *>(he + (size_t)S * nE);
+    for (int k = 0; k < S; ++k) {
+        const Req &r = *sl.reqs[k];
+        for (int a = 0; a < nt1; ++a) hc[(size_t)k * nt1 + a] = (a < (int)r.coeffs.size()) ? r.coeffs[a] : 0.0;
+        for (int e = 0; e < nE; ++e) he[(size_t)k * nE + e] = r.e_lab[std::min(e, r.n_E - 1)];
+        hn[k] = r.n_E;
+    }
+    double *dc = static_cast<double *>(X.ws_in.p), *de = dc + (size_t)S * nt1;
+    int *dn = reinterpret_cast<int *>(de + (size_t)S * nE);
+    double *dout = static_cast<double *>(X.ws_out.p);
+    CK(cudaMemcpyAsync(dc, hc, in_bytes, cudaMemcpyHostToDevice, X.stream));
+    if ((st = run_diag(c, X, v, m.vset_id, v.n_terms > 1 ? dc : nullptr, S, r0.prec, X.eig))) return st;
+    PlanDev plan{};
+    if ((st = run_tbin(c, X, v, X.eig, de, nE, dn, plan))) return st;
+    if ((st = run_outputs(c, X, v, X.eig, nE, plan, dout, dout + sl.nt, dout + sl.nt + sl.nd))) return st;
+    CK(cudaMemcpyAsync(dout + sl.nt + sl.nd + sl.ns, X.err, sizeof(int), cudaMemcpyDeviceToDevice, X.stream));
+    CK(cudaMemsetAsync(X.err, 0, sizeof(int), X.stream));
+    CK(cudaMemcpyAsync(sl.pin_out, dout, out_bytes, cudaMemcpyDeviceToHost, X.stream));
+    sl.done.store(0);
+    CK(cudaLaunchHostFunc(X.stream, slot_done_cb, &sl));
+    return WPCD_OK;
+}
+
+void finish_batch(Server *sv, Slot &sl)
+{
+    const int S = sl.S, nE = sl.nE;
+    const ModelS &m = sv->models[sl.reqs[0]->model];
+    const int nch = m.v->n_ch;
+    const double *T = sl.pin_out, *D = T + sl.nt, *G = D + sl.nd;
+    int derr = *reinterpret_cast<const int *>(G + sl.ns);
+    const auto now = Clock::now();
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (int k = 0; k < S; ++k) {
+        Req &r = *sl.reqs[k];
+        r.T.resize((size_t)nch * r.n_E * 8);
+        r.delta.resize((size_t)nch * r.n_E * 3);
+        r.sigma.resize(r.n_E);
+        for (int ch = 0; ch < nch; ++ch) {
+            memcpy(&r.T[(size_t)ch * r.n_E * 8], T + (((size_t)k * nch + ch) * nE) * 8, sizeof(double) * 8 * r.n_E);
+            memcpy(&r.delta[(size_t)ch * r.n_E * 3], D + (((size_t)k * nch + ch) * nE) * 3,
+                   sizeof(double) * 3 * r.n_E);
+        }
+        memcpy(r.sigma.data(), G + (size_t)k * nE, sizeof(double) * r.n_E);
+        r.status = derr == 0 ? WPCD_OK : (derr == kDevNoConverge ? WPCD_ERR_NOCONVERGE : WPCD_ERR_ARG);
+        r.latency_us = std::chrono::duration<double, std::micro>(now - r.t_submit).count();
+        r.state = 2;
+        sv->queued_bytes -= r.bytes;
+    }
+    sv->completed += S;
+    sl.reqs.clear();
+    sl.busy = false;
+    sv->cv.notify_all();
+}
+
+void fail_batch(Server *sv, Slot &sl, wpcd_status st)
+{
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (auto &r : sl.reqs) {
+        r->status = st;
+        r->state = 2;
+        sv->queued_bytes -= r->bytes;
+    }
+    sl.reqs.clear();
+    sl.busy = false;
+    sv->cv.notify_all();
+}
+
+void serve_loop(Server *sv)
+{
+    cudaSetDevice(sv->c->device);
+    for (;;) {
+        bool any_busy = false;
+        for (auto &slp : sv->slots) {
+            Slot &sl = *slp;
+            if (sl.busy && sl.done.load()) finish_batch(sv, sl);
+            any_busy |= sl.busy;
+        }
+        for (auto &slp : sv->slots) {
+            Slot &sl = *slp;
+            if (sl.busy) continue;
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                if (sv->queue.empty()) break;
+                const int model = sv->queue.front()->model, prec = sv->queue.front()->prec;
+                for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)sl.reqs.size() < sv->max_batch;) {
+                    if ((*it)->model == model && (*it)->prec == prec) {
+                        (*it)->state = 1;
+                        sl.reqs.push_back(*it);
+                        it = sv->queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+                sv->batches += 1;
+                sv->batched_requests += sl.reqs.size();
+            }
+            sl.busy = true;
+            any_busy = true;
+            wpcd_status st = launch_batch(sv, sl);
+            if (st) {
+                cudaStreamSynchronize(sl.X.stream);
+                fail_batch(sv, sl, st);
+            }
+        }
+        std::unique_lock<std::mutex> lk(sv->mu);
+        if (sv->stop && sv->queue.empty() && !any_busy) break;
+        if (sv->queue.empty() || !any_busy)
+            sv->cv.wait_for(lk, std::chrono::microseconds(any_busy ? 20 : 2000));
+    }
+}
+
+}  // namespace
+
+bool serve_owns(wpcd_ctx *c, int id)
+{
+    if (!c || !c->server) return false;
+    for (auto &m : c->server->models) {
+        if (m.vset_id == id) return true;
+        for (int mid : m.mesh_ids)
+            if (mid == id) return true;
+    }
+    return false;
+}
+
+void serve_shutdown(wpcd_ctx *c)
+{
+    Server *sv = c->server;
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    for (auto &slp : sv->slots) {
+        Slot &sl = *slp;
+        cudaStreamSynchronize(sl.X.stream);
+        free_eig(c, sl.X.eig);
+        for (auto *b : {&sl.X.ws_plan_i, &sl.X.ws_plan_d, &sl.X.ws_tbin, &sl.X.ws_phbin, &sl.X.ws_ref, &sl.X.ws_in,
+                        &sl.X.ws_out})
+            dfree(c, b->p);
+        dfree(c, sl.X.err);
+        if (sl.pin_in) cudaFreeHost(sl.pin_in);
+        if (sl.pin_out) cudaFreeHost(sl.pin_out);
+        cudaStreamDestroy(sl.X.stream);
+    }
+    c->server = nullptr;
+    delete sv;
+}
+
+extern "C" {
+
+wpcd_status wpcd_serve_start(wpcd_ctx *c, const wpcd_channel *channels, int n_ch, int generator_id,
+                             const double *gen_params_host, int n_gen_params, int n_terms, const int *n_wp_list,
+                             int n_nwp, int max_batch, int n_slots, int max_queue)
+{
+    if (!c || !channels || n_ch < 1 || !n_wp_list || n_nwp < 1 || max_batch < 1 || n_slots < 1 || n_slots > 16 ||
+        max_queue < 1 || generator_id == WPCD_GEN_FINE)
+        return WPCD_ERR_ARG;
+    if (c->server) return WPCD_ERR_ARG;
+    auto sv = std::make_unique<Server>();
+    sv->c = c;
+    sv->n_ch = n_ch;
+    sv->n_terms = n_terms;
+    sv->max_batch = max_batch;
+    sv->max_queue = (size_t)max_queue;
+    wpcd_status st;
+    for (int k = 0; k < n_nwp; ++k) {
+        ModelS m;
+        m.n_wp = n_wp_list[k];
+        int mid = -1;
+        if ((st = wpcd_mesh(c, m.n_wp, 0, 100.0 / kHbarc, 2.0, 8.0, 8, 0, &mid))) return st;
+        m.mesh_ids.assign(n_ch, mid);
+        if ((st = wpcd_project(c, m.mesh_ids.data(), channels, n_ch, generator_id, gen_params_host, n_gen_params,
+                               nullptr, n_terms, &m.vset_id)))
+            return st;
+        {
+            std::lock_guard<std::mutex> lk(c->mu);
+            m.v = find(c, m.vset_id, kVSet)->vset.get();
+        }
+        sv->models.push_back(m);
+    }
+    CK(cudaSetDevice(c->device));
+    for (int k = 0; k < n_slots; ++k) {
+        auto sl = std::make_unique<Slot>();
+        CK(cudaStreamCreateWithFlags(&sl->X.stream, cudaStreamNonBlocking));
+        if ((st = dalloc(c, &sl->X.err, 1))) return st;
+        CK(cudaMemsetAsync(sl->X.err, 0, sizeof(int), sl->X.stream));
+        sv->slots.push_back(std::move(sl));
+    }
+    CK(cudaStreamSynchronize(c->main.stream));
+    Server *raw = sv.release();
+    c->server = raw;
+    raw->worker = std::thread(serve_loop, raw);
+    return WPCD_OK;
+}
+
+wpcd_status wpcd_serve_stop(wpcd_ctx *c)
+{
+    if (!c || !c->server) return WPCD_ERR_ARG;
+    serve_shutdown(c);
+    return WPCD_OK;
+}
+
+wpcd_status wpcd_submit(wpcd_ctx *c, const wpcd_request *rq, uint64_t *ticket)
+{
+    if (!c || !c->server || !rq || !ticket || !rq->e_lab || rq->n_E < 1) return WPCD_ERR_ARG;
+    Server *sv = c->server;
+    if (rq->prec != WPCD_PREC_FP64 && rq->prec != WPCD_PREC_MIXED) return WPCD_ERR_ARG;
+    if (sv->n_terms > 1 && (!rq->coeffs || rq->n_terms != sv->n_terms - 1)) return WPCD_ERR_ARG;
+    int model = -1;
+    for (size_t k = 0; k < sv->models.size(); ++k)
+        if (sv->models[k].n_wp == rq->n_wp) model = (int)k;
+    if (model < 0) return WPCD_ERR_ARG;
+    // the eigensolver of the requested precision must hold the largest matrix of the model
+    const int maxn = sv->models[model].v->maxn;
+    if (rq->prec == WPCD_PREC_FP64 ? jacobi_smem_bytes(maxn, false) > 227 * 1024
+                                   : jacobi_mixed_smem_bytes(maxn, false) > 227 * 1024)
+        return WPCD_ERR_ARG;
+    for (int e = 0; e < rq->n_E; ++e)
+        if (!(rq->e_lab[e] > 0.0)) return WPCD_ERR_ARG;
+    auto r = std::make_shared<Req>();
+    r->model = model;
+    r->prec = rq->prec;
+    r->n_E = rq->n_E;
+    if (sv->n_terms > 1) r->coeffs.assign(rq->coeffs, rq->coeffs + rq->n_terms);
+    r->e_lab.assign(rq->e_lab, rq->e_lab + rq->n_E);
+    r->bytes = request_bytes(sv->models[model], rq->prec);
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stop) return WPCD_ERR_ARG;
+    const size_t cap = c->budget ? (c->budget > c->in_use ? c->budget - c->in_use : 0) : (size_t)-1;
+    if (sv->queue.size() >= sv->max_queue || (c->budget && sv->queued_bytes + r->bytes > cap))
+        return WPCD_ERR_BUDGET;
+    r->ticket = sv->next_ticket++;
+    r->t_submit = Clock::now();
+    sv->queued_bytes += r->bytes;
+    sv->queue.push_back(r);
+    sv->table[r->ticket] = r;
+    *ticket = r->ticket;
+    sv->cv.notify_all();
+    return WPCD_OK;
+}
+
+static void fill_result(const Req &r, int n_ch, wpcd_result *out)
+{
+    out->status = r.status;
+    out->n_E = r.n_E;
+    out->n_ch = n_ch;
+    out->delta = r.delta.data();
+    out->sigma = r.sigma.data();
+    out->T = r.T.data();
+    out->latency_us = r.latency_us;
+}
+
+wpcd_status wpcd_poll(wpcd_ctx *c, uint64_t ticket, wpcd_result *out)
+{
+    if (!c || !c->server || !out) return WPCD_ERR_ARG;
+    Server *sv = c->server;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->table.find(ticket);
+    if (it == sv->table.end()) return WPCD_ERR_HANDLE;
+    if (it->second->state != 2) return WPCD_ERR_NOTREADY;
+    fill_result(*it->second, sv->n_ch, out);
+    return WPCD_OK;
+}
+
+wpcd_status wpcd_wait(wpcd_ctx *c, uint64_t ticket, int timeout_ms, wpcd_result *out)
+{
+    if (!c || !c->server || !out) return WPCD_ERR_ARG;
+    Server *sv = c->server;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->table.find(ticket);
+    if (it == sv->table.end()) return WPCD_ERR_HANDLE;
+    std::shared_ptr<Req> r = it->second;
+    if (!sv->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->state == 2; }))
+        return WPCD_ERR_TIMEOUT;
+    fill_result(*r, sv->n_ch, out);
+    return WPCD_OK;
+}
+
+void wpcd_release_result(wpcd_ctx *c, uint64_t ticket)
+{
+    if (!c || !c->server) return;
+    std::lock_guard<std::mutex> lk(c->server->mu);
+    auto it = c->server->table.find(ticket);
+    if (it != c->server->table.end() && it->second->state == 2) c->server->table.erase(it);
+}
+
+wpcd_status wpcd_serve_stats(wpcd_ctx *c, unsigned long long *completed, unsigned long long *batches,
+                             unsigned long long *queued)
+{
+    if (!c || !c->server) return WPCD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->server->mu);
+    if (completed) *completed = c->server->completed;
+    if (batches) *batches = c->server->batches;
+    if (queued) *queued = c->server->queue.size();
     return WPCD_OK;
 }
 

@@ -18,16 +18,18 @@ constexpr int kTThreads = 256;
 // ---------------------------------------------------------------------------------------------
 __global__ void k_plan(const ChanDev *chans, int n_ch, int maxN, const double *e_lab, int n_E, PlanDev plan, int *err)
 {
-    const int c = blockIdx.x;
+    const int c = blockIdx.x, ps = blockIdx.y;
     const ChanDev ch = chans[c];
     const int N = ch.N;
+    const int nE = plan_nE(plan, ps, n_E);
+    const size_t pc = (size_t)ps * n_ch + c;
     __shared__ int mark[kMaxNwp];
     for (int i = threadIdx.x; i < N; i += blockDim.x) mark[i] = 0;
     __syncthreads();
-    for (int e = threadIdx.x; e < n_E; e += blockDim.x) {
-        const double T = e_lab[e];
+    for (int e = threadIdx.x; e < nE; e += blockDim.x) {
+        const double T = e_lab[(size_t)ps * n_E + e];
         const double p = sqrt(kMn * T / 2.0) / kHbarc;
-        if (c == 0) plan.pE[e] = p;
+        if (c == 0) plan.pE[(size_t)ps * n_E + e] = p;
         int bin = 0, j = 0;
         if (!(T > 0.0) || !(p < ch.kb[N])) {
             record_error(err, kDevEnergyOutside);
@@ -48,8 +50,8 @@ __global__ void k_plan(const ChanDev *chans, int n_ch, int maxN, const double *e
             }
             j = lo < 0 ? 0 : (lo > N - 2 ? N - 2 : lo);
         }
-        plan.bin[(size_t)c * n_E + e] = bin;
-        plan.brk[(size_t)c * n_E + e] = j;
+        plan.bin[pc * n_E + e] = bin;
+        plan.brk[pc * n_E + e] = j;
         atomicExch(&mark[bin], 1);
         atomicExch(&mark[j], 1);
         atomicExch(&mark[j + 1], 1);
@@ -58,15 +60,15 @@ __global__ void k_plan(const ChanDev *chans, int n_ch, int maxN, const double *e
     if (threadIdx.x == 0) {
         int cnt = 0;
         for (int i = 0; i < N; ++i)
-            if (mark[i]) plan.list[(size_t)c * maxN + cnt++] = i;
-        plan.cnt[c] = cnt;
+            if (mark[i]) plan.list[pc * maxN + cnt++] = i;
+        plan.cnt[pc] = cnt;
     }
 }
 
 cudaError_t launch_plan(const ChanDev *chans_dev, int n_ch, int maxN, const double *e_lab, int n_E, PlanDev plan,
-                        int *err, cudaStream_t st)
+                        int *err, cudaStream_t st, int n_plans)
 {
-    k_plan<<<n_ch, 256, 0, st>>>(chans_dev, n_ch, maxN, e_lab, n_E, plan, err);
+    k_plan<<<dim3(n_ch, n_plans), 256, 0, st>>>(chans_dev, n_ch, maxN, e_lab, n_E, plan, err);
     return cudaGetLastError();
 }
 
@@ -110,8 +112,11 @@ __device__ __forceinline__ void block_sum_vec(double *v, double *red /* [NV][32]
 //    mu q T; phases (Stapp for coupled channels).
 // tbin: [S][n_ch][maxN][K][K] complex (8 doubles per bin); phbin: [S][n_ch][maxN][3].
 // ---------------------------------------------------------------------------------------------
+// TC: eigenvector type (double on the FP64 path; float on the mixed path, where
+// the VC rows are accumulated in FP32 and everything after them stays FP64).
+template <typename TC>
 __global__ void __launch_bounds__(kTThreads) k_tbin(const ChanDev *chans, int n_ch, int n_terms, const double *coeffs,
-                                                    const double *eps_all, const double *C_all, PlanDev plan, int maxN,
+                                                    const double *eps_all, const TC *C_all, PlanDev plan, int maxN,
                                                     double *tbin, double *phbin, int *err)
 {
     const int c = blockIdx.x % n_ch, smp = blockIdx.x / n_ch;
@@ -134,7 +139,8 @@ __global__ void __launch_bounds__(kTThreads) k_tbin(const ChanDev *chans, int n_
     __shared__ int s_nb, s_bad;
 
     const double *eg = eps_all + ch.eps_off + (size_t)smp * n;
-    const double *C = C_all + ch.c_off + (size_t)smp * n * n;
+    const TC *C = C_all + ch.c_off + (size_t)smp * n * n;
+    TC *vrowc = reinterpret_cast<TC *>(red + 6 * 32);  // K x n copy of the V rows in the accumulation type
     const double *cf = coeffs ? coeffs + (size_t)smp * (n_terms - 1) : nullptr;
 
     if (tid == 0) { s_nb = 0; s_bad = 0; }
@@ -185,10 +191,11 @@ __global__ void __launch_bounds__(kTThreads) k_tbin(const ChanDev *chans, int n_
     }
     __syncthreads();
 
-    const int cnt = plan.cnt[c];
+    const size_t pc = (size_t)plan_of(plan, smp) * n_ch + c;
+    const int cnt = plan.cnt[pc];
     const size_t obase = ((size_t)smp * n_ch + c) * maxN;
     for (int ii = 0; ii < cnt; ++ii) {
-        const int i = plan.list[(size_t)c * maxN + ii];
+        const int i = plan.list[pc * maxN + ii];
         // rows (a, i) of V = V0 + sum_a c_a V_a
         for (int e = tid; e < K * n; e += nt) {
             const int a = e / n, jj = e - a * n;
@@ -196,15 +203,16 @@ __global__ void __launch_bounds__(kTThreads) k_tbin(const ChanDev *chans, int n_
             double v = ch.V[off];
             for (int t = 1; t < n_terms; ++t) v = fma(cf[t - 1], ch.V[(size_t)t * n * n + off], v);
             vrow[a * n + jj] = v;
+            vrowc[a * n + jj] = (TC)v;
         }
         __syncthreads();
         // R = V_rows C
         for (int e = tid; e < K * n; e += nt) {
             const int a = e / n, s = e - a * n;
-            const double *vr = vrow + a * n;
-            double acc = 0.0;
+            const TC *vr = vrowc + a * n;
+            TC acc = 0;
             for (int j = 0; j < n; ++j) acc = fma(vr[j], C[(size_t)j * n + s], acc);
-            R[a * n + s] = acc;
+            R[a * n + s] = (double)acc;
         }
         __syncthreads();
         const double Ea = ch.kb[i] * ch.kb[i] / (2.0 * kMu), Ebn = ch.kb[i + 1] * ch.kb[i + 1] / (2.0 * kMu);
@@ -287,9 +295,9 @@ cudaError_t launch_tbin(const ChanDev *chans_dev, int n_ch, int n_samples, int n
                         double *phbin, int *err, cudaStream_t st)
 {
     const size_t smem = tbin_smem_bytes(2 * maxN);
-    cudaFuncSetAttribute(k_tbin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_tbin<<<(unsigned)(n_samples * n_ch), kTThreads, smem, st>>>(chans_dev, n_ch, n_terms, coeffs, eps_all, C_all,
-                                                                   plan, maxN, tbin, phbin, err);
+    cudaFuncSetAttribute(k_tbin<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_tbin<double><<<(unsigned)(n_samples * n_ch), kTThreads, smem, st>>>(chans_dev, n_ch, n_terms, coeffs, eps_all,
+                                                                           C_all, plan, maxN, tbin, phbin, err);
     return cudaGetLastError();
 }
 
@@ -305,7 +313,9 @@ __global__ void k_gather_t(int n_ch, int n_samples, int n_E, int maxN, PlanDev p
     const int e = (int)(idx % n_E);
     const size_t sc = idx / n_E;
     const int c = (int)(sc % n_ch);
-    const int bin = plan.bin[(size_t)c * n_E + e];
+    const int ps = plan_of(plan, (int)(sc / n_ch));
+    if (e >= plan_nE(plan, ps, n_E)) return;
+    const int bin = plan.bin[((size_t)ps * n_ch + c) * n_E + e];
     const double *src = tbin + (sc * maxN + bin) * 8;
     double *dst = t_out + idx * 8;
     const double2 *s2 = reinterpret_cast<const double2 *>(src);
@@ -346,12 +356,14 @@ __global__ void k_observables(const ChanDev *chans, int n_ch, int n_samples, int
     if (idx >= (size_t)n_samples * n_E) return;
     const int e = (int)(idx % n_E);
     const int smp = (int)(idx / n_E);
-    const double p = plan.pE[e];
+    const int ps = plan_of(plan, smp);
+    if (e >= plan_nE(plan, ps, n_E)) return;
+    const double p = plan.pE[(size_t)ps * n_E + e];
     const double rad = kPi / 180.0;
     double acc = 0.0;
     for (int c = 0; c < n_ch; ++c) {
         const ChanDev ch = chans[c];
-        const int j = plan.brk[(size_t)c * n_E + e];
+        const int j = plan.brk[((size_t)ps * n_ch + c) * n_E + e];
         const double q0 = 0.5 * (ch.kb[j] + ch.kb[j + 1]), q1 = 0.5 * (ch.kb[j + 1] + ch.kb[j + 2]);
         const double w = (p - q0) / (q1 - q0);
         const double *ph = phbin + (((size_t)smp * n_ch + c) * maxN) * 3;

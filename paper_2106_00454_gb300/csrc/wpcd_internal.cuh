@@ -2,6 +2,7 @@
 // CUDA translation units of libwpcd (sm_103a).  Not part of the C ABI.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -45,14 +46,21 @@ struct ChanDev {
     long long c_off;    // offset of this channel's eigenvector block [S][n][n]
 };
 
-// Energy plan of one channel for one energy list.
+// Energy plan: for each plan p (one shared by all samples, or one per sample
+// when every sample carries its own energy list) and channel c.  n_E below is
+// the stride of an energy list (its largest length).
 struct PlanDev {
-    int *bin;      // [n_ch][n_E] free bin holding p(E)
-    int *brk;      // [n_ch][n_E] lower index j of the midpoint segment used to interpolate
-    int *cnt;      // [n_ch] number of distinct bins whose T is needed
-    int *list;     // [n_ch][maxN] those bins, ascending
-    double *pE;    // [n_E] c.m. momentum of each energy
+    int *bin;           // [P][n_ch][n_E] free bin holding p(E)
+    int *brk;           // [P][n_ch][n_E] lower index j of the midpoint segment used to interpolate
+    int *cnt;           // [P][n_ch] number of distinct bins whose T is needed
+    int *list;          // [P][n_ch][maxN] those bins, ascending
+    double *pE;         // [P][n_E] c.m. momentum of each energy
+    int per_sample;     // 0: P = 1, the plan of every sample; 1: P = n_samples
+    const int *n_E_s;   // per-sample list lengths (per_sample only; NULL = all n_E)
 };
+
+__device__ __forceinline__ int plan_of(const PlanDev &pl, int smp) { return pl.per_sample ? smp : 0; }
+__device__ __forceinline__ int plan_nE(const PlanDev &pl, int ps, int n_E) { return pl.n_E_s ? pl.n_E_s[ps] : n_E; }
 
 // Bytes of dynamic shared memory this launch was given.
 __device__ __forceinline__ unsigned dyn_smem_bytes()
@@ -65,8 +73,9 @@ __device__ __forceinline__ unsigned dyn_smem_bytes()
 // Shared-memory layouts (doubles) of the kernels, used by kernel and launcher alike.
 __host__ __device__ inline size_t tbin_smem_doubles(int n)  // n = K * N of the channel
 {
-    // eps n, branch members 2n, branch boundaries 2(n+1), lo/hi 2n, V rows 2n, R 2n, reduction 6 x 32
-    return (size_t)11 * n + 2 + 6 * 32;
+    // eps n, branch members 2n, branch boundaries 2(n+1), lo/hi 2n, V rows 2n, R 2n, reduction 6 x 32,
+    // V rows again in the accumulation type (at most 2n doubles)
+    return (size_t)13 * n + 2 + 6 * 32;
 }
 
 __device__ __forceinline__ void record_error(int *err, int code)
@@ -78,6 +87,36 @@ __device__ __forceinline__ void record_error(int *err, int code)
 __device__ __forceinline__ int pk(int i, int j)
 {
     return (i <= j) ? (j * (j + 1) / 2 + i) : (i * (i + 1) / 2 + j);
+}
+
+// Round-robin tournament (npad even): pair k of round r.  Every unordered pair
+// of 0..npad-1 occurs in exactly one of the npad-1 rounds; each round is a
+// perfect matching, so its rotations commute.
+__device__ __forceinline__ void jac_pair_of(int r, int k, int npad, int &p, int &q)
+{
+    const int M = npad - 1;
+    int a, b;
+    if (k == 0) {
+        a = 0;
+        b = 1 + (r % M);
+    } else {
+        a = 1 + (r + k) % M;
+        b = 1 + (r - k + M) % M;
+    }
+    p = a < b ? a : b;
+    q = a < b ? b : a;
+}
+
+// Sum of one double over the CTA (blockDim a multiple of 32, <= 2048); every thread gets it.
+__device__ __forceinline__ double cta_sum64(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    return t;
 }
 
 }  // namespace wpcd
@@ -100,9 +139,27 @@ size_t jacobi_smem_bytes(int n, bool c_in_smem);
 bool jacobi_c_in_smem(int n);
 cudaError_t launch_jacobi_f64(const ChanDev *chans_dev, const int *work_ch_dev, int n_work_ch, int n_samples,
                               int sample0, int n_terms, const double *coeffs, int n, double *eps_all,
-                              double *C_all, int *status_all, int n_ch_total, int *err, cudaStream_t st);
+                              double *C_all, int *status_all, int n_ch_total, int *err, cudaStream_t st,
+                              int threads = 256);
+int jacobi_f64_occupancy(int n, int threads);
+int jacobi_mixed_occupancy(int n, int threads);
+size_t jacobi_mixed_smem_bytes(int n, bool c_in_smem);
+cudaError_t launch_jacobi_mixed(const ChanDev *chans_dev, const int *work_ch_dev, int n_work_ch, int n_samples,
+                                int sample0, int n_terms, const double *coeffs, int n, double *lam_s, double *X_s,
+                                float *Cf_s, int *status_all, int n_ch_total, int *err, cudaStream_t st,
+                                int threads = 256);
+size_t oz_slice_elems(int n);
+cudaError_t launch_oz_gemm(int n, int items, bool ta, const double *A, const double *B, double *C,
+                           __nv_bfloat16 *sa, __nv_bfloat16 *sb, int *ea, int *eb, cudaStream_t st);
+size_t refine_scratch_per_item(int n, int engine);
+cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_samples, int sample0, int n,
+                          int n_terms, const double *coeffs, void *scratch, double *eps_all, double *X_all,
+                          int iters, int engine, cudaStream_t st);
+cudaError_t launch_batched_dgemm(int n, int items, bool ta, const double *A, const double *B, double *C,
+                                 void *scratch, int engine, cudaStream_t st);
+size_t batched_dgemm_scratch(int n, int items);
 cudaError_t launch_plan(const ChanDev *chans_dev, int n_ch, int maxN, const double *e_lab, int n_E, PlanDev plan,
-                        int *err, cudaStream_t st);
+                        int *err, cudaStream_t st, int n_plans = 1);
 cudaError_t launch_tbin(const ChanDev *chans_dev, int n_ch, int n_samples, int n_terms, const double *coeffs,
                         const double *eps_all, const double *C_all, PlanDev plan, int maxN, double *tbin,
                         double *phbin, int *err, cudaStream_t st);

@@ -25,7 +25,12 @@ def oracle_run(orc, wl: W.Workload, samples=None):
     return t, d, s
 
 
-def gpu_run(ctx, model, wl: W.Workload, device="cuda:0", via="solve"):
+# Mixed-precision path tolerances (against the FP64 oracle)
+TOL_MIXED_DELTA_DEG = 1e-3
+TOL_MIXED_SIGMA_MB = 1e-2
+
+
+def gpu_run(ctx, model, wl: W.Workload, device="cuda:0", via="solve", prec=0):
     import torch
     S, nch, nE = wl.n_samples, len(wl.channels), len(wl.e_lab)
     coeffs = None if wl.n_terms == 1 else torch.tensor(wl.coeffs, dtype=torch.float64, device=device)
@@ -34,9 +39,9 @@ def gpu_run(ctx, model, wl: W.Workload, device="cuda:0", via="solve"):
     d = torch.zeros((S, nch, nE, 3), dtype=torch.float64, device=device)
     s = torch.zeros((S, nE), dtype=torch.float64, device=device)
     if via == "solve":
-        ctx.solve(model.vset, coeffs, S, e, t, d, s)
+        ctx.solve(model.vset, coeffs, S, e, t, d, s, prec=prec)
     else:
-        eid = ctx.diag(model.vset, coeffs, S)
+        eid = ctx.diag(model.vset, coeffs, S, prec=prec)
         ctx.tmatrix(eid, e, t)
         ctx.observables(eid, e, d, s)
         ctx.release(eid)
@@ -70,3 +75,26 @@ def compare(wl, gpu, ora, tol_t=TOL_T, tol_d=TOL_DELTA_DEG, tol_s=TOL_SIGMA_REL,
     rs = np.max(np.abs(gs - os_) / np.maximum(np.abs(os_), 1e-300))
     assert rs <= tol_s, ("sigma", rs)
     return report
+
+
+def compare_mixed(wl, gpu, ora, tol_d=TOL_MIXED_DELTA_DEG, tol_s=TOL_MIXED_SIGMA_MB, sample_idx=None):
+    """Mixed path: every (sample, channel, energy) phase within tol_d degrees and
+    every cross section within tol_s mb of the FP64 oracle.  Returns the worst
+    errors for reporting."""
+    gt, gd, gs = gpu
+    ot, od, os_ = ora
+    if sample_idx is not None:
+        gt, gd, gs = gt[sample_idx], gd[sample_idx], gs[sample_idx]
+    worst = {"delta_deg": 0.0, "eps_deg": 0.0, "sigma_mb": 0.0, "T_rel": 0.0}
+    for c, ch in enumerate(wl.channels):
+        ncomp = 2 if ch.coupled else 1
+        dd = float(np.max(np.abs(dphase(gd[:, c, :, :ncomp], od[:, c, :, :ncomp]))))
+        worst["delta_deg"] = max(worst["delta_deg"], dd)
+        if ch.coupled:
+            worst["eps_deg"] = max(worst["eps_deg"], float(np.max(np.abs(gd[:, c, :, 2] - od[:, c, :, 2]))))
+        sc = np.max(np.abs(ot[:, c]))
+        worst["T_rel"] = max(worst["T_rel"], float(np.max(np.abs(gt[:, c] - ot[:, c])) / sc))
+    worst["sigma_mb"] = float(np.max(np.abs(gs - os_)))
+    assert worst["delta_deg"] <= tol_d and worst["eps_deg"] <= tol_d, worst
+    assert worst["sigma_mb"] <= tol_s, worst
+    return worst

@@ -1,0 +1,53 @@
+"""FP64-accurate batched products (the mixed path's refinement engine) against
+an extended-precision reference.  Tensor-core Ozaki engine: the 48-bit
+rounding of every row of op(A) and column of B bounds the error by
+2^-49 (max_k|A_ik| sum_k|B_kj| + sum_k|A_ik| max_k|B_kj|) (2^-47 tested); FP64
+engine: n 2^-52 (|A| |B|)_ij."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_00454_gb300 import api, build
+    build.build()
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _mats(n, items, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((items, n, n)) * 10.0 ** rng.uniform(-8, 8, (items, n, 1))  # rows over 16 decades
+    B = rng.standard_normal((items, n, n)) * 10.0 ** rng.uniform(-8, 8, (items, 1, n))  # columns likewise
+    A[0, 1, :] = 0.0  # an all-zero row
+    return A, B
+
+
+@pytest.mark.parametrize("n", [8, 40, 100, 200, 300])
+@pytest.mark.parametrize("trans_a", [False, True])
+def test_batched_dgemm_engines(ctx, n, trans_a):
+    import torch
+    from paper_2106_00454_gb300 import api
+    A, B = _mats(n, 3, n + (7 if trans_a else 0))
+    opA = np.swapaxes(A, 1, 2) if trans_a else A
+    ref = np.matmul(opA.astype(np.longdouble), B.astype(np.longdouble))
+    absAB = np.matmul(np.abs(opA), np.abs(B))
+    aA, aB = np.abs(opA), np.abs(B)
+    scaled = (aA.max(axis=2, keepdims=True) * aB.sum(axis=1, keepdims=True)
+              + aA.sum(axis=2, keepdims=True) * aB.max(axis=1, keepdims=True))
+    dA = torch.tensor(A, device="cuda:0")
+    dB = torch.tensor(B, device="cuda:0")
+    for engine, tol, bound in [(api.REFINE_TENSOR, 2.0 ** -47, scaled), (api.REFINE_FP64, n * 2.0 ** -52, absAB)]:
+        dC = torch.full_like(dA, float("nan"))
+        ctx.batched_dgemm(dA, dB, dC, trans_a=trans_a, engine=engine)
+        ctx.sync()
+        C = dC.cpu().numpy()
+        err = np.abs(C.astype(np.longdouble) - ref)
+        assert np.all(np.isfinite(C))
+        assert np.all(err <= tol * bound + 1e-300), (engine, float(np.max(err / (bound + 1e-300))))

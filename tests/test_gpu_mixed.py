@@ -1,0 +1,112 @@
+"""Mixed-precision path (FP32 Jacobi + FP64 Rayleigh refinement) against the
+FP64 oracle: |d delta|, |d eps_J| <= 1e-3 deg and |d sigma| <= 0.01 mb for every
+(sample, channel, energy)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2106_00454_gb300 import inputs as W
+
+from parity_util import compare_mixed, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+MIXED = 1
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2106_00454_gb300 import api, build
+    build.build()
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _report(name, worst):
+    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+    if os.path.isdir(out):
+        with open(os.path.join(out, "mixed_errors.jsonl"), "a") as f:
+            f.write(json.dumps({"case": name, **worst}) + "\n")
+
+
+def test_mixed_yamaguchi(ctx, orc):
+    from paper_2106_00454_gb300 import api
+    wl = W.workload_yamaguchi()
+    md = api.Model(ctx, wl)
+    _report("yamaguchi", compare_mixed(wl, gpu_run(ctx, md, wl, prec=MIXED), oracle_run(orc, wl)))
+
+
+def test_mixed_all_channels(ctx, orc):
+    """Workload 2 (20 channels, N_WP = 100) through the mixed path."""
+    from paper_2106_00454_gb300 import api
+    wl = W.workload_all_channels()
+    md = api.Model(ctx, wl)
+    _report("all_channels_nwp100", compare_mixed(wl, gpu_run(ctx, md, wl, prec=MIXED), oracle_run(orc, wl)))
+
+
+def test_mixed_all_channels_fp64_refine_engine(ctx, orc):
+    """Workload 2 with the refinement products on the FP64 CUDA cores."""
+    from paper_2106_00454_gb300 import api
+    wl = W.workload_all_channels()
+    md = api.Model(ctx, wl)
+    ctx.set_refine_engine(api.REFINE_FP64)
+    try:
+        gpu = gpu_run(ctx, md, wl, prec=MIXED)
+    finally:
+        ctx.set_refine_engine(api.REFINE_TENSOR)
+    _report("all_channels_nwp100_fp64_engine", compare_mixed(wl, gpu, oracle_run(orc, wl)))
+
+
+def test_mixed_batched_sampled(ctx, orc):
+    """Workload 3 at full size through the mixed path; sampled samples vs the oracle."""
+    from paper_2106_00454_gb300 import api
+    wl = W.workload_batched()
+    md = api.Model(ctx, wl)
+    gpu = gpu_run(ctx, md, wl, prec=MIXED)
+    pick = [0, 2048, 4095]
+    _report("batched_4096_sampled", compare_mixed(wl, gpu, oracle_run(orc, wl, samples=pick), sample_idx=pick))
+
+
+def test_mixed_nwp150_sampled(ctx, orc):
+    """Workload 4's generator (20 channels, N_WP = 150, coupled 300 x 300) on a
+    small batch, every sample against the oracle."""
+    from paper_2106_00454_gb300 import api
+    wl = W.workload_mixed(n_samples=2)
+    md = api.Model(ctx, wl)
+    _report("nwp150_2samples", compare_mixed(wl, gpu_run(ctx, md, wl, prec=MIXED), oracle_run(orc, wl)))
+
+
+def test_mixed_eigenvalues_refined(ctx, orc):
+    torch = pytest.importorskip("torch")
+    from paper_2106_00454_gb300 import api
+    wl = W.workload_batched(n_samples=2)
+    ch = wl.channels[4]
+    wl1 = W.Workload("e", [ch], [100], wl.gen, wl.gen_params, wl.n_terms, wl.coeffs, wl.e_lab)
+    md = api.Model(ctx, wl1)
+    cf = torch.tensor(wl.coeffs, dtype=torch.float64, device="cuda:0")
+    e64 = ctx.diag(md.vset, cf, 2, prec=0)
+    e32 = ctx.diag(md.vset, cf, 2, prec=MIXED)
+    ctx.sync()
+    worst, where, orth = 0.0, None, 0.0
+    for s in range(2):
+        a, _ = ctx.eig_get(e64, s, 0, 200)
+        b, C = ctx.eig_get(e32, s, 0, 200)
+        # The resolvent sees an eigenvalue error through the SWP bin width it
+        # shifts, ~ (e_{s+2} - e_{s-2})/4 for the two interleaved branches;
+        # judged below 1 fm^-1 (~200 MeV c.m.), the region the energies reach.
+        idx = np.arange(200)
+        width = (a[np.minimum(idx + 2, 199)] - a[np.maximum(idx - 2, 0)]) / 4.0
+        sel = a < 1.0
+        r = np.abs(a - b) / width
+        k = int(np.argmax(np.where(sel, r, 0)))
+        if r[k] > worst:
+            worst, where = float(r[k]), (s, k, float(a[k]), float(b[k]))
+        orth = max(orth, float(np.linalg.norm(C.T @ C - np.eye(200))))
+    _report("eigenvalue_error_over_bin_width", {"worst": worst, "at": where, "orthogonality": orth})
+    assert orth < 1e-8
+    assert worst < 1e-4, where

@@ -218,3 +218,23 @@ def test_batched_full_size_sampled(ctx, orc):
     ora = oracle_run(orc, wl, samples=pick)
     compare(wl, gpu, ora, sample_idx=pick)
     assert np.all(np.isfinite(gpu[2]))
+
+
+def test_autotune_table_and_results(ctx):
+    """The autotuner records a CTA size per (n, precision) and the results stay
+    within the FP64 tolerances of the fixed 256-thread launch."""
+    from paper_2106_00454_gb300 import api
+    wl = W.workload_batched(n_samples=40)
+    md = _model(ctx, wl)
+    ctx.set_autotune(False)
+    a = gpu_run(ctx, md, wl)
+    ctx.set_autotune(True)
+    b = gpu_run(ctx, md, wl)
+    table = ctx.tuning()
+    ns = {2 * n if ch.coupled else n for n, ch in zip(wl.nwp, wl.channels)}
+    assert {e["n"] for e in table if e["precision"] == "fp64"} >= ns
+    assert all(e["threads"] in (64, 128, 256, 512) for e in table)
+    for c in range(len(wl.channels)):
+        sc = np.max(np.abs(a[0][:, c]))
+        assert np.max(np.abs(a[0][:, c] - b[0][:, c])) <= 1e-11 * sc
+    assert np.max(np.abs(dphase(a[1], b[1]))) <= 1e-9
