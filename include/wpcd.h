@@ -237,11 +237,11 @@ enum {
  * n x n row-major FP64 matrices stored back to back, queued on the context
  * stream -- the refinement products of the mixed path, exposed for reuse and
  * testing.  engine WPCD_REFINE_TENSOR: each row of op(A) and column of B is
- * scaled by a power of two, rounded to 48 bits and split into six 8-bit
- * digits (exact in BF16); digit products are summed exactly in FP32 on the
- * tensor cores (k <= 256 per sum) and combined in FP64 (Ozaki, Ogita, Oishi,
- * Rump, "Error-free transformations of matrix multiplication", 2012).  Error
- * <~ 2^-49 (max_k|op(A)_ik| sum_k|B_kj| + sum_k|op(A)_ik| max_k|B_kj|).
+ * scaled by a power of two, rounded to 47 bits and split into six balanced
+ * 8-bit digits (exact in BF16); digit products are summed exactly in FP32 on
+ * the tensor cores (k <= 256 per sum) and combined in FP64 (Ozaki, Ogita,
+ * Oishi, Rump, "Error-free transformations of matrix multiplication", 2012).
+ * Error <~ 2^-48 (max_k|op(A)_ik| sum_k|B_kj| + sum_k|op(A)_ik| max_k|B_kj|).
  * engine WPCD_REFINE_FP64: FP64 FMA.
  * n <= 1024.  Errors: WPCD_ERR_ARG, WPCD_ERR_NOMEM, WPCD_ERR_CUDA. */
 wpcd_status wpcd_batched_dgemm(wpcd_ctx *ctx, int n, int items, int trans_a, const double *A_dev,

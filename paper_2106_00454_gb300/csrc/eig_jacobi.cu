@@ -201,9 +201,13 @@ __global__ void __launch_bounds__(kJacMaxThreads) k_jacobi_f64(const ChanDev *ch
                 int p = pp_[k], q = qq_[k];
                 if (q >= n) continue;
                 double c = rc[k], s = rs[k];
-                double cp = C[(size_t)row * n + p], cq = C[(size_t)row * n + q];
-                C[(size_t)row * n + p] = c * cp - s * cq;
-                C[(size_t)row * n + q] = s * cp + c * cq;
+                // in shared memory C is column-major (conflict-free row walks);
+                // in global memory it stays row-major for the in-place final permutation
+                const size_t ip = C_SMEM ? (size_t)p * n + row : (size_t)row * n + p;
+                const size_t iq = C_SMEM ? (size_t)q * n + row : (size_t)row * n + q;
+                double cp = C[ip], cq = C[iq];
+                C[ip] = c * cp - s * cq;
+                C[iq] = s * cp + c * cq;
             }
             __syncthreads();
         }
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(kJacMaxThreads) k_jacobi_f64(const ChanDev *ch
     if (C_SMEM) {
         for (int e = tid; e < n * n; e += nt) {
             int row = e / n, col = e - row * n;
-            Cg[(size_t)row * n + rank[col]] = Cs[e];
+            Cg[(size_t)row * n + rank[col]] = Cs[(size_t)col * n + row];
         }
     } else {
         // permute in place row by row through the (now free) A storage

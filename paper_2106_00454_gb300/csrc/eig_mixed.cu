@@ -157,9 +157,11 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
                 const int p = pp_[k], q = qq_[k];
                 if (q >= n || rs[k] == 0.0f) continue;
                 const float c = rc[k], s = rs[k];
-                const float cp = C[(size_t)row * n + p], cq = C[(size_t)row * n + q];
-                C[(size_t)row * n + p] = c * cp - s * cq;
-                C[(size_t)row * n + q] = s * cp + c * cq;
+                // C is kept column-major (column s contiguous): consecutive
+                // threads walk consecutive rows of the same two columns
+                const float cp = C[(size_t)p * n + row], cq = C[(size_t)q * n + row];
+                C[(size_t)p * n + row] = c * cp - s * cq;
+                C[(size_t)q * n + row] = s * cp + c * cq;
             }
             __syncthreads();
         }
@@ -171,8 +173,11 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
     }
 
     // ---- FP32 eigenpairs out, as FP64, unsorted
-    double *X = X_s + (size_t)blockIdx.x * n * n;
-    for (int e = tid; e < n * n; e += nt) X[e] = (double)C[e];
+    double *X = X_s + (size_t)blockIdx.x * n * n;  // row-major out of the column-major C
+    for (int e = tid; e < n * n; e += nt) {
+        const int col = e / n, row = e - col * n;
+        X[(size_t)row * n + col] = (double)C[e];
+    }
     for (int i = tid; i < n; i += nt) lam_s[(size_t)blockIdx.x * n + i] = (double)A[pk(i, i)];
     if (tid == 0) {
         status_all[(size_t)smp * n_ch_total + cidx] = converged ? sweeps : -1;

@@ -6,18 +6,17 @@
 // FP64 product into a few exact low-precision ones:
 //   * every row of the left operand and every column of the right one is
 //     scaled by a power of two (2^e = the smallest power above its largest
-//     magnitude), rounded to 48 bits and cut into P = 6 digits of 8 bits:
-//     v / 2^e = sum_p s_p 2^{-8(p+1)}, the top digit signed (|s_0| <= 256),
-//     the others in [0, 255] -- all exact in BF16;
-//   * the product of two slices is a sum of integer products of magnitude
-//     <= 2^16; over k <= 256 terms the sum stays below 2^24, so the tensor
-//     core's FP32 accumulation is exact;
-//   * C_ij = 2^{e_i + f_j} sum_{p+q <= P+1} 2^{-8(p+q)} (A_p B_q)_ij,
-//     accumulated in FP64 (terms with p+q > P+1 lie below 2^{-8(P+2)}).
-// The error is that of the 48-bit rounding: |dC_ij| <~ 2^-49 (2^{e_i}
-// sum_k |B_kj| + 2^{f_j} sum_k |A_ik|), i.e. ~1e-14 relative to the row and
-// column scales (the refinement needs far less; FP64 FMA would give ~n 2^-53
-// of sum_k |A_ik B_kj|).  The slices are stored k-contiguous ([p][vector][k],
+//     magnitude), rounded to 47 bits and cut into P = 6 balanced digits of 8
+//     bits: v / 2^e = sum_p d_p 2^{-8(p+1)+1}, d_1..d_5 in [-128, 127] and
+//     |d_0| <= 129 -- all exact in BF16;
+//   * the product of two digit slices is a sum of integer products of
+//     magnitude < 2^15; over k <= 256 terms the sum stays below 2^23, so the
+//     tensor core's FP32 accumulation is exact;
+//   * C_ij = 2^{e_i + f_j} sum_{p+q <= P-1} 2^{-8(p+q+2)+2} (A_p B_q)_ij,
+//     accumulated in FP64 (the 15 dropped pairs weigh at most 2^-62 each).
+// The error is dominated by the 47-bit rounding, |dC_ij| <~ 2^-48 (2^{e_i}
+// sum_k |B_kj| + 2^{f_j} sum_k |A_ik|), ~4e-15 relative to the row and column
+// scales.  The slices are stored k-contiguous ([p][vector][k],
 // k padded to a multiple of 32) for both operands, the layout the
 // m16n8k16 row.col tensor instruction consumes.
 #include <cuda_bf16.h>
@@ -61,18 +60,21 @@ __global__ void k_oz_exp(int n, const double *M_all, int *e_all)
     e_all[(size_t)b * n + v] = ex;
 }
 
-// The six 8-bit digits of x / 2^e: N = rint(x 2^{48-e}) (|N| <= 2^48), then
-// N = s0 2^40 + s1 2^32 + ... + s5 with s0 signed (|s0| <= 256) and s1..s5 in
-// [0, 255] -- all exact in BF16, all products below 2^16.
+// The six balanced 8-bit digits of x / 2^e: N = rint(x 2^{47-e}) (|N| <= 2^47),
+// then N = d0 2^40 + d1 2^32 + ... + d5 with d1..d5 in [-128, 127] and
+// |d0| <= 129 -- all exact in BF16, every digit product below 2^15 in
+// magnitude, and the signs of the truncated lower products vary, so their
+// sum grows like sqrt(k) instead of k.
 __device__ __forceinline__ void oz_digits(double x, int e, __nv_bfloat16 *d, size_t stride)
 {
-    const int be = 1023 + 48 - e;  // biased exponent of 2^{48-e}
-    const double scale = (be >= 1 && be <= 2046) ? __hiloint2double(be << 20, 0) : ldexp(1.0, 48 - e);  // exact
+    const int be = 1023 + 47 - e;  // biased exponent of 2^{47-e}
+    const double scale = (be >= 1 && be <= 2046) ? __hiloint2double(be << 20, 0) : ldexp(1.0, 47 - e);  // exact
     long long N = __double2ll_rn(x * scale);
 #pragma unroll
     for (int p = kOzP - 1; p >= 1; --p) {
-        d[(size_t)p * stride] = __float2bfloat16_rn((float)(int)(N & 0xFF));
-        N >>= 8;  // arithmetic shift: floor division, keeps the sign in the top digit
+        const long long dig = ((N + 128) & 0xFF) - 128;
+        d[(size_t)p * stride] = __float2bfloat16_rn((float)(int)dig);
+        N = (N - dig) >> 8;  // exact: N - dig is a multiple of 256
     }
     d[0] = __float2bfloat16_rn((float)(int)N);
 }
@@ -123,9 +125,7 @@ __device__ __forceinline__ void mma_bf16(float *c, unsigned a0, unsigned a1, uns
 }
 
 // C[b] = A[b] B[b] from row slices of A and column slices of B.  64 x 64
-// output tile per CTA, 4 warps of 32 x 32; per slice pair an exact FP32
-// accumulation over k (flushed to FP64 every 256 k), then FP64 accumulation
-// over the pairs.
+// output tile per CTA, 4 warps of 32 x 32.
 __global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, const __nv_bfloat16 *A_s, const int *ea_all,
                                                  const __nv_bfloat16 *B_s, const int *eb_all, double *C_all)
 {
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, const __nv_bfloa
     const int b = blockIdx.z;
     const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = lane >> 2, t = lane & 3;
+    const int g4 = lane >> 2, t = lane & 3;
     const int wr = (warp >> 1) * 32, wc = (warp & 1) * 32;
     const __nv_bfloat16 *Ab = A_s + (size_t)b * kOzP * n * Kp;
     const __nv_bfloat16 *Bb = B_s + (size_t)b * kOzP * n * Kp;
@@ -147,9 +147,20 @@ __global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, const __nv_bfloa
 #pragma unroll
             for (int u = 0; u < 4; ++u) acc[i][j][u] = 0.0;
 
-    for (int p = 0; p < kOzP; ++p) {
-        for (int q = 0; p + q < kOzP; ++q) {
-            const double scale = ldexp(1.0, -8 * (p + q + 2));
+    // Digit pairs grouped by d = p + q (common weight 2^{-8(d+2)+2}).  Each
+    // pair's FP32 sum over at most 256 k is an exact integer below 2^23; the
+    // group adds them as int32 (at most 6 pairs x 2 k-chunks: below 2^27) and
+    // reaches the FP64 accumulator once per group.
+    for (int d = 0; d < kOzP; ++d) {
+        int g[2][4][4];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) g[i][j][u] = 0;
+        for (int p = 0; p <= d; ++p) {
+            const int q = d - p;
             const __nv_bfloat16 *Ap = Ab + (size_t)p * n * Kp;
             const __nv_bfloat16 *Bq = Bb + (size_t)q * n * Kp;
             float c32[2][4][4];
@@ -178,7 +189,7 @@ __global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, const __nv_bfloa
                     unsigned af[2][4], bf[4][2];
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
-                        const __nv_bfloat16 *base = &As[(wr + i * 16 + g) * kOzLd + ks + 2 * t];
+                        const __nv_bfloat16 *base = &As[(wr + i * 16 + g4) * kOzLd + ks + 2 * t];
                         af[i][0] = ld_u32(base);
                         af[i][1] = ld_u32(base + 8 * kOzLd);
                         af[i][2] = ld_u32(base + 8);
@@ -186,7 +197,7 @@ __global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, const __nv_bfloa
                     }
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const __nv_bfloat16 *base = &Bs[(wc + j * 8 + g) * kOzLd + ks + 2 * t];
+                        const __nv_bfloat16 *base = &Bs[(wc + j * 8 + g4) * kOzLd + ks + 2 * t];
                         bf[j][0] = ld_u32(base);
                         bf[j][1] = ld_u32(base + 8);
                     }
@@ -203,12 +214,19 @@ __global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, const __nv_bfloa
                         for (int j = 0; j < 4; ++j)
 #pragma unroll
                             for (int u = 0; u < 4; ++u) {
-                                acc[i][j][u] = fma((double)c32[i][j][u], scale, acc[i][j][u]);
+                                g[i][j][u] += __float2int_rn(c32[i][j][u]);
                                 c32[i][j][u] = 0.f;
                             }
                 }
             }
         }
+        const double scale = ldexp(1.0, -8 * (d + 2) + 2);  // digit weights 2^{-8(p+1)+1}
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[i][j][u] = fma((double)g[i][j][u], scale, acc[i][j][u]);
     }
     const int *ea = ea_all + (size_t)b * n, *eb = eb_all + (size_t)b * n;
     double *C = C_all + (size_t)b * n * n;
@@ -218,7 +236,7 @@ __global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, const __nv_bfloa
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int r = row0 + wr + i * 16 + g + (u >= 2 ? 8 : 0);
+                const int r = row0 + wr + i * 16 + g4 + (u >= 2 ? 8 : 0);
                 const int c = col0 + wc + j * 8 + 2 * t + (u & 1);
                 if (r < n && c < n) C[(size_t)r * n + c] = ldexp(acc[i][j][u], ea[r] + eb[c]);
             }

@@ -217,6 +217,18 @@ __global__ void __launch_bounds__(kTThreads) k_tbin(const ChanDev *chans, int n_
         __syncthreads();
         const double Ea = ch.kb[i] * ch.kb[i] / (2.0 * kMu), Ebn = ch.kb[i + 1] * ch.kb[i + 1] / (2.0 * kMu);
         const double dE = Ebn - Ea;
+        // D(B) = X(Eb, B) - X(Ea, B) once per SWP boundary of each branch (the
+        // branch-member array is free by now); state s then needs D(B_s) - D(B_s+1)
+        const int dstride = (K == 2) ? (n >> 1) + 2 : n + 1;
+        double *Dv = Eb;
+        for (int e = tid; e < K * dstride; e += nt) {
+            const int b = e / dstride, pos = e - b * dstride;
+            if (pos <= mcount[b]) {
+                const double B = Bb[b * (n + 1) + pos];
+                Dv[e] = xlogabs(Ebn - B) - xlogabs(Ea - B);
+            }
+        }
+        __syncthreads();
         double acc[6] = {0, 0, 0, 0, 0, 0};  // (00 re, im), (01 re, im), (11 re, im)
         for (int s = tid; s < n; s += nt) {
             double gre, gim;
@@ -225,7 +237,10 @@ __global__ void __launch_bounds__(kTThreads) k_tbin(const ChanDev *chans, int n_
                 gim = 0.0;
             } else {
                 const double b0 = lo[s], b1 = hi[s], dB = b1 - b0;
-                const double num = xlogabs(Ebn - b0) - xlogabs(Ea - b0) - xlogabs(Ebn - b1) + xlogabs(Ea - b1);
+                const int d = s - nb;
+                const int b = (K == 2) ? (((n - 1 - s) & 1) == 0 ? 1 : 0) : 0;
+                const int pos = (K == 2) ? d / 2 : d;
+                const double num = Dv[b * dstride + pos] - Dv[b * dstride + pos + 1];
                 gre = num / (dE * dB);
                 const double l = Ea > b0 ? Ea : b0, h = Ebn < b1 ? Ebn : b1;
                 gim = (h > l) ? -kPi * (h - l) / (dE * dB) : 0.0;
