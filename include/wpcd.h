@@ -61,10 +61,22 @@ typedef enum {
  * S, phases) is FP64 on both paths. */
 typedef enum { WPCD_PREC_FP64 = 0, WPCD_PREC_MIXED = 1 } wpcd_precision;
 
-/* Resolvent used for the on-shell T (App. B).  FREE_BIN: the SWP resolvent
- * averaged over the free bin that holds the on-shell energy (the averaging of
- * Sec. 3.2, "resolvent energy averaging"). */
-typedef enum { WPCD_AVG_FREE_BIN = 0 } wpcd_resolvent;
+/* Resolvent used for the on-shell T (App. B).
+ * FREE_BIN: the SWP resolvent averaged over the free bin that holds the
+ *   on-shell energy (the averaging of Sec. 3.2, "resolvent energy averaging";
+ *   App. B closed form with the sign of W corrected).  T per free bin,
+ *   converted at the bin midpoint; phases interpolated between midpoints.
+ * SWP_INDEX: the App. B formula as printed, averaging over SWP bin i of the
+ *   channel's single branch instead of free bin i.  Defined for uncoupled
+ *   channels without bound states: a vset with a coupled channel is refused
+ *   (WPCD_ERR_ARG); a solve that has a bound state gets NaN outputs and
+ *   wpcd_sync reports WPCD_ERR_ARG.
+ * POINT: no averaging; the point resolvent of App. B,
+ *   g_s(E) = [ln|(E - B_s)/(E - B_s+1)| - i pi 1{E in [B_s, B_s+1]}] / dB_s
+ *   (1/(E - e_b) for a bound state), evaluated at each requested energy, with
+ *   the continuum conversion, S and the phases at p(E) itself (no
+ *   interpolation).  An energy exactly on an SWP boundary gives a non-finite T. */
+typedef enum { WPCD_AVG_FREE_BIN = 0, WPCD_AVG_SWP_INDEX = 1, WPCD_POINT = 2 } wpcd_resolvent;
 
 /* Partial-wave channel.  Uncoupled: l = lp.  Coupled (K = 2): l = J-1,
  * lp = J+1 and the channel is the 2x2 block pair on degenerate FWP copies
@@ -179,8 +191,8 @@ wpcd_status wpcd_eig_get(wpcd_ctx *ctx, int eig_id, int sample, int channel, dou
 
 /* ---- (a4-a7) on-shell T: Sec. 3.2 steps 3-5, App. B -----------------------------------------------
  * For every sample, channel and requested energy: the SWP boundaries of
- * Eq. "pseudostate wave packet boundaries", the energy-averaged resolvent of
- * App. B averaged over the free bin D_i holding p(E), and
+ * Eq. "pseudostate wave packet boundaries", the resolvent of App. B chosen by
+ * res (default: averaged over the free bin D_i holding p(E)), and
  *   T_ab(i) = V_(a,i),(b,i) + sum_s (VC)_(a,i),s gbar_s (VC)_(b,i),s,
  * converted to the continuum at q = the bin midpoint (Eq. "operator in cont and
  * disc representation").  e_lab_dev: [n_E] MeV, ascending, each inside the
@@ -201,6 +213,11 @@ wpcd_status wpcd_tmatrix(wpcd_ctx *ctx, int eig_id, const double *e_lab_dev, int
  * Either output may be NULL.  Errors as wpcd_tmatrix. */
 wpcd_status wpcd_observables(wpcd_ctx *ctx, int eig_id, const double *e_lab_dev, int n_E, double *delta_dev,
                              double *sigma_dev);
+
+/* wpcd_observables with another resolvent (wpcd_observables uses FREE_BIN).
+ * POINT gives the phases at each p(E) directly, without interpolation. */
+wpcd_status wpcd_observables_res(wpcd_ctx *ctx, int eig_id, const double *e_lab_dev, int n_E, wpcd_resolvent res,
+                                 double *delta_dev, double *sigma_dev);
 
 /* ---- the whole hot path in one call --------------------------------------------------------------
  * wpcd_diag + wpcd_tmatrix + wpcd_observables for one batch, with the

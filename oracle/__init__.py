@@ -64,13 +64,14 @@ def lib():
                 "or_contract": (None, [i, i, _dp, _dp, _dp, _dp, _dp, _dp]),
                 "or_phases_from_S": (None, [i, _dp, _dp]),
                 "or_S_from_T": (None, [i, d, _dp, _dp]),
-                "or_channel_solve": (i, [i, _dp, i, i, i, _dp, _dp, _dp, _dp, _dp, _ip]),
+                "or_channel_solve": (i, [i, _dp, i, i, i, _dp, _dp, i, _dp, _dp, _dp, _ip]),
+                "or_channel_solve_point": (i, [i, _dp, i, i, i, _dp, _dp, i, _dp, _dp, _dp]),
                 "or_interp_phase": (None, [i, _dp, _dp, i, d, _dp]),
                 "or_sigma_term": (d, [i, i, _dp]),
                 "or_sigma_prefactor_mb": (d, [d]),
                 "or_mi_kmatrix": (i, [i, _dp, i, i, i, i, i, i, i, _dp, i, d, d, _dp]),
                 "or_S_from_K": (None, [i, d, _dp, _dp]),
-                "or_batch": (i, [i, _ip, _ip, _lp, _dp, i, i, _lp, _dp, i, _dp, i, _dp, _dp, _dp, _dp, i]),
+                "or_batch": (i, [i, _ip, _ip, _lp, _dp, i, i, _lp, _dp, i, _dp, i, _dp, i, _dp, _dp, _dp, i]),
                 "or_max_threads": (i, []),
             }
             for name, (res, args) in sig.items():
@@ -249,9 +250,14 @@ def sigma_prefactor_mb(p):
 
 
 # ----------------------------------------------------------------------------- solves
-def channel_solve(mesh: Mesh, K, Vt, c, wp_kind=0):
+AVG_FREE_BIN, AVG_SWP_INDEX, POINT = 0, 1, 2  # resolvent modes
+
+
+def channel_solve(mesh: Mesh, K, Vt, c, wp_kind=0, mode=AVG_FREE_BIN):
     """One channel-solve at every free bin.
 
+    mode: AVG_FREE_BIN (resolvent averaged over the free bin) or AVG_SWP_INDEX
+    (over SWP bin i; uncoupled channels without bound states, else rc = -4).
     Returns (Tc [N,K,K] complex continuum T at the bin midpoints in fm^2,
     ph [N,3] degrees, eps [n], rc) where rc = number of bound states or a
     negative error code."""
@@ -264,9 +270,24 @@ def channel_solve(mesh: Mesh, K, Vt, c, wp_kind=0):
     ph = np.zeros((N, 3))
     eps = np.zeros(n)
     sweeps = ctypes.c_int()
-    rc = lib().or_channel_solve(N, _d(mesh.kb), wp_kind, K, n_terms, _d(Vt), _d(c), Tc.ctypes.data_as(_dp),
-                                _d(ph), _d(eps), ctypes.byref(sweeps))
+    rc = lib().or_channel_solve(N, _d(mesh.kb), wp_kind, K, n_terms, _d(Vt), _d(c), int(mode),
+                                Tc.ctypes.data_as(_dp), _d(ph), _d(eps), ctypes.byref(sweeps))
     return Tc, ph, eps, rc
+
+
+def channel_solve_point(mesh: Mesh, K, Vt, c, p_list, wp_kind=0):
+    """Point-resolvent channel-solve at each momentum of p_list (fm^-1, inside
+    the mesh): (Tc [nE,K,K] complex fm^2, ph [nE,3] degrees, rc)."""
+    Vt = _f64(Vt)
+    n_terms = Vt.shape[0]
+    c = _f64(np.zeros(max(n_terms - 1, 1)) if c is None else c)
+    p_list = _f64(np.atleast_1d(p_list))
+    nE = p_list.shape[0]
+    Tc = np.zeros((nE, K, K), dtype=np.complex128)
+    ph = np.zeros((nE, 3))
+    rc = lib().or_channel_solve_point(mesh.N, _d(mesh.kb), wp_kind, K, n_terms, _d(Vt), _d(c), nE, _d(p_list),
+                                      Tc.ctypes.data_as(_dp), _d(ph))
+    return Tc, ph, rc
 
 
 def mi_kmatrix(gen, gp, ch, n_terms, c, p, NQ=96, cmap=1.0):
@@ -280,11 +301,12 @@ def mi_kmatrix(gen, gp, ch, n_terms, c, p, NQ=96, cmap=1.0):
     return Km.reshape(K, K)
 
 
-def batch(channels, meshes, Vts, coeffs, e_lab, wp_kind=0, n_threads=0):
+def batch(channels, meshes, Vts, coeffs, e_lab, wp_kind=0, n_threads=0, mode=AVG_FREE_BIN):
     """Every (sample, channel) solve plus interpolation and sigma_tot.
 
     channels: list of 6-tuples (s, J, l, lp, coupled, tz); meshes: one Mesh per
     channel; Vts: one (n_terms, n, n) array per channel; coeffs: (S, n_terms-1).
+    mode: AVG_FREE_BIN, AVG_SWP_INDEX or POINT (T and phases at each energy).
     Returns (t_out [S,ch,E,2,2] complex, delta [S,ch,E,3] deg, sigma [S,E] mb, rc)."""
     n_ch = len(channels)
     chdesc = np.ascontiguousarray(np.array(channels, dtype=np.int32).reshape(n_ch, 6))
@@ -302,7 +324,7 @@ def batch(channels, meshes, Vts, coeffs, e_lab, wp_kind=0, n_threads=0):
     delta = np.zeros((S, n_ch, nE, 3))
     sigma = np.zeros((S, nE))
     rc = lib().or_batch(n_ch, _i(chdesc), _i(nwp), kb_off.ctypes.data_as(_lp), _d(kb_all), wp_kind, n_terms,
-                        vt_off.ctypes.data_as(_lp), _d(vt_all), S, _d(coeffs), nE, _d(e_lab),
+                        vt_off.ctypes.data_as(_lp), _d(vt_all), S, _d(coeffs), nE, _d(e_lab), int(mode),
                         t_out.ctypes.data_as(_dp), _d(delta), _d(sigma), int(n_threads))
     return t_out, delta, sigma, rc
 

@@ -578,12 +578,15 @@ void or_S_from_T(int K, double p, const double complex *T, double complex *S)
 /*   H = diag(H0) (per l-block) + Vt[0] + sum_a c_a Vt[a];                    */
 /*   eigenpairs; SWP boundaries; gbar for free bin i; T_ii; continuum T at    */
 /*   q = kbar_i; S; phases.                                                   */
+/* mode 0: resolvent averaged over free bin i (reading G8); mode 1: over SWP  */
+/* bin i (the printed App. B form; uncoupled channels without bound states). */
 /* Outputs: Tc [N][K][K] complex continuum T(kbar_i,kbar_i) in fm^2,          */
 /*          ph [N][3] degrees, eps [n].  Returns the number of bound states,  */
-/*          or a negative code (-1 no convergence, -2 bad branch sizes).      */
+/*          or a negative code (-1 no convergence, -2 bad branch sizes,       */
+/*          -4 mode 1 on a coupled channel or with a bound state).            */
 /* ------------------------------------------------------------------------- */
 int or_channel_solve(int N, const double *kb, int wp_kind, int K, int n_terms, const double *Vt,
-                     const double *c, double complex *Tc, double *ph, double *eps_out, int *sweeps_out)
+                     const double *c, int mode, double complex *Tc, double *ph, double *eps_out, int *sweeps_out)
 {
     int n = K * N;
     double mu = or_mu();
@@ -609,10 +612,18 @@ int or_channel_solve(int N, const double *kb, int wp_kind, int K, int n_terms, c
     int nb = or_swp_boundaries(n, K, eps, branch, pos, mcount, bnd);
     for (int b = 0; b < K; ++b)
         if (mcount[b] < 2) rc = -2;
+    /* SWP-index averaging (App. B as printed, reading G8 alternative): the      */
+    /* average runs over SWP bin i of the one branch, which lines up with free   */
+    /* bin i only for an uncoupled channel without bound states.                  */
+    if (mode == 1 && rc == 0 && (K != 1 || nb != 0)) rc = -4;
     double *R = (double *)malloc(sizeof(double) * K * n);
     double *gre = (double *)malloc(sizeof(double) * n), *gim = (double *)malloc(sizeof(double) * n);
     for (int i = 0; i < N && rc == 0; ++i) {
         double Ea = kb[i] * kb[i] / (2.0 * mu), Eb = kb[i + 1] * kb[i + 1] / (2.0 * mu);
+        if (mode == 1) { /* average over SWP bin i instead of free bin i */
+            Ea = bnd[i];
+            Eb = bnd[i + 1];
+        }
         /* rows (a, i) of VC */
         for (int a = 0; a < K; ++a)
             for (int s = 0; s < n; ++s) {
@@ -646,6 +657,88 @@ int or_channel_solve(int N, const double *kb, int wp_kind, int K, int n_terms, c
         or_phases_from_S(K, S, ph + 3 * i);
     }
     if (eps_out) memcpy(eps_out, eps, sizeof(double) * n);
+    free(H); free(V); free(C); free(eps); free(branch); free(pos); free(bnd); free(R); free(gre); free(gim);
+    return rc < 0 ? rc : nb;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Point-resolvent variant (App. B point form with reading G6): no energy     */
+/* average; at each requested energy E = p^2/(2 mu), with i the free bin      */
+/* holding p,                                                                 */
+/*   T_ab(E) = V_(a,i),(b,i) + sum_s (VC)_(a,i),s g_s(E) (VC)_(b,i),s,        */
+/*   g_s(E) = [ln|(E - B_s)/(E - B_{s+1})| - i pi 1{E in [B_s, B_{s+1}]}]/dB_s */
+/*   for a scattering state, 1/(E - e_b) for a bound state,                   */
+/* converted to the continuum at q = p itself (the pointwise reading of Eq.   */
+/* "operator in cont and disc representation"); S and the phases at p, with   */
+/* no interpolation.  p_list [nE] ascending inside the mesh.                  */
+/* Outputs: Tc [nE][K][K] complex fm^2, ph [nE][3] degrees.  Returns the      */
+/* number of bound states or a negative code (-1, -2 as above; -3 an energy   */
+/* outside the mesh).                                                         */
+/* ------------------------------------------------------------------------- */
+int or_channel_solve_point(int N, const double *kb, int wp_kind, int K, int n_terms, const double *Vt,
+                           const double *c, int nE, const double *p_list, double complex *Tc, double *ph)
+{
+    int n = K * N;
+    double mu = or_mu();
+    double *H = (double *)malloc(sizeof(double) * n * n);
+    double *V = (double *)malloc(sizeof(double) * n * n);
+    double *C = (double *)malloc(sizeof(double) * n * n);
+    double *eps = (double *)malloc(sizeof(double) * n);
+    for (int i = 0; i < n * n; ++i) {
+        double v = Vt[i];
+        for (int a = 1; a < n_terms; ++a) v += c[a - 1] * Vt[(size_t)a * n * n + i];
+        V[i] = v;
+        H[i] = v;
+    }
+    for (int blk = 0; blk < K; ++blk)
+        for (int i = 0; i < N; ++i) H[(blk * N + i) * n + (blk * N + i)] += or_h0(wp_kind, kb[i], kb[i + 1]);
+    int rc = or_jacobi(n, H, eps, C) < 0 ? -1 : 0;
+    int *branch = (int *)malloc(sizeof(int) * n), *pos = (int *)malloc(sizeof(int) * n);
+    int mcount[2];
+    double *bnd = (double *)malloc(sizeof(double) * 2 * (n + 1));
+    int nb = or_swp_boundaries(n, K, eps, branch, pos, mcount, bnd);
+    for (int b = 0; b < K; ++b)
+        if (mcount[b] < 2) rc = -2;
+    double *R = (double *)malloc(sizeof(double) * K * n);
+    double *gre = (double *)malloc(sizeof(double) * n), *gim = (double *)malloc(sizeof(double) * n);
+    for (int e = 0; e < nE && rc == 0; ++e) {
+        double p = p_list[e], E = p * p / (2.0 * mu);
+        int i = -1;
+        for (int j = 0; j < N; ++j)
+            if (kb[j] <= p && p < kb[j + 1]) i = j;
+        if (i < 0) {
+            rc = -3;
+            break;
+        }
+        for (int a = 0; a < K; ++a)
+            for (int s2 = 0; s2 < n; ++s2) {
+                double acc = 0.0;
+                for (int j = 0; j < n; ++j) acc += V[(a * N + i) * n + j] * C[j * n + s2];
+                R[a * n + s2] = acc;
+            }
+        for (int s2 = 0; s2 < n; ++s2) {
+            if (branch[s2] < 0) {
+                gre[s2] = 1.0 / (E - eps[s2]);
+                gim[s2] = 0.0;
+            } else {
+                const double *B = bnd + (size_t)branch[s2] * (n + 1);
+                or_g_point(E, B[pos[s2]], B[pos[s2] + 1], &gre[s2], &gim[s2]);
+            }
+        }
+        double Vd[4], Tr[4], Ti[4];
+        for (int a = 0; a < K; ++a)
+            for (int b = 0; b < K; ++b) Vd[a * K + b] = V[(a * N + i) * n + (b * N + i)];
+        or_contract(n, K, Vd, R, gre, gim, Tr, Ti);
+        double Ni = wp_norm(wp_kind, kb[i], kb[i + 1]);
+        double fac = wp_f(wp_kind, p) * wp_f(wp_kind, p) / (Ni * p * p);
+        double complex Tq[4], S[4];
+        for (int ab = 0; ab < K * K; ++ab) {
+            Tq[ab] = fac * (Tr[ab] + I * Ti[ab]);
+            Tc[(size_t)e * K * K + ab] = Tq[ab];
+        }
+        or_S_from_T(K, p, Tq, S);
+        or_phases_from_S(K, S, ph + 3 * e);
+    }
     free(H); free(V); free(C); free(eps); free(branch); free(pos); free(bnd); free(R); free(gre); free(gim);
     return rc < 0 ? rc : nb;
 }
@@ -816,6 +909,56 @@ void or_S_from_K(int K, double p, const double *Km, double complex *S)
     S[3] = Ai[2] * Bm[1] + Ai[3] * Bm[3];
 }
 
+static int batch_point(int n_ch, const int *chdesc, const int *nwp, const long *kb_off, const double *kb_all,
+                       int wp_kind, int n_terms, const long *vt_off, const double *Vt_all, int n_samples,
+                       const double *coeffs, int n_E, const double *e_lab, double complex *t_out, double *delta_out,
+                       double *sigma_out, int n_threads)
+{
+    int err = 0;
+    double *p = (double *)malloc(sizeof(double) * n_E);
+    for (int e = 0; e < n_E; ++e) p[e] = or_p_of_tlab(e_lab[e]);
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic) collapse(2)
+#endif
+    for (int smp = 0; smp < n_samples; ++smp)
+        for (int c = 0; c < n_ch; ++c) {
+            int K = chdesc[c * 6 + 4] ? 2 : 1;
+            double complex *Tc = (double complex *)malloc(sizeof(double complex) * n_E * K * K);
+            double *ph = (double *)malloc(sizeof(double) * n_E * 3);
+            int rc = or_channel_solve_point(nwp[c], kb_all + kb_off[c], wp_kind, K, n_terms, Vt_all + vt_off[c],
+                                            coeffs + (size_t)smp * (n_terms - 1), n_E, p, Tc, ph);
+            if (rc < 0) {
+#ifdef _OPENMP
+#pragma omp critical(or_err)
+#endif
+                if (!err) err = rc;
+            }
+            for (int e = 0; e < n_E; ++e) {
+                double complex *tout = t_out + (((size_t)smp * n_ch + c) * n_E + e) * 4;
+                double *dout = delta_out + (((size_t)smp * n_ch + c) * n_E + e) * 3;
+                for (int ab = 0; ab < 4; ++ab) tout[ab] = 0.0;
+                for (int k = 0; k < 3; ++k) dout[k] = rc < 0 ? 0.0 : ph[3 * e + k];
+                if (rc >= 0)
+                    for (int a = 0; a < K; ++a)
+                        for (int b = 0; b < K; ++b) tout[a * 2 + b] = Tc[(size_t)e * K * K + a * K + b];
+            }
+            free(Tc);
+            free(ph);
+        }
+    for (int smp = 0; smp < n_samples; ++smp)
+        for (int e = 0; e < n_E; ++e) {
+            double acc = 0.0;
+            for (int c = 0; c < n_ch; ++c)
+                if (chdesc[c * 6 + 5] == 0)
+                    acc += or_sigma_term(chdesc[c * 6 + 1], chdesc[c * 6 + 4] ? 2 : 1,
+                                         delta_out + (((size_t)smp * n_ch + c) * n_E + e) * 3);
+            sigma_out[(size_t)smp * n_E + e] = or_sigma_prefactor_mb(p[e]) * acc;
+        }
+    free(p);
+    return err;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Batch driver used for the CPU baseline and the large parity cases: every   */
 /* (sample, channel) is one channel-solve; the channel loop of each sample is */
@@ -823,13 +966,18 @@ void or_S_from_K(int K, double p, const double *Km, double complex *S)
 /* starts at Vt_all + vt_off[c]; meshes per channel (kb_all + kb_off[c],     */
 /* N = nwp[c]).  Outputs: t_out [S][n_ch][n_E][2][2] complex (continuum T of  */
 /* the bin holding p(E)), delta_out [S][n_ch][n_E][3] deg, sigma_out [S][n_E] */
-/* mb.  OpenMP over (sample, channel).  Returns 0 or the first error code.    */
+/* mb.  mode: 0 free-bin average, 1 SWP-bin average, 2 point resolvent (T    */
+/* and phases at each p(E) directly).  OpenMP over (sample, channel).         */
+/* Returns 0 or the first error code.                                         */
 /* ------------------------------------------------------------------------- */
 int or_batch(int n_ch, const int *chdesc /* n_ch x 6 */, const int *nwp, const long *kb_off, const double *kb_all,
              int wp_kind, int n_terms, const long *vt_off, const double *Vt_all, int n_samples,
-             const double *coeffs, int n_E, const double *e_lab, double complex *t_out, double *delta_out,
+             const double *coeffs, int n_E, const double *e_lab, int mode, double complex *t_out, double *delta_out,
              double *sigma_out, int n_threads)
 {
+    if (mode == 2) /* point resolvent: T and phases at each energy, no interpolation */
+        return batch_point(n_ch, chdesc, nwp, kb_off, kb_all, wp_kind, n_terms, vt_off, Vt_all, n_samples, coeffs,
+                           n_E, e_lab, t_out, delta_out, sigma_out, n_threads);
     int err = 0;
     long maxN = 0;
     for (int c = 0; c < n_ch; ++c)
@@ -848,7 +996,7 @@ int or_batch(int n_ch, const int *chdesc /* n_ch x 6 */, const int *nwp, const l
             double complex *Tc = Tall + ((size_t)smp * n_ch + c) * maxN * 4;
             double *ph = phall + ((size_t)smp * n_ch + c) * maxN * 3;
             int rc = or_channel_solve(N, kb_all + kb_off[c], wp_kind, K, n_terms, Vt_all + vt_off[c],
-                                      coeffs + (size_t)smp * (n_terms - 1), Tc, ph, eps, NULL);
+                                      coeffs + (size_t)smp * (n_terms - 1), mode, Tc, ph, eps, NULL);
             if (rc < 0) {
 #ifdef _OPENMP
 #pragma omp critical(or_err)

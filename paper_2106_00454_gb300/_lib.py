@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libwpcd.so"
 EXPORTED = [
     "wpcd_create", "wpcd_destroy", "wpcd_strerror", "wpcd_set_option", "wpcd_sync", "wpcd_bytes_in_use",
     "wpcd_mesh", "wpcd_mesh_get", "wpcd_project", "wpcd_vset_get", "wpcd_vset_info", "wpcd_diag",
-    "wpcd_diag_status", "wpcd_eig_get", "wpcd_tmatrix", "wpcd_observables", "wpcd_solve", "wpcd_solve_host",
+    "wpcd_diag_status", "wpcd_eig_get", "wpcd_tmatrix", "wpcd_observables", "wpcd_observables_res", "wpcd_solve", "wpcd_solve_host",
     "wpcd_release", "wpcd_kernel_launches", "wpcd_profile", "wpcd_profile_read",
     "wpcd_channel_solve_noalloc", "wpcd_serve_start", "wpcd_serve_stop", "wpcd_submit", "wpcd_poll", "wpcd_wait",
     "wpcd_release_result", "wpcd_serve_stats", "wpcd_batched_dgemm", "wpcd_tuning",
@@ -62,6 +62,7 @@ _SIG = {
     "wpcd_eig_get": (_i, [_vp, _i, _i, _i, _vp, _vp]),
     "wpcd_tmatrix": (_i, [_vp, _i, _vp, _i, _i, _vp]),
     "wpcd_observables": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
+    "wpcd_observables_res": (_i, [_vp, _i, _vp, _i, _i, _vp, _vp]),
     "wpcd_solve": (_i, [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp, _vp, _vp]),
     "wpcd_solve_host": (_i, [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp, _vp, _vp]),
     "wpcd_release": (_i, [_vp, _i]),

@@ -16,7 +16,7 @@ from . import inputs as W
 WPCD_OK = 0
 WPCD_ERR_NOTREADY = -7
 PREC_FP64, PREC_MIXED = 0, 1
-AVG_FREE_BIN = 0
+AVG_FREE_BIN, AVG_SWP_INDEX, POINT = 0, 1, 2  # resolvent (wpcd_resolvent)
 EXEC_BATCHED, EXEC_PLAIN = 0, 1
 REFINE_TENSOR, REFINE_FP64 = 0, 1
 OPT_EXEC, OPT_REFINE, OPT_AUTOTUNE = 1, 2, 3
@@ -58,6 +58,7 @@ class Context:
         _ck(self.lib.wpcd_create(ctypes.byref(h), device, hbm_budget_bytes, ctypes.c_void_p(self.stream.cuda_stream)),
             "wpcd_create")
         self.h = h
+        self.refine_engine = REFINE_TENSOR  # the library's default
 
     def close(self):
         if self.h:
@@ -76,6 +77,7 @@ class Context:
 
     def set_refine_engine(self, engine: int):
         _ck(self.lib.wpcd_set_option(self.h, OPT_REFINE, engine), "wpcd_set_option")
+        self.refine_engine = engine
 
     def batched_dgemm(self, A, B, C, trans_a=False, engine=REFINE_TENSOR):
         """C[b] = op(A[b]) @ B[b] for (items, n, n) float64 device tensors."""
@@ -177,23 +179,28 @@ class Context:
         _ck(self.lib.wpcd_eig_get(self.h, eig_id, sample, channel, _ptr(eps), _ptr(C)), "wpcd_eig_get")
         return eps, C
 
-    def tmatrix(self, eig_id, e_lab, t_out):
-        _ck(self.lib.wpcd_tmatrix(self.h, eig_id, _ptr(e_lab), e_lab.numel(), AVG_FREE_BIN, _ptr(t_out)),
-            "wpcd_tmatrix")
+    def tmatrix(self, eig_id, e_lab, t_out, res=AVG_FREE_BIN):
+        _ck(self.lib.wpcd_tmatrix(self.h, eig_id, _ptr(e_lab), e_lab.numel(), res, _ptr(t_out)), "wpcd_tmatrix")
 
-    def observables(self, eig_id, e_lab, delta=None, sigma=None):
-        _ck(self.lib.wpcd_observables(self.h, eig_id, _ptr(e_lab), e_lab.numel(), _ptr(delta), _ptr(sigma)),
-            "wpcd_observables")
+    def observables(self, eig_id, e_lab, delta=None, sigma=None, res=AVG_FREE_BIN):
+        if res == AVG_FREE_BIN:
+            _ck(self.lib.wpcd_observables(self.h, eig_id, _ptr(e_lab), e_lab.numel(), _ptr(delta), _ptr(sigma)),
+                "wpcd_observables")
+        else:
+            _ck(self.lib.wpcd_observables_res(self.h, eig_id, _ptr(e_lab), e_lab.numel(), res, _ptr(delta),
+                                              _ptr(sigma)), "wpcd_observables_res")
 
-    def solve(self, vset_id, coeffs, n_samples, e_lab, t_out=None, delta=None, sigma=None, prec=PREC_FP64):
+    def solve(self, vset_id, coeffs, n_samples, e_lab, t_out=None, delta=None, sigma=None, prec=PREC_FP64,
+              res=AVG_FREE_BIN):
         _ck(self.lib.wpcd_solve(self.h, vset_id, _ptr(coeffs), n_samples, _ptr(e_lab), e_lab.numel(), prec,
-                                AVG_FREE_BIN, _ptr(t_out), _ptr(delta), _ptr(sigma)), "wpcd_solve")
+                                res, _ptr(t_out), _ptr(delta), _ptr(sigma)), "wpcd_solve")
 
-    def solve_host(self, vset_id, coeffs, n_samples, e_lab, t_out=None, delta=None, sigma=None, prec=PREC_FP64):
+    def solve_host(self, vset_id, coeffs, n_samples, e_lab, t_out=None, delta=None, sigma=None, prec=PREC_FP64,
+                   res=AVG_FREE_BIN):
         e_lab = np.ascontiguousarray(e_lab, dtype=np.float64)
         coeffs = None if coeffs is None else np.ascontiguousarray(coeffs, dtype=np.float64)
         _ck(self.lib.wpcd_solve_host(self.h, vset_id, _ptr(coeffs), n_samples, _ptr(e_lab), e_lab.size, prec,
-                                     AVG_FREE_BIN, _ptr(t_out), _ptr(delta), _ptr(sigma)), "wpcd_solve_host")
+                                     res, _ptr(t_out), _ptr(delta), _ptr(sigma)), "wpcd_solve_host")
 
 
 class ServedResult:

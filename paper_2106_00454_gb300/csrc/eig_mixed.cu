@@ -43,7 +43,7 @@ template <bool C_SMEM>
 __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *chans, const int *work_ch, int n_work_ch,
                                                                int sample0, int n_terms, const double *coeffs,
                                                                double *lam_s, double *X_s, float *Cf_s,
-                                                               int *status_all, int n_ch_total, int *err)
+                                                               double *H_s, int *status_all, int n_ch_total, int *err)
 {
     const int wc = blockIdx.x % n_work_ch;
     const int smp = sample0 + blockIdx.x / n_work_ch;
@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
     float *C = C_SMEM ? Cs : Cg;
     const double *cf = coeffs ? coeffs + (size_t)smp * (n_terms - 1) : nullptr;
 
-    // ---- H in FP64, rounded to FP32
+    // ---- H in FP64, rounded to FP32; the FP64 H also goes to H_s for the refinement
+    double *Hg = H_s ? H_s + (size_t)blockIdx.x * n * n : nullptr;
     for (int e = tid; e < n * n; e += nt) {
         int i = e / n, j = e - i * n;
         if (i > j) continue;
@@ -84,6 +85,10 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
         for (int a = 1; a < n_terms; ++a) v = fma(cf[a - 1], ch.V[(size_t)a * n * n + e], v);
         if (i == j) v += ch.h0[i % N];
         A[pk(i, j)] = (float)v;
+        if (Hg) {
+            Hg[e] = v;
+            Hg[(size_t)j * n + i] = v;
+        }
     }
     for (int e = tid; e < n * n; e += nt) {
         int i = e / n, j = e - i * n;
@@ -187,7 +192,8 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
 
 cudaError_t launch_jacobi_mixed(const ChanDev *chans_dev, const int *work_ch_dev, int n_work_ch, int n_samples,
                                 int sample0, int n_terms, const double *coeffs, int n, double *lam_s, double *X_s,
-                                float *Cf_s, int *status_all, int n_ch_total, int *err, cudaStream_t st, int threads)
+                                float *Cf_s, double *H_s, int *status_all, int n_ch_total, int *err, cudaStream_t st,
+                                int threads)
 {
     if (threads < 32 || threads > kMixMaxThreads || (threads & 31)) return cudaErrorInvalidValue;
     const bool cs = mix_smem(n, true) <= kMixSmemCap;
@@ -197,14 +203,16 @@ cudaError_t launch_jacobi_mixed(const ChanDev *chans_dev, const int *work_ch_dev
     if (cs) {
         cudaFuncSetAttribute(k_jacobi_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_jacobi_mixed<true><<<grid, threads, smem, st>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
-                                                              coeffs, lam_s, X_s, Cf_s, status_all, n_ch_total, err);
+                                                              coeffs, lam_s, X_s, Cf_s, H_s, status_all, n_ch_total, err);
     } else {
         cudaFuncSetAttribute(k_jacobi_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_jacobi_mixed<false><<<grid, threads, smem, st>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
-                                                               coeffs, lam_s, X_s, Cf_s, status_all, n_ch_total, err);
+                                                               coeffs, lam_s, X_s, Cf_s, H_s, status_all, n_ch_total, err);
     }
     return cudaGetLastError();
 }
+
+bool jacobi_mixed_c_in_smem(int n) { return mix_smem(n, true) <= kMixSmemCap; }
 
 int jacobi_mixed_occupancy(int n, int threads)
 {

@@ -149,7 +149,8 @@ extern "C" wpcd_status wpcd_channel_solve_noalloc(int n_wp, int mesh_kind, doubl
     CKN(launch_mesh(N, mesh_kind, alpha_fm, t, kmax_fm, Q, wp_kind, glx, glw, kb, kq, wq, h0, st));
     CKN(launch_jacobi_f64(chan, list, 1, n_samples, 0, n_terms, cf, n, eps, C, status, 1, status_dev, st));
     CKN(launch_plan(chan, 1, N, e_lab_dev, n_E, plan, status_dev, st));
-    CKN(launch_tbin(chan, 1, n_samples, n_terms, cf, eps, C, plan, N, tbin, phbin, status_dev, st));
+    CKN(launch_tbin(chan, 1, n_samples, n_terms, cf, eps, C, plan, N, n_E, tbin, phbin, status_dev, st, false,
+                    WPCD_AVG_FREE_BIN));
     if (t_out_dev) CKN(launch_gather_t(chan, 1, n_samples, n_E, N, plan, tbin, t_out_dev, st));
     if (delta_dev) CKN(launch_observables(chan, 1, n_samples, n_E, N, plan, phbin, delta_dev, nullptr, st));
 #undef CKN

@@ -13,7 +13,8 @@
 //     magnitude < 2^15; over k <= 256 terms the sum stays below 2^23, so the
 //     tensor core's FP32 accumulation is exact;
 //   * C_ij = 2^{e_i + f_j} sum_{p+q <= P-1} 2^{-8(p+q+2)+2} (A_p B_q)_ij,
-//     accumulated in FP64 (the 15 dropped pairs weigh at most 2^-62 each).
+//     accumulated exactly in int64 and rounded once to FP64 (the 15 dropped
+//     pairs weigh at most 2^-62 each).
 // The error is dominated by the 47-bit rounding, |dC_ij| <~ 2^-48 (2^{e_i}
 // sum_k |B_kj| + 2^{f_j} sum_k |A_ik|), ~4e-15 relative to the row and column
 // scales.  The slices are stored k-contiguous ([p][vector][k],
@@ -124,13 +125,65 @@ __device__ __forceinline__ void mma_bf16(float *c, unsigned a0, unsigned a1, uns
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// v 2^e as a double (round half away from zero), from the IEEE-754 layout with
+// integer operations only; FP64 arithmetic only where the result leaves the
+// normal range.
+__device__ __forceinline__ double i64_times_pow2(long long v, int e)
+{
+    if (v == 0) return 0.0;
+    unsigned long long m = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    int msb = 63 - __clzll((long long)m);
+    unsigned long long frac;
+    if (msb > 52) {
+        int sh = msb - 52;
+        m += 1ull << (sh - 1);  // m < 2^63: no overflow
+        if (m >> (msb + 1)) {   // the rounding carried into a new leading bit
+            ++msb;
+            ++sh;
+        }
+        frac = m >> sh;
+    } else {
+        frac = m << (52 - msb);
+    }
+    const int be = msb + e + 1023;
+    if (be < 1 || be > 2046) return ldexp((double)v, e);
+    const unsigned long long bits =
+        (v < 0 ? (1ull << 63) : 0ull) | ((unsigned long long)be << 52) | (frac & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// 16-byte global -> shared copy; src_bytes = 0 fills the 16 bytes with zeros.
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+constexpr int kOzStages = 3;                 // cp.async ring depth
+constexpr int kOzStageElems = 2 * 64 * kOzLd;  // A and B tiles of one step (bf16)
+
 // C[b] = A[b] B[b] from row slices of A and column slices of B.  64 x 64
-// output tile per CTA, 4 warps of 32 x 32.
+// output tile per CTA, 4 warps of 32 x 32.  The (digit pair, k-chunk) steps
+// run as one sequence through a 3-stage cp.async ring, so the loads of step
+// t + 2 overlap the tensor-core work of step t; fragments come from shared
+// memory through ldmatrix.
 __global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, const __nv_bfloat16 *A_s, const int *ea_all,
                                                  const __nv_bfloat16 *B_s, const int *eb_all, double *C_all)
 {
-    __shared__ __align__(16) __nv_bfloat16 As[64 * kOzLd];
-    __shared__ __align__(16) __nv_bfloat16 Bs[64 * kOzLd];
+    __shared__ __align__(128) __nv_bfloat16 ring[kOzStages * kOzStageElems];
     const int b = blockIdx.z;
     const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -138,95 +191,109 @@ __global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, const __nv_bfloa
     const int wr = (warp >> 1) * 32, wc = (warp & 1) * 32;
     const __nv_bfloat16 *Ab = A_s + (size_t)b * kOzP * n * Kp;
     const __nv_bfloat16 *Bb = B_s + (size_t)b * kOzP * n * Kp;
+    const int nk = Kp / kOzKC;                           // k-chunks per digit pair
+    const int n_steps = nk * (kOzP * (kOzP + 1) / 2);    // 21 pairs (p + q <= P - 1)
+    const unsigned ring_s = smem_u32(ring);
 
-    double acc[2][4][4];
+    // issue cursor: the (d, p, chunk) of the next step to load
+    int id = 0, ip = 0, ik = 0;
+    auto issue = [&](int stage) {
+        const int q = id - ip;
+        const __nv_bfloat16 *Ap = Ab + (size_t)ip * n * Kp;
+        const __nv_bfloat16 *Bq = Bb + (size_t)q * n * Kp;
+        const unsigned sA = ring_s + (unsigned)(stage * kOzStageElems) * 2u;
+        const unsigned sB = sA + 64u * kOzLd * 2u;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {  // 64 rows x 32 k of each operand: 256 16-byte pieces, 2 per thread
+            const int e = tid + u * 128;
+            const int r = e >> 2, kk = (e & 3) * 8;
+            const int ra = row0 + r < n ? row0 + r : n - 1, rb = col0 + r < n ? col0 + r : n - 1;
+            cp_async16(sA + (unsigned)(r * kOzLd + kk) * 2u, Ap + (size_t)ra * Kp + ik * kOzKC + kk,
+                       row0 + r < n ? 16 : 0);
+            cp_async16(sB + (unsigned)(r * kOzLd + kk) * 2u, Bq + (size_t)rb * Kp + ik * kOzKC + kk,
+                       col0 + r < n ? 16 : 0);
+        }
+        if (++ik == nk) {
+            ik = 0;
+            if (++ip > id) {
+                ip = 0;
+                ++id;
+            }
+        }
+    };
+
+    // v = sum over pairs of their sums times 2^{36-8d} (for d = 5 shifted down
+    // by 4 bits instead): C_ij = v 2^{e_i + f_j - 50}, exact up to those 4 bits.
+    long long acc[2][4][4];
+    float c32[2][4][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc[i][j][u] = 0.0;
+            for (int u = 0; u < 4; ++u) {
+                acc[i][j][u] = 0;
+                c32[i][j][u] = 0.f;
+            }
 
-    // Digit pairs grouped by d = p + q (common weight 2^{-8(d+2)+2}).  Each
-    // pair's FP32 sum over at most 256 k is an exact integer below 2^23; the
-    // group adds them as int32 (at most 6 pairs x 2 k-chunks: below 2^27) and
-    // reaches the FP64 accumulator once per group.
-    for (int d = 0; d < kOzP; ++d) {
-        int g[2][4][4];
+    // Digit pair (p, q) weighs 2^{-8(d+2)+2}, d = p + q.  Its FP32 sum over
+    // at most 256 k is an exact integer of magnitude at most 256 * 129 * 128
+    // < 2^23; it joins the int64 accumulator shifted by 36 - 8d (|v| < 2^62:
+    // at most 6 pairs x 2 k-blocks of 2^22 per d), with no FP64 arithmetic.
+    issue(0);
+    cp_async_commit();
+    if (n_steps > 1) issue(1);
+    cp_async_commit();
+    int cd = 0, cp = 0, ck = 0;  // compute cursor
+    for (int st = 0; st < n_steps; ++st) {
+        cp_async_wait1();  // step st has landed (only the newest group may be in flight)
+        __syncthreads();   // ... for every thread, and step st - 1's stage is free again
+        if (st + 2 < n_steps) issue((st + 2) % kOzStages);
+        cp_async_commit();
+        const unsigned sA = ring_s + (unsigned)((st % kOzStages) * kOzStageElems) * 2u;
+        const unsigned sB = sA + 64u * kOzLd * 2u;
 #pragma unroll
-        for (int i = 0; i < 2; ++i)
+        for (int ks = 0; ks < kOzKC; ks += 16) {
+            unsigned af[2][4], bf[4][2];
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int i = 0; i < 2; ++i) {  // rows wr + 16 i + (lane & 15), k ks + 8 (lane >> 4)
+                const int r = wr + i * 16 + (lane & 15), k = ks + 8 * (lane >> 4);
+                ldsm_x4(sA + (unsigned)(r * kOzLd + k) * 2u, af[i][0], af[i][1], af[i][2], af[i][3]);
+            }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) g[i][j][u] = 0;
-        for (int p = 0; p <= d; ++p) {
-            const int q = d - p;
-            const __nv_bfloat16 *Ap = Ab + (size_t)p * n * Kp;
-            const __nv_bfloat16 *Bq = Bb + (size_t)q * n * Kp;
-            float c32[2][4][4];
+            for (int jj = 0; jj < 2; ++jj) {  // columns wc + 16 jj + 8 (m >> 1) + (lane & 7), k ks + 8 (m & 1)
+                const int m = lane >> 3;
+                const int r = wc + jj * 16 + 8 * (m >> 1) + (lane & 7), k = ks + 8 * (m & 1);
+                ldsm_x4(sB + (unsigned)(r * kOzLd + k) * 2u, bf[2 * jj][0], bf[2 * jj][1], bf[2 * jj + 1][0],
+                        bf[2 * jj + 1][1]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    mma_bf16(c32[i][j], af[i][0], af[i][1], af[i][2], af[i][3], bf[j][0], bf[j][1]);
+        }
+        const int k_end = (ck + 1) * kOzKC;
+        if ((k_end % kOzKMax) == 0 || ck + 1 == nk) {  // keep every FP32 sum exact
+            const int sh = 36 - 8 * cd;                 // weight 2^{-8(d+2)+2} = 2^{sh-50}
 #pragma unroll
             for (int i = 0; i < 2; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) c32[i][j][u] = 0.f;
-            for (int k0 = 0; k0 < Kp; k0 += kOzKC) {
-                __syncthreads();
-                // 64 rows x 32 k of each operand: 256 16-byte pieces each, 2 per thread
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int e = tid + u * 128;
-                    const int r = e >> 2, kk = (e & 3) * 8;
-                    uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
-                    if (row0 + r < n) va = *reinterpret_cast<const uint4 *>(Ap + (size_t)(row0 + r) * Kp + k0 + kk);
-                    if (col0 + r < n) vb = *reinterpret_cast<const uint4 *>(Bq + (size_t)(col0 + r) * Kp + k0 + kk);
-                    *reinterpret_cast<uint4 *>(&As[r * kOzLd + kk]) = va;
-                    *reinterpret_cast<uint4 *>(&Bs[r * kOzLd + kk]) = vb;
-                }
-                __syncthreads();
-#pragma unroll
-                for (int ks = 0; ks < kOzKC; ks += 16) {
-                    unsigned af[2][4], bf[4][2];
-#pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        const __nv_bfloat16 *base = &As[(wr + i * 16 + g4) * kOzLd + ks + 2 * t];
-                        af[i][0] = ld_u32(base);
-                        af[i][1] = ld_u32(base + 8 * kOzLd);
-                        af[i][2] = ld_u32(base + 8);
-                        af[i][3] = ld_u32(base + 8 * kOzLd + 8);
+                    for (int u = 0; u < 4; ++u) {
+                        const int v = __float2int_rn(c32[i][j][u]);
+                        acc[i][j][u] += sh >= 0 ? ((long long)v << sh) : (long long)(v >> -sh);
+                        c32[i][j][u] = 0.f;
                     }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const __nv_bfloat16 *base = &Bs[(wc + j * 8 + g4) * kOzLd + ks + 2 * t];
-                        bf[j][0] = ld_u32(base);
-                        bf[j][1] = ld_u32(base + 8);
-                    }
-#pragma unroll
-                    for (int i = 0; i < 2; ++i)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            mma_bf16(c32[i][j], af[i][0], af[i][1], af[i][2], af[i][3], bf[j][0], bf[j][1]);
-                }
-                if (((k0 + kOzKC) % kOzKMax) == 0 || k0 + kOzKC >= Kp) {  // keep every FP32 sum exact
-#pragma unroll
-                    for (int i = 0; i < 2; ++i)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                g[i][j][u] += __float2int_rn(c32[i][j][u]);
-                                c32[i][j][u] = 0.f;
-                            }
-                }
+        }
+        if (++ck == nk) {
+            ck = 0;
+            if (++cp > cd) {
+                cp = 0;
+                ++cd;
             }
         }
-        const double scale = ldexp(1.0, -8 * (d + 2) + 2);  // digit weights 2^{-8(p+1)+1}
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) acc[i][j][u] = fma((double)g[i][j][u], scale, acc[i][j][u]);
     }
     const int *ea = ea_all + (size_t)b * n, *eb = eb_all + (size_t)b * n;
     double *C = C_all + (size_t)b * n * n;
@@ -238,31 +305,44 @@ __global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, const __nv_bfloa
             for (int u = 0; u < 4; ++u) {
                 const int r = row0 + wr + i * 16 + g4 + (u >= 2 ? 8 : 0);
                 const int c = col0 + wc + j * 8 + 2 * t + (u & 1);
-                if (r < n && c < n) C[(size_t)r * n + c] = ldexp(acc[i][j][u], ea[r] + eb[c]);
+                if (r < n && c < n) C[(size_t)r * n + c] = i64_times_pow2(acc[i][j][u], ea[r] + eb[c] - 50);
             }
 }
 
 // C = op(A) B for `items` n x n FP64 matrices (op(A) = A^T when ta), through
 // the slices.  Scratch: sa, sb hold oz_slice_elems(n) bf16 per item; ea, eb n ints per item.
+// Digit slices of the rows (cols = false) or columns (cols = true) of `items`
+// n x n matrices: S [items][P][n][Kp] bf16, e [items][n].
+cudaError_t launch_oz_split(int n, int items, bool cols, const double *M, __nv_bfloat16 *S, int *e, cudaStream_t st)
+{
+    const int Kp = oz_kpad(n);
+    if (cols) {
+        k_oz_exp<true><<<dim3((n + 127) / 128, items), 128, 0, st>>>(n, M, e);
+        k_oz_split_cols<<<dim3((n + 31) / 32, (Kp + 31) / 32, items), dim3(32, 8), 0, st>>>(n, Kp, M, e, S);
+    } else {
+        k_oz_exp<false><<<dim3((n + 7) / 8, items), 256, 0, st>>>(n, M, e);
+        k_oz_split_rows<<<dim3((Kp + 127) / 128, n, items), 128, 0, st>>>(n, Kp, M, e, S);
+    }
+    return cudaGetLastError();
+}
+
+// C = A B from the row slices of A and the column slices of B.
+cudaError_t launch_oz_gemm_slices(int n, int items, const __nv_bfloat16 *sa, const int *ea, const __nv_bfloat16 *sb,
+                                  const int *eb, double *C, cudaStream_t st)
+{
+    const int tiles = (n + 63) / 64;
+    k_oz_gemm<<<dim3(tiles, tiles, items), 128, 0, st>>>(n, oz_kpad(n), sa, ea, sb, eb, C);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_oz_gemm(int n, int items, bool ta, const double *A, const double *B, double *C,
                            __nv_bfloat16 *sa, __nv_bfloat16 *sb, int *ea, int *eb, cudaStream_t st)
 {
-    const int Kp = oz_kpad(n);
+    cudaError_t e;
     // rows of op(A): rows of A, or columns of A when transposed; columns of B
-    const dim3 gcol((n + 127) / 128, items), grow((n + 7) / 8, items);
-    const dim3 grows((Kp + 127) / 128, n, items), gtile((n + 31) / 32, (Kp + 31) / 32, items);
-    if (ta) {
-        k_oz_exp<true><<<gcol, 128, 0, st>>>(n, A, ea);
-        k_oz_split_cols<<<gtile, dim3(32, 8), 0, st>>>(n, Kp, A, ea, sa);
-    } else {
-        k_oz_exp<false><<<grow, 256, 0, st>>>(n, A, ea);
-        k_oz_split_rows<<<grows, 128, 0, st>>>(n, Kp, A, ea, sa);
-    }
-    k_oz_exp<true><<<gcol, 128, 0, st>>>(n, B, eb);
-    k_oz_split_cols<<<gtile, dim3(32, 8), 0, st>>>(n, Kp, B, eb, sb);
-    const int tiles = (n + 63) / 64;
-    k_oz_gemm<<<dim3(tiles, tiles, items), 128, 0, st>>>(n, Kp, sa, ea, sb, eb, C);
-    return cudaGetLastError();
+    if ((e = launch_oz_split(n, items, ta, A, sa, ea, st))) return e;
+    if ((e = launch_oz_split(n, items, true, B, sb, eb, st))) return e;
+    return launch_oz_gemm_slices(n, items, sa, ea, sb, eb, C, st);
 }
 
 }  // namespace wpcd

@@ -12,7 +12,8 @@
 //     X <- X (I + E),
 // which squares the eigenvector error.  After the last iteration every
 // eigenvalue is the FP64 Rayleigh quotient of its refined vector,
-// lambda_i = (X^T H X)_ii / (X^T X)_ii.  The four products are batched FP64
+// lambda_i = (X^T H X)_ii / (X^T X)_ii.  The FP64 H comes from the FP32 solve,
+// which forms it before rounding.  The four products are batched FP64
 // GEMMs over every (sample, channel) item of one chunk of a size bucket; the
 // working matrices of item b sit contiguously at b * n^2 in scratch buffers,
 // and the final sort writes the eigenpairs into the eigen-buffer layout
@@ -23,24 +24,6 @@
 #include "wpcd_internal.cuh"
 
 namespace wpcd {
-
-// H = diag(H0) + V0 + sum_a c_a V_a in FP64, full n x n.
-__global__ void k_assemble_h64(const ChanDev *chans, const int *work, int nw, int sample0, int n, int n_terms,
-                               const double *coeffs, double *H_all)
-{
-    const int b = blockIdx.y;
-    const int wc = b % nw, smp = sample0 + b / nw;
-    const ChanDev ch = chans[work[wc]];
-    double *H = H_all + (size_t)b * n * n;
-    const double *cf = coeffs ? coeffs + (size_t)smp * (n_terms - 1) : nullptr;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
-        double v = ch.V[e];
-        for (int a = 1; a < n_terms; ++a) v = fma(cf[a - 1], ch.V[(size_t)a * n * n + e], v);
-        const int i = e / n, j = e - i * n;
-        if (i == j) v += ch.h0[i % ch.N];
-        H[e] = v;
-    }
-}
 
 // Batched C = op(A) B (n x n, row-major), op(A) = A^T when TA.  64 x 64 output
 // tile per CTA, 16-deep k steps through shared memory, 4 x 4 outputs per thread.
@@ -110,18 +93,17 @@ __global__ void __launch_bounds__(256) k_bgemm64(int n, const double *A_all, con
 }
 
 // One CTA per item: lambda, the threshold delta, and I + E written over G.
-__global__ void __launch_bounds__(256) k_oa_update(int n, const double *H_all, const double *S_all, double *G_all,
-                                                   double *lam_all)
+__global__ void __launch_bounds__(256) k_oa_update(int n, const double *S_all, double *G_all, double *lam_all)
 {
     extern __shared__ double lam[];  // n
     __shared__ double red[32];
     const int b = blockIdx.x;
     const size_t off = (size_t)b * n * n;
-    const double *H = H_all + off, *S = S_all + off;
+    const double *S = S_all + off;
     double *G = G_all + off;
     for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = S[(size_t)i * n + i] / G[(size_t)i * n + i];
     __syncthreads();
-    double sd = 0.0, hh = 0.0, rr = 0.0;
+    double sd = 0.0, rr = 0.0;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, j = e - i * n;
         const double s = S[e] - (i == j ? lam[i] : 0.0);
@@ -140,7 +122,6 @@ __global__ void __launch_bounds__(256) k_oa_update(int n, const double *H_all, c
     __syncthreads();
     lmax = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lmax = fmax(lmax, red[w]);
-    (void)hh;
     const double delta = 2.0 * (sqrt(sd) + lmax * sqrt(rr));
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int i = e / n, j = e - i * n;
@@ -210,56 +191,78 @@ size_t sort_eig_smem(int n) { return (size_t)n * 8 + (size_t)n * 4; }
 size_t refine_scratch_per_item(int n, int engine)
 {
     size_t b = (size_t)5 * n * n * 8 + (size_t)n * 8;  // X, H, Y, W1, W2, lambda
-    if (engine == 0) b += 2 * oz_slice_elems(n) * 2 + (size_t)2 * n * 4 + 512;
+    if (engine == 0) b += 5 * oz_slice_elems(n) * 2 + (size_t)5 * n * 4 + 512;  // 5 digit-slice sets
     return b;
 }
 
 // Refine the eigenpairs of `items` = n_samples * nw items of one bucket chunk.
 // scratch: refine_scratch_per_item(n, engine) bytes per item, carved here.
-// Xs (first n^2 doubles of each item's block) holds the FP32-solve
-// eigenvectors as FP64 on entry.  iters must be even.
+// On entry Xs (the first n^2-double block of each item) holds the FP32-solve
+// eigenvectors as FP64 and H (the second block) the FP64 Hamiltonian, both
+// written by the FP32 solve.  iters must be even.
 cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_samples, int sample0, int n,
                           int n_terms, const double *coeffs, void *scratch, double *eps_all, double *X_all,
                           int iters, int engine, cudaStream_t st)
 {
+    (void)n_terms;
+    (void)coeffs;
     if (iters < 0 || (iters & 1)) return cudaErrorInvalidValue;
     const int items = n_samples * nw;
     const size_t nn = (size_t)items * n * n;
     double *Xs = static_cast<double *>(scratch);
     double *H = Xs + nn, *Y = H + nn, *W1 = Y + nn, *W2 = W1 + nn, *lam = W2 + nn;
-    // slices start on a 256-byte boundary (16-byte vector loads)
-    const uintptr_t sa_addr = (reinterpret_cast<uintptr_t>(lam + (size_t)items * n) + 255) & ~(uintptr_t)255;
-    __nv_bfloat16 *sa = reinterpret_cast<__nv_bfloat16 *>(sa_addr);
-    __nv_bfloat16 *sb = sa + (size_t)items * oz_slice_elems(n);
-    int *ea = reinterpret_cast<int *>(sb + (size_t)items * oz_slice_elems(n));
-    int *eb = ea + (size_t)items * n;
+    // digit slices start on a 256-byte boundary (16-byte vector loads)
+    const uintptr_t s0 = (reinterpret_cast<uintptr_t>(lam + (size_t)items * n) + 255) & ~(uintptr_t)255;
+    const size_t se = (size_t)items * oz_slice_elems(n);
+    __nv_bfloat16 *sH = reinterpret_cast<__nv_bfloat16 *>(s0);
+    __nv_bfloat16 *sXc = sH + se, *sYc = sXc + se, *sXr = sYc + se, *sEc = sXr + se;
+    int *eH = reinterpret_cast<int *>(sEc + se);
+    int *eXc = eH + (size_t)items * n, *eYc = eXc + (size_t)items * n, *eXr = eYc + (size_t)items * n;
+    int *eEc = eXr + (size_t)items * n;
     const int tiles = (n + kBM - 1) / kBM;
     const dim3 gg(tiles, tiles, items);
-    auto gemm = [&](bool ta, const double *A, const double *B, double *C) {
-        if (engine == 0) return launch_oz_gemm(n, items, ta, A, B, C, sa, sb, ea, eb, st);
-        if (ta) k_bgemm64<true><<<gg, 256, 0, st>>>(n, A, B, C);
-        else k_bgemm64<false><<<gg, 256, 0, st>>>(n, A, B, C);
-        return cudaGetLastError();
-    };
-    const int ab = (n * n + 255) / 256 < 64 ? (n * n + 255) / 256 : 64;
-    k_assemble_h64<<<dim3(ab, items), 256, 0, st>>>(chans, work, nw, sample0, n, n_terms, coeffs, H);
-    double *x = Xs, *xn = Y;
     cudaError_t e = cudaSuccess;
-    for (int it = 0; it < iters && e == cudaSuccess; ++it) {
-        if ((e = gemm(false, H, x, xn))) break;   // Y = H X
-        if ((e = gemm(true, x, xn, W1))) break;   // S = X^T Y
-        if ((e = gemm(true, x, x, W2))) break;    // G = X^T X
-        k_oa_update<<<items, 256, (size_t)n * 8, st>>>(n, H, W1, W2, lam);
-        if ((e = gemm(false, x, W2, xn))) break;  // X (I + E)
+#define CKR(x)                       \
+    do {                             \
+        if ((e = (x)) != cudaSuccess) \
+            return e;                \
+    } while (0)
+    double *x = Xs, *xn = Y;
+    if (engine == 0) CKR(launch_oz_split(n, items, false, H, sH, eH, st));  // rows of H, reused
+    for (int it = 0; it < iters; ++it) {
+        if (engine == 0) {
+            CKR(launch_oz_split(n, items, true, x, sXc, eXc, st));               // columns of X
+            CKR(launch_oz_gemm_slices(n, items, sH, eH, sXc, eXc, xn, st));       // Y = H X
+            CKR(launch_oz_split(n, items, true, xn, sYc, eYc, st));              // columns of Y
+            CKR(launch_oz_gemm_slices(n, items, sXc, eXc, sYc, eYc, W1, st));     // S = X^T Y
+            CKR(launch_oz_gemm_slices(n, items, sXc, eXc, sXc, eXc, W2, st));     // G = X^T X
+        } else {
+            k_bgemm64<false><<<gg, 256, 0, st>>>(n, H, x, xn);
+            k_bgemm64<true><<<gg, 256, 0, st>>>(n, x, xn, W1);
+            k_bgemm64<true><<<gg, 256, 0, st>>>(n, x, x, W2);
+        }
+        k_oa_update<<<items, 256, (size_t)n * 8, st>>>(n, W1, W2, lam);
+        if (engine == 0) {
+            CKR(launch_oz_split(n, items, false, x, sXr, eXr, st));              // rows of X
+            CKR(launch_oz_split(n, items, true, W2, sEc, eEc, st));              // columns of I + E
+            CKR(launch_oz_gemm_slices(n, items, sXr, eXr, sEc, eEc, xn, st));     // X (I + E)
+        } else {
+            k_bgemm64<false><<<gg, 256, 0, st>>>(n, x, W2, xn);
+        }
         double *t = x;
         x = xn;
         xn = t;
     }
-    if (e != cudaSuccess) return e;
-    if (iters > 0) {
-        if ((e = gemm(false, H, x, xn))) return e;  // Y = H X for the Rayleigh quotients
+    if (iters > 0) {  // Y = H X for the Rayleigh quotients
+        if (engine == 0) {
+            CKR(launch_oz_split(n, items, true, x, sXc, eXc, st));
+            CKR(launch_oz_gemm_slices(n, items, sH, eH, sXc, eXc, xn, st));
+        } else {
+            k_bgemm64<false><<<gg, 256, 0, st>>>(n, H, x, xn);
+        }
         k_rayleigh<<<items, 256, 0, st>>>(n, x, xn, lam);
     }
+#undef CKR
     k_sort_eig<<<items, 256, sort_eig_smem(n), st>>>(chans, work, nw, sample0, n, lam, Xs, eps_all, X_all);
     return cudaGetLastError();
 }

@@ -380,14 +380,14 @@ wpcd_status run_diag(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, const double *
                 return launch_jacobi_f64(e.cd_dev, work, nw, ns, smp0, v.n_terms, cf, n, e.eps, e.C, e.status, v.n_ch,
                                          X.err, X.stream, th);
             // the FP32 solve alone, into the start of the refinement scratch
-            const bool cs = jacobi_mixed_smem_bytes(n, true) <= 200 * 1024;
+            const bool cs = jacobi_mixed_c_in_smem(n);
             const size_t per = refine_scratch_per_item(n, c->refine_engine) + (cs ? 0 : (size_t)n * n * 4) + 256;
             if (ws_reserve(c, X, X.ws_ref, per * nw * ns)) return cudaErrorMemoryAllocation;
             unsigned char *base = static_cast<unsigned char *>(X.ws_ref.p);
             double *Xs = reinterpret_cast<double *>(base);
             return launch_jacobi_mixed(e.cd_dev, work, nw, ns, smp0, v.n_terms, cf, n, Xs + (size_t)5 * ns * nw * n * n,
                                        Xs, reinterpret_cast<float *>(base + refine_scratch_per_item(n, c->refine_engine) * nw * ns),
-                                       e.status, v.n_ch, X.err, X.stream, th);
+                                       Xs + (size_t)ns * nw * n * n, e.status, v.n_ch, X.err, X.stream, th);
         });
         if (threads < 0) return WPCD_ERR_CUDA;
         if (prec == WPCD_PREC_FP64) {
@@ -396,7 +396,7 @@ wpcd_status run_diag(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, const double *
                                  X.err, X.stream, threads));
             return WPCD_OK;
         }
-        const bool c_smem = jacobi_mixed_smem_bytes(n, true) <= 200 * 1024;
+        const bool c_smem = jacobi_mixed_c_in_smem(n);
         const size_t ref_item = refine_scratch_per_item(n, c->refine_engine);
         const size_t per_item = ref_item + (c_smem ? 0 : (size_t)n * n * 4) + 256;
         int chunk = (int)std::max<size_t>(1, kRefineScratchBytes / (per_item * nw));
@@ -405,14 +405,15 @@ wpcd_status run_diag(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, const double *
         if (st2) return st2;
         unsigned char *base = static_cast<unsigned char *>(X.ws_ref.p);
         double *Xs = reinterpret_cast<double *>(base);  // first block of the refinement scratch
-        double *lam = Xs + (size_t)5 * chunk * nw * n * n;
         float *Cf = reinterpret_cast<float *>(base + ref_item * nw * chunk);
         for (int s0 = 0; s0 < nsmp; s0 += chunk) {
             const int ns = std::min(chunk, nsmp - s0);
             {
                 Launch L(c, X, WPCD_PHASE_EIGEN);
-                CK(launch_jacobi_mixed(e.cd_dev, work, nw, ns, smp0 + s0, v.n_terms, cf, n, lam, Xs, Cf, e.status,
-                                       v.n_ch, X.err, X.stream, threads));
+                // the FP64 H goes to the second n^2 block of the refinement scratch (layout of launch_refine)
+                CK(launch_jacobi_mixed(e.cd_dev, work, nw, ns, smp0 + s0, v.n_terms, cf, n,
+                                       Xs + (size_t)5 * ns * nw * n * n, Xs, Cf, Xs + (size_t)ns * nw * n * n,
+                                       e.status, v.n_ch, X.err, X.stream, threads));
             }
             Launch L(c, X, WPCD_PHASE_REFINE);
             CK(launch_refine(e.cd_dev, work, nw, ns, smp0 + s0, n, v.n_terms, cf, base, e.eps, e.C, kRefineIters,
@@ -436,7 +437,7 @@ wpcd_status run_diag(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, const double *
 // n_E_s (device, per-sample list lengths) every sample has its own energy
 // list at e_lab + s * n_E; otherwise one list serves all samples.
 wpcd_status run_tbin(wpcd_ctx *c, Exec &X, VSetH &v, EigH &e, const double *e_lab, int n_E, const int *n_E_s,
-                     PlanDev &plan)
+                     PlanDev &plan, int res = WPCD_AVG_FREE_BIN)
 {
     const int nch = v.n_ch, maxN = v.maxN, S = e.n_samples;
     const int P = n_E_s ? S : 1;
@@ -444,8 +445,9 @@ wpcd_status run_tbin(wpcd_ctx *c, Exec &X, VSetH &v, EigH &e, const double *e_la
     const size_t ni = (size_t)P * (2 * (size_t)nch * n_E + nch + (size_t)nch * maxN);
     if ((st = ws_reserve(c, X, X.ws_plan_i, ni * sizeof(int)))) return st;
     if ((st = ws_reserve(c, X, X.ws_plan_d, (size_t)P * n_E * sizeof(double)))) return st;
-    if ((st = ws_reserve(c, X, X.ws_tbin, (size_t)S * nch * maxN * 8 * sizeof(double)))) return st;
-    if ((st = ws_reserve(c, X, X.ws_phbin, (size_t)S * nch * maxN * 3 * sizeof(double)))) return st;
+    const size_t stride = res == WPCD_POINT ? (size_t)n_E : (size_t)maxN;  // items per (sample, channel)
+    if ((st = ws_reserve(c, X, X.ws_tbin, (size_t)S * nch * stride * 8 * sizeof(double)))) return st;
+    if ((st = ws_reserve(c, X, X.ws_phbin, (size_t)S * nch * stride * 3 * sizeof(double)))) return st;
     int *pi = static_cast<int *>(X.ws_plan_i.p);
     plan.bin = pi;
     plan.brk = pi + (size_t)P * nch * n_E;
@@ -461,25 +463,37 @@ wpcd_status run_tbin(wpcd_ctx *c, Exec &X, VSetH &v, EigH &e, const double *e_la
     Launch L(c, X, WPCD_PHASE_TMATRIX);
     const double *cf = v.n_terms > 1 ? e.coeffs : nullptr;
     double *tb = static_cast<double *>(X.ws_tbin.p), *pb = static_cast<double *>(X.ws_phbin.p);
-    CK(launch_tbin(e.cd_dev, nch, S, v.n_terms, cf, e.eps, e.C, plan, maxN, tb, pb, X.err, X.stream));
+    CK(launch_tbin(e.cd_dev, nch, S, v.n_terms, cf, e.eps, e.C, plan, maxN, n_E, tb, pb, X.err, X.stream,
+                   e.prec == WPCD_PREC_MIXED, res));
     return WPCD_OK;
 }
 
 // T at the energies and/or phases + cross sections, after run_tbin.
 wpcd_status run_outputs(wpcd_ctx *c, Exec &X, VSetH &v, EigH &e, int n_E, PlanDev &plan, double *t_out,
-                        double *delta, double *sigma)
+                        double *delta, double *sigma, int res = WPCD_AVG_FREE_BIN)
 {
+    const bool direct = res == WPCD_POINT;  // values at the energies themselves
     if (t_out) {
         Launch L(c, X, WPCD_PHASE_GATHER);
         CK(launch_gather_t(e.cd_dev, v.n_ch, e.n_samples, n_E, v.maxN, plan, static_cast<double *>(X.ws_tbin.p),
-                           t_out, X.stream));
+                           t_out, X.stream, direct));
     }
     if (delta || sigma) {
         Launch L(c, X, WPCD_PHASE_OBSERVABLES);
         CK(launch_observables(e.cd_dev, v.n_ch, e.n_samples, n_E, v.maxN, plan, static_cast<double *>(X.ws_phbin.p),
-                              delta, sigma, X.stream));
+                              delta, sigma, X.stream, direct));
     }
     return WPCD_OK;
+}
+
+// A resolvent the vset supports: the SWP-bin average needs uncoupled channels.
+bool resolvent_ok(const VSetH &v, int res)
+{
+    if (res == WPCD_AVG_FREE_BIN || res == WPCD_POINT) return true;
+    if (res != WPCD_AVG_SWP_INDEX) return false;
+    for (int k = 0; k < v.n_ch; ++k)
+        if (v.cd[k].K != 1) return false;
+    return true;
 }
 
 wpcd_status check_energies(const double *e_lab, int n_E)
@@ -594,6 +608,7 @@ wpcd_status wpcd_sync(wpcd_ctx *c)
     switch (h) {
     case kDevOk: return WPCD_OK;
     case kDevEnergyOutside: return WPCD_ERR_ARG;
+    case kDevMode: return WPCD_ERR_ARG;
     case kDevNoConverge: return WPCD_ERR_NOCONVERGE;
     case kDevBadSize: return WPCD_ERR_CUDA;
     default: return WPCD_ERR_ARG;
@@ -879,28 +894,30 @@ wpcd_status wpcd_eig_get(wpcd_ctx *c, int eig_id, int sample, int channel, doubl
     return WPCD_OK;
 }
 
-static wpcd_status tmatrix_impl(wpcd_ctx *c, VSetH &v, EigH &e, const double *e_lab, int n_E, double *t_out,
-                                double *delta, double *sigma)
+static wpcd_status tmatrix_impl(wpcd_ctx *c, VSetH &v, EigH &e, const double *e_lab, int n_E, int res,
+                                double *t_out, double *delta, double *sigma)
 {
+    if (!resolvent_ok(v, res)) return WPCD_ERR_ARG;
     PlanDev plan{};
-    wpcd_status st = run_tbin(c, c->main, v, e, e_lab, n_E, nullptr, plan);
+    wpcd_status st = run_tbin(c, c->main, v, e, e_lab, n_E, nullptr, plan, res);
     if (st) return st;
-    return run_outputs(c, c->main, v, e, n_E, plan, t_out, delta, sigma);
+    return run_outputs(c, c->main, v, e, n_E, plan, t_out, delta, sigma, res);
 }
 
 wpcd_status wpcd_tmatrix(wpcd_ctx *c, int eig_id, const double *e_lab, int n_E, wpcd_resolvent res, double *t_out)
 {
-    if (!c || !t_out || res != WPCD_AVG_FREE_BIN || check_energies(e_lab, n_E)) return WPCD_ERR_ARG;
+    if (!c || !t_out || check_energies(e_lab, n_E)) return WPCD_ERR_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
     Handle *h = find(c, eig_id, kEig);
     if (!h) return WPCD_ERR_HANDLE;
     Handle *hv = find(c, h->eig->vset_id, kVSet);
     if (!hv) return WPCD_ERR_HANDLE;
     CK(cudaSetDevice(c->device));
-    return tmatrix_impl(c, *hv->vset, *h->eig, e_lab, n_E, t_out, nullptr, nullptr);
+    return tmatrix_impl(c, *hv->vset, *h->eig, e_lab, n_E, res, t_out, nullptr, nullptr);
 }
 
-wpcd_status wpcd_observables(wpcd_ctx *c, int eig_id, const double *e_lab, int n_E, double *delta, double *sigma)
+wpcd_status wpcd_observables_res(wpcd_ctx *c, int eig_id, const double *e_lab, int n_E, wpcd_resolvent res,
+                                 double *delta, double *sigma)
 {
     if (!c || check_energies(e_lab, n_E) || (!delta && !sigma)) return WPCD_ERR_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
@@ -909,24 +926,29 @@ wpcd_status wpcd_observables(wpcd_ctx *c, int eig_id, const double *e_lab, int n
     Handle *hv = find(c, h->eig->vset_id, kVSet);
     if (!hv) return WPCD_ERR_HANDLE;
     CK(cudaSetDevice(c->device));
-    return tmatrix_impl(c, *hv->vset, *h->eig, e_lab, n_E, nullptr, delta, sigma);
+    return tmatrix_impl(c, *hv->vset, *h->eig, e_lab, n_E, res, nullptr, delta, sigma);
+}
+
+wpcd_status wpcd_observables(wpcd_ctx *c, int eig_id, const double *e_lab, int n_E, double *delta, double *sigma)
+{
+    return wpcd_observables_res(c, eig_id, e_lab, n_E, WPCD_AVG_FREE_BIN, delta, sigma);
 }
 
 wpcd_status wpcd_solve(wpcd_ctx *c, int vset_id, const double *coeffs, int S, const double *e_lab, int n_E,
                        wpcd_precision prec, wpcd_resolvent res, double *t_out, double *delta, double *sigma)
 {
-    if (!c || S < 1 || (prec != WPCD_PREC_FP64 && prec != WPCD_PREC_MIXED) || res != WPCD_AVG_FREE_BIN ||
-        check_energies(e_lab, n_E))
+    if (!c || S < 1 || (prec != WPCD_PREC_FP64 && prec != WPCD_PREC_MIXED) || check_energies(e_lab, n_E))
         return WPCD_ERR_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
     Handle *hv = find(c, vset_id, kVSet);
     if (!hv) return WPCD_ERR_HANDLE;
     VSetH &v = *hv->vset;
     if (v.n_terms > 1 && !coeffs) return WPCD_ERR_ARG;
+    if (!resolvent_ok(v, res)) return WPCD_ERR_ARG;
     CK(cudaSetDevice(c->device));
     wpcd_status st = run_diag(c, c->main, v, vset_id, coeffs, S, prec, c->main.eig);
     if (st) return st;
-    return tmatrix_impl(c, v, c->main.eig, e_lab, n_E, t_out, delta, sigma);
+    return tmatrix_impl(c, v, c->main.eig, e_lab, n_E, res, t_out, delta, sigma);
 }
 
 wpcd_status wpcd_solve_host(wpcd_ctx *c, int vset_id, const double *coeffs_h, int S, const double *e_lab_h, int n_E,

@@ -74,50 +74,81 @@ cudaError_t launch_plan(const ChanDev *chans_dev, int n_ch, int maxN, const doub
 
 __device__ __forceinline__ double xlogabs(double d) { return d == 0.0 ? 0.0 : d * log(fabs(d)); }
 
+// Warp sum of v[0..NV); lane 0 writes it to red[warp * 6 + k].
 template <int NV>
-__device__ __forceinline__ void block_sum_vec(double *v, double *red /* [NV][32] */)
+__device__ __forceinline__ void warp_sum_to(double *v, double *red /* [32][6] */)
 {
 #pragma unroll
     for (int k = 0; k < NV; ++k)
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
     if ((threadIdx.x & 31) == 0)
 #pragma unroll
-        for (int k = 0; k < NV; ++k) red[k * 32 + w] = v[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double t = 0.0;
-        for (int q = 0; q < nw; ++q) t += red[k * 32 + q];
-        v[k] = t;
-    }
+        for (int k = 0; k < NV; ++k) red[(threadIdx.x >> 5) * 6 + k] = v[k];
 }
 
 // ---------------------------------------------------------------------------------------------
-// T at the needed bins.  One CTA per (sample, channel).
+// On-shell T.  One CTA per (sample, channel).
 //  - SWP boundaries (Eq. "pseudostate wave packet boundaries"): the positive
 //    eigenvalues of each branch give B_1 = 0, B_i = (e_{i-1}+e_i)/2,
 //    B_{m+1} = e_m + (B_m - B_{m-1})/2.  Coupled channels: the positive
 //    eigenvalues, sorted, are dealt to the two branches alternately from the
 //    top (largest -> branch 1).
-//  - for each needed free bin i: the rows (a, i) of V (rebuilt from the terms
-//    and the sample's coefficients), R = V_rows C, the resolvent averaged
-//    over the free bin [E_i, E_{i+1}]
-//      gbar_s = [X(Eb,B_s) - X(Ea,B_s) - X(Eb,B_s+1) + X(Ea,B_s+1)]/(dE dB)
-//               - i pi |[Ea,Eb] ^ [B_s,B_s+1]| / (dE dB),   X(a,b) = (a-b) ln|a-b|,
-//    or ln((Eb - e_b)/(Ea - e_b))/dE for a bound state e_b < 0, and
-//      T_ab = V_(a,i),(b,i) + sum_s R_as gbar_s R_bs.
-//  - continuum T at q = the bin midpoint: T f(q)^2 / (N_i q^2); S = 1 - 2 pi i
-//    mu q T; phases (Stapp for coupled channels).
-// tbin: [S][n_ch][maxN][K][K] complex (8 doubles per bin); phbin: [S][n_ch][maxN][3].
+//  - for each item (a needed free bin i, or a requested energy E in free bin i):
+//    the VC rows R_as = sum_j V_(a,i),j C_js and the resolvent
+//      MODE 0 (free-bin average, App. B with the sign of W corrected): over
+//        [Ea, Eb] = [E_i, E_{i+1}],
+//        gbar_s = [X(Eb,B_s) - X(Ea,B_s) - X(Eb,B_s+1) + X(Ea,B_s+1)]/(dE dB)
+//                 - i pi |[Ea,Eb] ^ [B_s,B_s+1]| / (dE dB),  X(a,b) = (a-b) ln|a-b|,
+//        or ln((Eb - e_b)/(Ea - e_b))/dE for a bound state e_b < 0;
+//      MODE 1 (SWP-bin average, App. B as printed): the same over SWP bin i,
+//        [Ea, Eb] = [B_i, B_{i+1}] (uncoupled channels without bound states);
+//      MODE 2 (point resolvent, App. B): at E itself,
+//        g_s = [ln|(E - B_s)/(E - B_s+1)| - i pi 1{E in [B_s, B_s+1]}] / dB,
+//        or 1/(E - e_b);
+//    then T_ab = V_(a,i),(b,i) + sum_s R_as g_s R_bs.
+//  - continuum T: T f(q)^2 / (N_i q^2) at q = the bin midpoint (modes 0, 1)
+//    or q = p(E) (mode 2); S = 1 - 2 pi i mu q T; phases (Stapp for coupled
+//    channels).
+// Averaged modes visit the needed bins in ascending order, so the X(E_{i+1}, B)
+// of one bin are the X(E_i, B) of the next whenever the bins are adjacent.
+// VCID: the VC rows from the eigen-equation.  H0 is diagonal in the free
+// packet basis, so V C = H C - H0 C = C diag(e) - H0 C, i.e.
+//     R_as = C_(a,i),s (e_s - h0_i),
+// exact for exact eigenpairs; its error is the eigen residual (~u ||H||
+// absolute).  Used on the mixed path, whose eigenpairs are refined to FP64
+// residuals; the FP64 path keeps the explicit products (their error scales with
+// ||V|| rather than ||H||, which holds the relative accuracy of small T).
+// Output, 8 doubles (complex 2 x 2) and 3 phases per item: modes 0, 1 at
+// [S][n_ch][stride = maxN][bin], mode 2 at [S][n_ch][stride = n_E][energy].
 // ---------------------------------------------------------------------------------------------
-// TC: eigenvector type (double on the FP64 path; float on the mixed path, where
-// the VC rows are accumulated in FP32 and everything after them stays FP64).
-template <typename TC>
-__global__ void __launch_bounds__(kTThreads) k_tbin(const ChanDev *chans, int n_ch, int n_terms, const double *coeffs,
-                                                    const double *eps_all, const TC *C_all, PlanDev plan, int maxN,
-                                                    double *tbin, double *phbin, int *err)
+__device__ __forceinline__ void phases_of_T(int K, double q, const double *T, double *po)
+{
+    // S = 1 - 2 pi i mu q T
+    const double g = 2.0 * kPi * kMu * q;
+    const double deg = 180.0 / kPi;
+    if (K == 1) {
+        const double sre = 1.0 + g * T[1], sim = -g * T[0];
+        po[0] = 0.5 * atan2(sim, sre) * deg;
+        po[1] = 0.0;
+        po[2] = 0.0;
+    } else {
+        const double s11r = 1.0 + g * T[1], s11i = -g * T[0];
+        const double s22r = 1.0 + g * T[7], s22i = -g * T[6];
+        const double s12r = g * T[3], s12i = -g * T[2];
+        const double dm = 0.5 * atan2(s11i, s11r), dp = 0.5 * atan2(s22i, s22r);
+        const double ph = dm + dp;
+        double x = s12i * cos(ph) - s12r * sin(ph);  // Re(-i S12 e^{-i ph})
+        x = x > 1.0 ? 1.0 : (x < -1.0 ? -1.0 : x);
+        po[0] = dm * deg;
+        po[1] = dp * deg;
+        po[2] = 0.5 * asin(x) * deg;
+    }
+}
+
+template <bool VCID, int MODE>
+__global__ void __launch_bounds__(kTThreads) k_tmat(const ChanDev *chans, int n_ch, int n_terms, const double *coeffs,
+                                                    const double *eps_all, const double *C_all, PlanDev plan,
+                                                    int n_E, int stride, double *tout, double *phout, int *err)
 {
     const int c = blockIdx.x % n_ch, smp = blockIdx.x / n_ch;
     const ChanDev ch = chans[c];
@@ -128,20 +159,27 @@ __global__ void __launch_bounds__(kTThreads) k_tbin(const ChanDev *chans, int n_
         return;
     }
     extern __shared__ double sm[];
-    double *eps = sm;              // n
-    double *Eb = eps + n;          // 2 x n   branch members
-    double *Bb = Eb + 2 * n;       // 2 x (n+1) branch boundaries
-    double *lo = Bb + 2 * (n + 1); // n  lower SWP boundary of eigenvalue s
-    double *hi = lo + n;           // n  upper
-    double *vrow = hi + n;         // K x n
-    double *R = vrow + 2 * n;      // K x n
-    double *red = R + 2 * n;       // 6 x 32
+    double *eps = sm;               // n
+    double *Eb = eps + n;           // 2 x n   branch members
+    double *Bb = Eb + 2 * n;        // 2 x (n+1) branch boundaries
+    double *lo = Bb + 2 * (n + 1);  // n  lower SWP boundary of eigenvalue s
+    double *hi = lo + n;            // n  upper
+    double *idB = hi + n;           // n  1 / (hi - lo)
+    double *XA = idB + n;           // n+4  D(B) = X(E_{i+1}, B) - X(E_i, B) per boundary slot (averaged modes)
+    double *XB = XA + n + 4;        // n+4  X(E_{i+1}, B)
+    double *vrow = XB + n + 4;      // K x n
+    double *R = vrow + 2 * n;       // K x n
+    double *red = R + 2 * n;        // 6 x 32
+    double *vd = red + 6 * 32;      // K x K diagonal V entries
     __shared__ int s_nb, s_bad;
 
     const double *eg = eps_all + ch.eps_off + (size_t)smp * n;
-    const TC *C = C_all + ch.c_off + (size_t)smp * n * n;
-    TC *vrowc = reinterpret_cast<TC *>(red + 6 * 32);  // K x n copy of the V rows in the accumulation type
+    const double *C = C_all + ch.c_off + (size_t)smp * n * n;
     const double *cf = coeffs ? coeffs + (size_t)smp * (n_terms - 1) : nullptr;
+    const int ps = plan_of(plan, smp);
+    const size_t pc = (size_t)ps * n_ch + c;
+    const int cnt = MODE == 2 ? plan_nE(plan, ps, n_E) : plan.cnt[pc];
+    const size_t obase = ((size_t)smp * n_ch + c) * stride;
 
     if (tid == 0) { s_nb = 0; s_bad = 0; }
     for (int s = tid; s < n; s += nt) eps[s] = eg[s];
@@ -150,6 +188,15 @@ __global__ void __launch_bounds__(kTThreads) k_tbin(const ChanDev *chans, int n_
         if (eps[s] < 0.0 && (s == n - 1 || !(eps[s + 1] < 0.0))) s_nb = s + 1;
     __syncthreads();
     const int nb = s_nb, P = n - nb;
+    if (MODE == 1 && (K != 1 || nb != 0)) {  // SWP-bin averaging is defined for these only
+        for (int ii = tid; ii < cnt; ii += nt) {
+            const int i = plan.list[pc * stride + ii];
+            for (int k = 0; k < 8; ++k) tout[(obase + i) * 8 + k] = __longlong_as_double(0x7ff8000000000000ll);
+            for (int k = 0; k < 3; ++k) phout[(obase + i) * 3 + k] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+        if (tid == 0) record_error(err, kDevMode);
+        return;
+    }
     int mcount[2];
     mcount[0] = (K == 2) ? P / 2 : P;
     mcount[1] = (K == 2) ? (P + 1) / 2 : 0;
@@ -188,139 +235,231 @@ __global__ void __launch_bounds__(kTThreads) k_tbin(const ChanDev *chans, int n_
         const int pos = (K == 2) ? d / 2 : d;
         lo[s] = Bb[b * (n + 1) + pos];
         hi[s] = Bb[b * (n + 1) + pos + 1];
+        idB[s] = 1.0 / (hi[s] - lo[s]);
     }
     __syncthreads();
 
-    const size_t pc = (size_t)plan_of(plan, smp) * n_ch + c;
-    const int cnt = plan.cnt[pc];
-    const size_t obase = ((size_t)smp * n_ch + c) * maxN;
+    const int dstride = (K == 2) ? (n >> 1) + 2 : n + 1;  // boundary slots per branch (K * dstride <= n + 4)
+    int prev = -2;                                          // bin whose upper-edge X values sit in XB
     for (int ii = 0; ii < cnt; ++ii) {
-        const int i = plan.list[pc * maxN + ii];
-        // rows (a, i) of V = V0 + sum_a c_a V_a
-        for (int e = tid; e < K * n; e += nt) {
-            const int a = e / n, jj = e - a * n;
-            const size_t off = (size_t)(a * N + i) * n + jj;
-            double v = ch.V[off];
-            for (int t = 1; t < n_terms; ++t) v = fma(cf[t - 1], ch.V[(size_t)t * n * n + off], v);
-            vrow[a * n + jj] = v;
-            vrowc[a * n + jj] = (TC)v;
+        int i;
+        double Ea = 0.0, Ebn = 0.0, E = 0.0, p = 0.0;
+        if (MODE == 2) {
+            i = plan.bin[pc * n_E + ii];
+            p = plan.pE[(size_t)ps * n_E + ii];
+            E = p * p / (2.0 * kMu);
+        } else {
+            i = plan.list[pc * stride + ii];
+            if (MODE == 1) {
+                Ea = Bb[i];
+                Ebn = Bb[i + 1];
+            } else {
+                Ea = ch.kb[i] * ch.kb[i] / (2.0 * kMu);
+                Ebn = ch.kb[i + 1] * ch.kb[i + 1] / (2.0 * kMu);
+            }
         }
-        __syncthreads();
-        // R = V_rows C
-        for (int e = tid; e < K * n; e += nt) {
-            const int a = e / n, s = e - a * n;
-            const TC *vr = vrowc + a * n;
-            TC acc = 0;
-            for (int j = 0; j < n; ++j) acc = fma(vr[j], C[(size_t)j * n + s], acc);
-            R[a * n + s] = (double)acc;
+        // this bin's eigenvector rows, first element per thread issued early so
+        // that the load overlaps the logarithms below
+        const double *C0 = C + (size_t)i * n, *C1 = C + (size_t)(N + i) * n;
+        double c0pre = 0.0, c1pre = 0.0;
+        if (VCID && tid < n) {
+            c0pre = C0[tid];
+            if (K == 2) c1pre = C1[tid];
         }
-        __syncthreads();
-        const double Ea = ch.kb[i] * ch.kb[i] / (2.0 * kMu), Ebn = ch.kb[i + 1] * ch.kb[i + 1] / (2.0 * kMu);
-        const double dE = Ebn - Ea;
-        // D(B) = X(Eb, B) - X(Ea, B) once per SWP boundary of each branch (the
-        // branch-member array is free by now); state s then needs D(B_s) - D(B_s+1)
-        const int dstride = (K == 2) ? (n >> 1) + 2 : n + 1;
-        double *Dv = Eb;
-        for (int e = tid; e < K * dstride; e += nt) {
-            const int b = e / dstride, pos = e - b * dstride;
-            if (pos <= mcount[b]) {
-                const double B = Bb[b * (n + 1) + pos];
-                Dv[e] = xlogabs(Ebn - B) - xlogabs(Ea - B);
+        if (MODE != 2) {
+            const bool reuse = (i == prev + 1);
+            if (reuse) {  // the previous upper edge is this lower edge
+                double *t = XA;
+                XA = XB;
+                XB = t;
+            }
+            // XB = X(E_{i+1}, B); XA becomes D(B) = X(E_{i+1}, B) - X(E_i, B) (its
+            // X(E_i, B) is either the previous bin's XB or computed here)
+            for (int e = tid; e < K * dstride; e += nt) {
+                const int b = e / dstride, pos = e - b * dstride;
+                if (pos <= mcount[b]) {
+                    const double B = Bb[b * (n + 1) + pos];
+                    const double xb = xlogabs(Ebn - B);
+                    XB[e] = xb;
+                    XA[e] = xb - (reuse ? XA[e] : xlogabs(Ea - B));
+                }
+            }
+        }
+        if (VCID) {
+            // the diagonal entries V_(a,i),(b,i) of V = V0 + sum_a c_a V_a
+            if (tid < K * K) {
+                const int a = tid / K, bb = tid - a * K;
+                const size_t off = (size_t)(a * N + i) * n + bb * N + i;
+                double v = ch.V[off];
+                for (int t = 1; t < n_terms; ++t) v = fma(cf[t - 1], ch.V[(size_t)t * n * n + off], v);
+                vd[tid] = v;
+            }
+        } else {
+            // rows (a, i) of V, then R = V_rows C
+            for (int e = tid; e < K * n; e += nt) {
+                const int a = e / n, jj = e - a * n;
+                const size_t off = (size_t)(a * N + i) * n + jj;
+                double v = ch.V[off];
+                for (int t = 1; t < n_terms; ++t) v = fma(cf[t - 1], ch.V[(size_t)t * n * n + off], v);
+                vrow[a * n + jj] = v;
+            }
+            __syncthreads();
+            for (int e = tid; e < K * n; e += nt) {
+                const int a = e / n, s = e - a * n;
+                const double *vr = vrow + a * n;
+                double acc = 0.0;
+                for (int j = 0; j < n; ++j) acc = fma(vr[j], C[(size_t)j * n + s], acc);
+                R[a * n + s] = acc;
             }
         }
         __syncthreads();
+        // thread 0 keeps the diagonal V entries in registers: the next item rewrites them
+        double v00 = 0.0, v01 = 0.0, v10 = 0.0, v11 = 0.0;
+        if (tid == 0) {
+            if (VCID) {
+                v00 = vd[0];
+                if (K == 2) { v01 = vd[1]; v10 = vd[2]; v11 = vd[3]; }
+            } else {
+                v00 = vrow[i];
+                if (K == 2) { v01 = vrow[N + i]; v10 = vrow[n + i]; v11 = vrow[n + N + i]; }
+            }
+        }
+        const double idE = MODE == 2 ? 0.0 : 1.0 / (Ebn - Ea);
+        const double h0i = VCID ? ch.h0[i] : 0.0;
         double acc[6] = {0, 0, 0, 0, 0, 0};  // (00 re, im), (01 re, im), (11 re, im)
         for (int s = tid; s < n; s += nt) {
-            double gre, gim;
+            double gre, gim = 0.0;
             if (s < nb) {
-                gre = log((Ebn - eps[s]) / (Ea - eps[s])) / dE;
-                gim = 0.0;
+                gre = MODE == 2 ? 1.0 / (E - eps[s]) : log((Ebn - eps[s]) / (Ea - eps[s])) * idE;
             } else {
-                const double b0 = lo[s], b1 = hi[s], dB = b1 - b0;
                 const int d = s - nb;
                 const int b = (K == 2) ? (((n - 1 - s) & 1) == 0 ? 1 : 0) : 0;
-                const int pos = (K == 2) ? d / 2 : d;
-                const double num = Dv[b * dstride + pos] - Dv[b * dstride + pos + 1];
-                gre = num / (dE * dB);
-                const double l = Ea > b0 ? Ea : b0, h = Ebn < b1 ? Ebn : b1;
-                gim = (h > l) ? -kPi * (h - l) / (dE * dB) : 0.0;
+                const int q = b * dstride + ((K == 2) ? d / 2 : d);
+                if (MODE == 2) {  // the log of the ratio: no cancellation far from the bin
+                    gre = log(fabs((E - lo[s]) / (E - hi[s]))) * idB[s];
+                    if (E >= lo[s] && E <= hi[s]) gim = -kPi * idB[s];
+                } else {
+                    const double w = idB[s] * idE;  // 1 / (dE dB)
+                    gre = (XA[q] - XA[q + 1]) * w;  // D(B_s) - D(B_s+1)
+                    const double l = Ea > lo[s] ? Ea : lo[s], h = Ebn < hi[s] ? Ebn : hi[s];
+                    if (h > l) gim = -kPi * (h - l) * w;
+                }
             }
-            const double r0 = R[s];
-            acc[0] = fma(r0 * r0, gre, acc[0]);
-            acc[1] = fma(r0 * r0, gim, acc[1]);
+            double r0, r1 = 0.0;
+            if (VCID) {
+                const double de = eps[s] - h0i;
+                r0 = (s == tid ? c0pre : C0[s]) * de;
+                if (K == 2) r1 = (s == tid ? c1pre : C1[s]) * de;
+            } else {
+                r0 = R[s];
+                if (K == 2) r1 = R[n + s];
+            }
+            const double r00 = r0 * r0;
+            acc[0] = fma(r00, gre, acc[0]);
             if (K == 2) {
-                const double r1 = R[n + s];
                 acc[2] = fma(r0 * r1, gre, acc[2]);
-                acc[3] = fma(r0 * r1, gim, acc[3]);
                 acc[4] = fma(r1 * r1, gre, acc[4]);
-                acc[5] = fma(r1 * r1, gim, acc[5]);
+            }
+            if (gim != 0.0) {  // only the few states whose SWP bin overlaps the energy (range)
+                acc[1] = fma(r00, gim, acc[1]);
+                if (K == 2) {
+                    acc[3] = fma(r0 * r1, gim, acc[3]);
+                    acc[5] = fma(r1 * r1, gim, acc[5]);
+                }
             }
         }
-        block_sum_vec<6>(acc, red);
+        // warp sums of the warps that hold states; thread 0 adds them up
+        const int nwa = min((int)(nt >> 5), (n + 31) >> 5);
+        if ((tid >> 5) < nwa) {
+            if (K == 2) warp_sum_to<6>(acc, red);
+            else warp_sum_to<2>(acc, red);
+        }
+        __syncthreads();
+        prev = i;
         if (tid == 0) {
-            const double kbar = 0.5 * (ch.kb[i] + ch.kb[i + 1]);
-            const double Ni = ch.wp_kind == 0 ? (ch.kb[i + 1] - ch.kb[i]) : dE;
-            const double f2 = ch.wp_kind == 0 ? 1.0 : kbar / kMu;
-            const double fac = f2 / (Ni * kbar * kbar);
+            for (int k = 0; k < 6; ++k) {
+                double t = 0.0;
+                if (K == 2 || k < 2)
+                    for (int w = 0; w < nwa; ++w) t += red[w * 6 + k];
+                acc[k] = t;
+            }
+            const double q = MODE == 2 ? p : 0.5 * (ch.kb[i] + ch.kb[i + 1]);
+            const double Ni = ch.wp_kind == 0 ? (ch.kb[i + 1] - ch.kb[i])
+                                              : (ch.kb[i + 1] * ch.kb[i + 1] - ch.kb[i] * ch.kb[i]) / (2.0 * kMu);
+            const double f2 = ch.wp_kind == 0 ? 1.0 : q / kMu;
+            const double fac = f2 / (Ni * q * q);
             double T[8];  // complex 2x2, row-major
-            T[0] = fac * (vrow[i] + acc[0]);
+            T[0] = fac * (v00 + acc[0]);
             T[1] = fac * acc[1];
             if (K == 2) {
-                T[2] = fac * (vrow[N + i] + acc[2]);
+                T[2] = fac * (v01 + acc[2]);
                 T[3] = fac * acc[3];
-                T[4] = fac * (vrow[n + i] + acc[2]);
+                T[4] = fac * (v10 + acc[2]);
                 T[5] = fac * acc[3];
-                T[6] = fac * (vrow[n + N + i] + acc[4]);
+                T[6] = fac * (v11 + acc[4]);
                 T[7] = fac * acc[5];
             } else {
                 T[2] = T[3] = T[4] = T[5] = T[6] = T[7] = 0.0;
             }
-            double *to = tbin + (obase + i) * 8;
+            double *to = tout + (obase + (MODE == 2 ? ii : i)) * 8;
             for (int k = 0; k < 8; ++k) to[k] = T[k];
-            // S = 1 - 2 pi i mu q T
-            const double g = 2.0 * kPi * kMu * kbar;
-            double *po = phbin + (obase + i) * 3;
-            const double deg = 180.0 / kPi;
-            if (K == 1) {
-                const double sre = 1.0 + g * T[1], sim = -g * T[0];
-                po[0] = 0.5 * atan2(sim, sre) * deg;
-                po[1] = 0.0;
-                po[2] = 0.0;
-            } else {
-                const double s11r = 1.0 + g * T[1], s11i = -g * T[0];
-                const double s22r = 1.0 + g * T[7], s22i = -g * T[6];
-                const double s12r = g * T[3], s12i = -g * T[2];
-                const double dm = 0.5 * atan2(s11i, s11r), dp = 0.5 * atan2(s22i, s22r);
-                const double ph = dm + dp;
-                double x = s12i * cos(ph) - s12r * sin(ph);  // Re(-i S12 e^{-i ph})
-                x = x > 1.0 ? 1.0 : (x < -1.0 ? -1.0 : x);
-                po[0] = dm * deg;
-                po[1] = dp * deg;
-                po[2] = 0.5 * asin(x) * deg;
-            }
         }
-        __syncthreads();
+        // no trailing barrier: the next item writes X, V, R and the warp sums only
+        // after its first barrier, which thread 0 reaches after reading them
+    }
+    // S and the phases of every item, one item per thread (their T were
+    // written above by thread 0 of this CTA)
+    __syncthreads();
+    for (int ii = tid; ii < cnt; ii += nt) {
+        const int slot = MODE == 2 ? ii : plan.list[pc * stride + ii];
+        const int i = MODE == 2 ? plan.bin[pc * n_E + ii] : slot;
+        const double q = MODE == 2 ? plan.pE[(size_t)ps * n_E + ii] : 0.5 * (ch.kb[i] + ch.kb[i + 1]);
+        phases_of_T(K, q, tout + (obase + slot) * 8, phout + (obase + slot) * 3);
     }
 }
 
 size_t tbin_smem_bytes(int nmax) { return tbin_smem_doubles(nmax) * sizeof(double); }
 
-cudaError_t launch_tbin(const ChanDev *chans_dev, int n_ch, int n_samples, int n_terms, const double *coeffs,
-                        const double *eps_all, const double *C_all, PlanDev plan, int maxN, double *tbin,
-                        double *phbin, int *err, cudaStream_t st)
+template <bool VCID, int MODE>
+static void launch_tmat_t(const ChanDev *chans_dev, int n_ch, int n_samples, int n_terms, const double *coeffs,
+                          const double *eps_all, const double *C_all, PlanDev plan, int n_E, int stride,
+                          size_t smem, double *tout, double *phout, int *err, cudaStream_t st)
 {
+    cudaFuncSetAttribute(k_tmat<VCID, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_tmat<VCID, MODE><<<(unsigned)(n_samples * n_ch), kTThreads, smem, st>>>(chans_dev, n_ch, n_terms, coeffs, eps_all,
+                                                                              C_all, plan, n_E, stride, tout, phout,
+                                                                              err);
+}
+
+cudaError_t launch_tbin(const ChanDev *chans_dev, int n_ch, int n_samples, int n_terms, const double *coeffs,
+                        const double *eps_all, const double *C_all, PlanDev plan, int maxN, int n_E, double *tout,
+                        double *phout, int *err, cudaStream_t st, bool vc_identity, int mode)
+{
+    if (mode < 0 || mode > 2) return cudaErrorInvalidValue;
     const size_t smem = tbin_smem_bytes(2 * maxN);
-    cudaFuncSetAttribute(k_tbin<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_tbin<double><<<(unsigned)(n_samples * n_ch), kTThreads, smem, st>>>(chans_dev, n_ch, n_terms, coeffs, eps_all,
-                                                                           C_all, plan, maxN, tbin, phbin, err);
+    const int stride = mode == 2 ? n_E : maxN;
+#define WPCD_TMAT(V, M) \
+    launch_tmat_t<V, M>(chans_dev, n_ch, n_samples, n_terms, coeffs, eps_all, C_all, plan, n_E, stride, smem, tout, phout, err, st)
+    if (vc_identity) {
+        if (mode == 0) WPCD_TMAT(true, 0);
+        else if (mode == 1) WPCD_TMAT(true, 1);
+        else WPCD_TMAT(true, 2);
+    } else {
+        if (mode == 0) WPCD_TMAT(false, 0);
+        else if (mode == 1) WPCD_TMAT(false, 1);
+        else WPCD_TMAT(false, 2);
+    }
+#undef WPCD_TMAT
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------------
-// T at the requested energies: the bin value of the bin holding p(E).
-// t_out: [S][n_ch][n_E][2][2] complex.
+// T at the requested energies: the value of the bin holding p(E) (averaged
+// resolvents, stride = maxN), or the energy's own value (point resolvent,
+// direct, stride = n_E).  t_out: [S][n_ch][n_E][2][2] complex.
 // ---------------------------------------------------------------------------------------------
-__global__ void k_gather_t(int n_ch, int n_samples, int n_E, int maxN, PlanDev plan, const double *tbin, double *t_out)
+__global__ void k_gather_t(int n_ch, int n_samples, int n_E, int stride, bool direct, PlanDev plan,
+                           const double *tbin, double *t_out)
 {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t total = (size_t)n_samples * n_ch * n_E;
@@ -330,8 +469,8 @@ __global__ void k_gather_t(int n_ch, int n_samples, int n_E, int maxN, PlanDev p
     const int c = (int)(sc % n_ch);
     const int ps = plan_of(plan, (int)(sc / n_ch));
     if (e >= plan_nE(plan, ps, n_E)) return;
-    const int bin = plan.bin[((size_t)ps * n_ch + c) * n_E + e];
-    const double *src = tbin + (sc * maxN + bin) * 8;
+    const int slot = direct ? e : plan.bin[((size_t)ps * n_ch + c) * n_E + e];
+    const double *src = tbin + (sc * stride + slot) * 8;
     double *dst = t_out + idx * 8;
     const double2 *s2 = reinterpret_cast<const double2 *>(src);
     double2 *d2 = reinterpret_cast<double2 *>(dst);
@@ -340,11 +479,12 @@ __global__ void k_gather_t(int n_ch, int n_samples, int n_E, int maxN, PlanDev p
 }
 
 cudaError_t launch_gather_t(const ChanDev *chans_dev, int n_ch, int n_samples, int n_E, int maxN, PlanDev plan,
-                            const double *tbin, double *t_out, cudaStream_t st)
+                            const double *tbin, double *t_out, cudaStream_t st, bool direct)
 {
     (void)chans_dev;
     const size_t total = (size_t)n_samples * n_ch * n_E;
-    k_gather_t<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n_ch, n_samples, n_E, maxN, plan, tbin, t_out);
+    k_gather_t<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n_ch, n_samples, n_E, direct ? n_E : maxN, direct,
+                                                                plan, tbin, t_out);
     return cudaGetLastError();
 }
 
@@ -352,9 +492,10 @@ cudaError_t launch_gather_t(const ChanDev *chans_dev, int n_ch, int n_samples, i
 // Phases interpolated linearly in p between the midpoints of the segment j,
 // j+1 (extended past the end midpoints), after moving delta_{j+1} by a
 // multiple of 180 deg to within 90 deg of delta_j; result mapped to
-// (-90, 90].  Total cross section sigma = pi/(2p^2) sum (2J+1) sum_l Re(1 -
-// S_ll) over the np channels (tz = 0), with S rebuilt from the interpolated
-// Stapp parameters.  One thread per (sample, energy).
+// (-90, 90]; with the point resolvent (direct) the phases at p(E) itself.
+// Total cross section sigma = pi/(2p^2) sum (2J+1) sum_l Re(1 - S_ll) over the
+// np channels (tz = 0), with S rebuilt from those Stapp parameters.  One
+// thread per (sample, energy).
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ double wrap90(double d)
 {
@@ -364,8 +505,8 @@ __device__ __forceinline__ double wrap90(double d)
     return d;
 }
 
-__global__ void k_observables(const ChanDev *chans, int n_ch, int n_samples, int n_E, int maxN, PlanDev plan,
-                              const double *phbin, double *delta, double *sigma)
+__global__ void k_observables(const ChanDev *chans, int n_ch, int n_samples, int n_E, int stride, bool direct,
+                              PlanDev plan, const double *phbin, double *delta, double *sigma)
 {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)n_samples * n_E) return;
@@ -378,24 +519,28 @@ __global__ void k_observables(const ChanDev *chans, int n_ch, int n_samples, int
     double acc = 0.0;
     for (int c = 0; c < n_ch; ++c) {
         const ChanDev ch = chans[c];
-        const int j = plan.brk[((size_t)ps * n_ch + c) * n_E + e];
-        const double q0 = 0.5 * (ch.kb[j] + ch.kb[j + 1]), q1 = 0.5 * (ch.kb[j + 1] + ch.kb[j + 2]);
-        const double w = (p - q0) / (q1 - q0);
-        const double *ph = phbin + (((size_t)smp * n_ch + c) * maxN) * 3;
+        const double *ph = phbin + (((size_t)smp * n_ch + c) * stride) * 3;
         double out[3];
-        const int ncomp = ch.K == 2 ? 2 : 1;
-        for (int k = 0; k < ncomp; ++k) {
-            const double d0 = ph[3 * j + k];
-            double d1 = ph[3 * (j + 1) + k];
-            d1 += 180.0 * round((d0 - d1) / 180.0);
-            out[k] = wrap90(d0 + w * (d1 - d0));
-        }
-        if (ch.K == 2) {
-            const double e0 = ph[3 * j + 2], e1 = ph[3 * (j + 1) + 2];
-            out[2] = e0 + w * (e1 - e0);
+        if (direct) {
+            for (int k = 0; k < 3; ++k) out[k] = ph[3 * e + k];
         } else {
-            out[1] = 0.0;
-            out[2] = 0.0;
+            const int j = plan.brk[((size_t)ps * n_ch + c) * n_E + e];
+            const double q0 = 0.5 * (ch.kb[j] + ch.kb[j + 1]), q1 = 0.5 * (ch.kb[j + 1] + ch.kb[j + 2]);
+            const double w = (p - q0) / (q1 - q0);
+            const int ncomp = ch.K == 2 ? 2 : 1;
+            for (int k = 0; k < ncomp; ++k) {
+                const double d0 = ph[3 * j + k];
+                double d1 = ph[3 * (j + 1) + k];
+                d1 += 180.0 * round((d0 - d1) / 180.0);
+                out[k] = wrap90(d0 + w * (d1 - d0));
+            }
+            if (ch.K == 2) {
+                const double e0 = ph[3 * j + 2], e1 = ph[3 * (j + 1) + 2];
+                out[2] = e0 + w * (e1 - e0);
+            } else {
+                out[1] = 0.0;
+                out[2] = 0.0;
+            }
         }
         if (delta) {
             double *d = delta + (((size_t)smp * n_ch + c) * n_E + e) * 3;
@@ -417,11 +562,12 @@ __global__ void k_observables(const ChanDev *chans, int n_ch, int n_samples, int
 }
 
 cudaError_t launch_observables(const ChanDev *chans_dev, int n_ch, int n_samples, int n_E, int maxN, PlanDev plan,
-                               const double *phbin, double *delta, double *sigma, cudaStream_t st)
+                               const double *phbin, double *delta, double *sigma, cudaStream_t st, bool direct)
 {
     const size_t total = (size_t)n_samples * n_E;
-    k_observables<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(chans_dev, n_ch, n_samples, n_E, maxN, plan, phbin,
-                                                                    delta, sigma);
+    k_observables<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(chans_dev, n_ch, n_samples, n_E,
+                                                                    direct ? n_E : maxN, direct, plan, phbin, delta,
+                                                                    sigma);
     return cudaGetLastError();
 }
 

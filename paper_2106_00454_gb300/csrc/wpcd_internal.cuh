@@ -26,7 +26,14 @@ constexpr int kYukParams = 19;
 constexpr int kMaxJ = 16;
 
 // Device error codes recorded in the context status word (first one wins).
-enum DevErr : int { kDevOk = 0, kDevEnergyOutside = 1, kDevNoConverge = 2, kDevBranch = 3, kDevBadSize = 4 };
+enum DevErr : int {
+    kDevOk = 0,
+    kDevEnergyOutside = 1,
+    kDevNoConverge = 2,
+    kDevBranch = 3,
+    kDevBadSize = 4,
+    kDevMode = 5  // resolvent mode not defined for this solve (SWP-bin average with a bound state)
+};
 
 // One channel of a projected potential set, as the kernels see it.
 struct ChanDev {
@@ -73,9 +80,9 @@ __device__ __forceinline__ unsigned dyn_smem_bytes()
 // Shared-memory layouts (doubles) of the kernels, used by kernel and launcher alike.
 __host__ __device__ inline size_t tbin_smem_doubles(int n)  // n = K * N of the channel
 {
-    // eps n, branch members 2n, branch boundaries 2(n+1), lo/hi 2n, V rows 2n, R 2n, reduction 6 x 32,
-    // V rows again in the accumulation type (at most 2n doubles)
-    return (size_t)13 * n + 2 + 6 * 32;
+    // eps n, branch members 2n, branch boundaries 2(n+1), lo/hi/inverse widths 3n, X(E, B) at the two
+    // bin edges 2(n+4), V rows 2n, R 2n, reduction 6 x 32, diagonal V entries 4
+    return (size_t)14 * n + 2 + 8 + 6 * 32 + 4;
 }
 
 __device__ __forceinline__ void record_error(int *err, int code)
@@ -143,14 +150,18 @@ cudaError_t launch_jacobi_f64(const ChanDev *chans_dev, const int *work_ch_dev, 
                               int threads = 256);
 int jacobi_f64_occupancy(int n, int threads);
 int jacobi_mixed_occupancy(int n, int threads);
+bool jacobi_mixed_c_in_smem(int n);   // eigenvector matrix in shared memory (else global)
 size_t jacobi_mixed_smem_bytes(int n, bool c_in_smem);
 cudaError_t launch_jacobi_mixed(const ChanDev *chans_dev, const int *work_ch_dev, int n_work_ch, int n_samples,
                                 int sample0, int n_terms, const double *coeffs, int n, double *lam_s, double *X_s,
-                                float *Cf_s, int *status_all, int n_ch_total, int *err, cudaStream_t st,
+                                float *Cf_s, double *H_s, int *status_all, int n_ch_total, int *err, cudaStream_t st,
                                 int threads = 256);
 size_t oz_slice_elems(int n);
 cudaError_t launch_oz_gemm(int n, int items, bool ta, const double *A, const double *B, double *C,
                            __nv_bfloat16 *sa, __nv_bfloat16 *sb, int *ea, int *eb, cudaStream_t st);
+cudaError_t launch_oz_split(int n, int items, bool cols, const double *M, __nv_bfloat16 *S, int *e, cudaStream_t st);
+cudaError_t launch_oz_gemm_slices(int n, int items, const __nv_bfloat16 *sa, const int *ea, const __nv_bfloat16 *sb,
+                                  const int *eb, double *C, cudaStream_t st);
 size_t refine_scratch_per_item(int n, int engine);
 cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_samples, int sample0, int n,
                           int n_terms, const double *coeffs, void *scratch, double *eps_all, double *X_all,
@@ -161,11 +172,12 @@ size_t batched_dgemm_scratch(int n, int items);
 cudaError_t launch_plan(const ChanDev *chans_dev, int n_ch, int maxN, const double *e_lab, int n_E, PlanDev plan,
                         int *err, cudaStream_t st, int n_plans = 1);
 cudaError_t launch_tbin(const ChanDev *chans_dev, int n_ch, int n_samples, int n_terms, const double *coeffs,
-                        const double *eps_all, const double *C_all, PlanDev plan, int maxN, double *tbin,
-                        double *phbin, int *err, cudaStream_t st);
+                        const double *eps_all, const double *C_all, PlanDev plan, int maxN, int n_E, double *tout,
+                        double *phout, int *err, cudaStream_t st, bool vc_identity, int mode);
 cudaError_t launch_gather_t(const ChanDev *chans_dev, int n_ch, int n_samples, int n_E, int maxN, PlanDev plan,
-                            const double *tbin, double *t_out, cudaStream_t st);
+                            const double *tbin, double *t_out, cudaStream_t st, bool direct = false);
 cudaError_t launch_observables(const ChanDev *chans_dev, int n_ch, int n_samples, int n_E, int maxN, PlanDev plan,
-                               const double *phbin, double *delta, double *sigma, cudaStream_t st);
+                               const double *phbin, double *delta, double *sigma, cudaStream_t st,
+                               bool direct = false);
 
 }  // namespace wpcd

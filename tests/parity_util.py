@@ -12,15 +12,16 @@ TOL_DELTA_DEG = 1e-8
 TOL_SIGMA_REL = 1e-8
 
 
-def oracle_run(orc, wl: W.Workload, samples=None):
-    """Oracle outputs for the workload (optionally a subset of samples)."""
+def oracle_run(orc, wl: W.Workload, samples=None, mode=0):
+    """Oracle outputs for the workload (optionally a subset of samples; mode =
+    resolvent: 0 free-bin average, 1 SWP-bin average, 2 point)."""
     meshes = [orc.Mesh(n, wl.mesh_kind, wl.alpha, wl.t, wl.kmax, wl.Q) for n in wl.nwp]
     Vts = [orc.project_channel(m, ch.astuple(), wl.gen, wl.gen_params, wl.n_terms, wl.wp_kind)
            for m, ch in zip(meshes, wl.channels)]
     coeffs = wl.coeffs if samples is None else wl.coeffs[samples]
     if wl.n_terms == 1:
         coeffs = np.zeros((coeffs.shape[0], 1))
-    t, d, s, rc = orc.batch([c.astuple() for c in wl.channels], meshes, Vts, coeffs, wl.e_lab, wl.wp_kind)
+    t, d, s, rc = orc.batch([c.astuple() for c in wl.channels], meshes, Vts, coeffs, wl.e_lab, wl.wp_kind, mode=mode)
     assert rc == 0, rc
     return t, d, s
 
@@ -30,7 +31,7 @@ TOL_MIXED_DELTA_DEG = 1e-3
 TOL_MIXED_SIGMA_MB = 1e-2
 
 
-def gpu_run(ctx, model, wl: W.Workload, device="cuda:0", via="solve", prec=0):
+def gpu_run(ctx, model, wl: W.Workload, device="cuda:0", via="solve", prec=0, res=0):
     import torch
     S, nch, nE = wl.n_samples, len(wl.channels), len(wl.e_lab)
     coeffs = None if wl.n_terms == 1 else torch.tensor(wl.coeffs, dtype=torch.float64, device=device)
@@ -39,11 +40,11 @@ def gpu_run(ctx, model, wl: W.Workload, device="cuda:0", via="solve", prec=0):
     d = torch.zeros((S, nch, nE, 3), dtype=torch.float64, device=device)
     s = torch.zeros((S, nE), dtype=torch.float64, device=device)
     if via == "solve":
-        ctx.solve(model.vset, coeffs, S, e, t, d, s, prec=prec)
+        ctx.solve(model.vset, coeffs, S, e, t, d, s, prec=prec, res=res)
     else:
         eid = ctx.diag(model.vset, coeffs, S, prec=prec)
-        ctx.tmatrix(eid, e, t)
-        ctx.observables(eid, e, d, s)
+        ctx.tmatrix(eid, e, t, res=res)
+        ctx.observables(eid, e, d, s, res=res)
         ctx.release(eid)
     ctx.sync()
     tc = t.cpu().numpy().view(np.complex128).reshape(S, nch, nE, 2, 2)
