@@ -22,8 +22,18 @@ constexpr float kRelTol = 1.1920929e-7f;  // 2^-23
 __host__ __device__ inline int mpad(int n) { return (n + 1) & ~1; }
 __host__ __device__ inline size_t mpacked(int n) { return (size_t)n * (n + 1) / 2; }
 
-// A float packed (>= 10 n floats for the refinement buffers) | cos, sin, a_pp', a_qq' float [h] |
-// p, q int [h] | reduction double [64] | rank int [n, even] | flags int [2] | C float [n*n]
+// Index pairs (P, P2), P < P2, of the rotation slots whose 2 x 2 blocks of A
+// one round updates: h (h - 1) / 2 of them, 8 bits each (h <= 256, which
+// every A that fits in shared memory satisfies).
+__host__ __device__ inline int mquads(int n)
+{
+    const int h = mpad(n) / 2;
+    return h * (h - 1) / 2;
+}
+
+// A float packed (>= 10 n floats) | cos, sin, a_pp', a_qq' float [h] | p, q int [h] |
+// reduction double [64] | rank int [n, even] | flags int [2] | slot pairs ushort [quads, even] |
+// C float [n*n]
 __host__ __device__ inline size_t mix_smem(int n, bool c_in_smem)
 {
     const int h = mpad(n) / 2;
@@ -33,6 +43,7 @@ __host__ __device__ inline size_t mix_smem(int n, bool c_in_smem)
     size_t b = a * 4 + (size_t)4 * h * 4 + (size_t)2 * h * 4;
     b = (b + 7) & ~(size_t)7;
     b += 64 * 8 + (size_t)mpad(n) * 4 + 2 * 4;
+    b += (size_t)((mquads(n) + 1) & ~1) * 2;
     if (c_in_smem) b += (size_t)n * n * 4;
     return b;
 }
@@ -71,7 +82,9 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
     double *red = reinterpret_cast<double *>(sb + off);
     int *rank = reinterpret_cast<int *>(red + 64);
     int *flags = rank + npad;
-    float *Cs = C_SMEM ? reinterpret_cast<float *>(flags + 2) : nullptr;
+    unsigned short *quad = reinterpret_cast<unsigned short *>(flags + 2);
+    const int nq = mquads(n);
+    float *Cs = C_SMEM ? reinterpret_cast<float *>(quad + ((nq + 1) & ~1)) : nullptr;
     float *Cg = Cf_s + (size_t)blockIdx.x * n * n;
     float *C = C_SMEM ? Cs : Cg;
     const double *cf = coeffs ? coeffs + (size_t)smp * (n_terms - 1) : nullptr;
@@ -93,6 +106,10 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
     for (int e = tid; e < n * n; e += nt) {
         int i = e / n, j = e - i * n;
         C[(size_t)i * n + j] = (i == j) ? 1.0f : 0.0f;
+    }
+    for (int e = tid; e < h * h; e += nt) {  // slot pairs in row order of P
+        const int P = e / h, P2 = e - P * h;
+        if (P < P2) quad[P * h - P * (P + 1) / 2 + (P2 - P - 1)] = (unsigned short)((P << 8) | P2);
     }
     __syncthreads();
 
@@ -131,9 +148,9 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
                 dqq[k] = aqq;
             }
             __syncthreads();
-            for (int e = tid; e < h * h; e += nt) {
-                const int P = e / h, P2 = e - P * h;
-                if (P >= P2) continue;
+            for (int e = tid; e < nq; e += nt) {
+                const unsigned pr = quad[e];
+                const int P = pr >> 8, P2 = pr & 0xFF;
                 const int p = pp_[P], q = qq_[P], p2 = pp_[P2], q2 = qq_[P2];
                 const float c = rc[P], s = rs[P], c2 = rc[P2], s2 = rs[P2];
                 if (s == 0.0f && s2 == 0.0f) continue;  // both rotations are the identity
@@ -157,16 +174,20 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
                     A[pk(p, q)] = 0.0f;
                 }
             }
-            for (int e = tid; e < h * n; e += nt) {
-                const int k = e / n, row = e - k * n;
+            // C is kept column-major (column s contiguous): one warp per rotation,
+            // its lanes walking consecutive rows of the two columns; a warp
+            // skips an identity rotation as a whole
+            for (int k = tid >> 5; k < h; k += nt >> 5) {
                 const int p = pp_[k], q = qq_[k];
-                if (q >= n || rs[k] == 0.0f) continue;
-                const float c = rc[k], s = rs[k];
-                // C is kept column-major (column s contiguous): consecutive
-                // threads walk consecutive rows of the same two columns
-                const float cp = C[(size_t)p * n + row], cq = C[(size_t)q * n + row];
-                C[(size_t)p * n + row] = c * cp - s * cq;
-                C[(size_t)q * n + row] = s * cp + c * cq;
+                const float s = rs[k];
+                if (q >= n || s == 0.0f) continue;
+                const float c = rc[k];
+                float *Cp = C + (size_t)p * n, *Cq = C + (size_t)q * n;
+                for (int row = tid & 31; row < n; row += 32) {
+                    const float cp = Cp[row], cq = Cq[row];
+                    Cp[row] = c * cp - s * cq;
+                    Cq[row] = s * cp + c * cq;
+                }
             }
             __syncthreads();
         }
