@@ -26,12 +26,22 @@ constexpr size_t kSmemCap = 200 * 1024;
 __host__ __device__ inline int npad_of(int n) { return (n + 1) & ~1; }
 __host__ __device__ inline size_t packed_len(int n) { return (size_t)n * (n + 1) / 2; }
 
-// A (packed) | cos, sin, new a_pp, new a_qq [h each] | p, q [h ints each] | reduction [64] | rank [n, even] | C [n*n]
+// Rotation-slot pairs (P, P2), P < P2, whose 2 x 2 blocks of A one round
+// updates, 8 bits each (h <= 256 for every A that fits in shared memory).
+__host__ __device__ inline int slot_pairs(int n)
+{
+    const int h = npad_of(n) / 2;
+    return h * (h - 1) / 2;
+}
+
+// A (packed) | cos, sin, new a_pp, new a_qq [h each] | p, q [h ints each] | reduction [64] | rank [n, even] |
+// C [n*n] | slot pairs ushort [even count]
 __host__ __device__ inline size_t jacobi_smem_bytes_dev(int n, bool c_in_smem)
 {
     int h = npad_of(n) / 2;
     size_t b = packed_len(n) * 8 + (size_t)4 * h * 8 + (size_t)2 * h * 4 + 64 * 8 + (size_t)((n + 1) & ~1) * 4;
     if (c_in_smem) b += (size_t)n * n * 8;
+    b += (size_t)((slot_pairs(n) + 1) & ~1) * 2;
     return b;
 }
 
@@ -97,6 +107,9 @@ __global__ void __launch_bounds__(kJacMaxThreads) k_jacobi_f64(const ChanDev *ch
     int *rank = reinterpret_cast<int *>(red + 64);    // [n]
     double *Cs = nullptr;
     if (C_SMEM) Cs = reinterpret_cast<double *>(rank + ((n + 1) & ~1));
+    unsigned short *quad = C_SMEM ? reinterpret_cast<unsigned short *>(Cs + (size_t)n * n)
+                                  : reinterpret_cast<unsigned short *>(rank + ((n + 1) & ~1));
+    const int nq = slot_pairs(n);
 
     double *Cg = C_all + ch.c_off + (size_t)smp * n * n;
     double *C = C_SMEM ? Cs : Cg;
@@ -116,6 +129,10 @@ __global__ void __launch_bounds__(kJacMaxThreads) k_jacobi_f64(const ChanDev *ch
     for (int e = tid; e < n * n; e += nt) {
         int i = e / n, j = e - i * n;
         C[(size_t)i * n + j] = (i == j) ? 1.0 : 0.0;
+    }
+    for (int e = tid; e < h * h; e += nt) {  // slot pairs in row order of P
+        const int P = e / h, P2 = e - P * h;
+        if (P < P2) quad[P * h - P * (P + 1) / 2 + (P2 - P - 1)] = (unsigned short)((P << 8) | P2);
     }
     fro2 = block_sum(fro2, red);
     const double tol2 = 1e-30 * fro2;  // (1e-15 ||H||_F)^2
@@ -166,12 +183,12 @@ __global__ void __launch_bounds__(kJacMaxThreads) k_jacobi_f64(const ChanDev *ch
             }
             __syncthreads();
             // phase 2a: off-diagonal 2x2 blocks (P < P') -> J_P^T B J_P'
-            const int nblk = h * h;
-            for (int e = tid; e < nblk; e += nt) {
-                int P = e / h, P2 = e - P * h;
-                if (P >= P2) continue;
+            for (int e = tid; e < nq; e += nt) {
+                const unsigned pr = quad[e];
+                const int P = pr >> 8, P2 = pr & 0xFF;
                 const int p = pp_[P], q = qq_[P], p2 = pp_[P2], q2 = qq_[P2];
                 const double c = rc[P], s = rs[P], c2 = rc[P2], s2 = rs[P2];
+                if (s == 0.0 && s2 == 0.0) continue;  // both rotations are the identity
                 const bool qv = q < n, q2v = q2 < n;
                 double b00 = A[pk(p, p2)];
                 double b01 = q2v ? A[pk(p, q2)] : 0.0;
@@ -196,18 +213,22 @@ __global__ void __launch_bounds__(kJacMaxThreads) k_jacobi_f64(const ChanDev *ch
                 }
             }
             // phase 2c: columns p, q of C
-            for (int e = tid; e < h * n; e += nt) {
-                int k = e / n, row = e - k * n;
-                int p = pp_[k], q = qq_[k];
-                if (q >= n) continue;
-                double c = rc[k], s = rs[k];
-                // in shared memory C is column-major (conflict-free row walks);
-                // in global memory it stays row-major for the in-place final permutation
-                const size_t ip = C_SMEM ? (size_t)p * n + row : (size_t)row * n + p;
-                const size_t iq = C_SMEM ? (size_t)q * n + row : (size_t)row * n + q;
-                double cp = C[ip], cq = C[iq];
-                C[ip] = c * cp - s * cq;
-                C[iq] = s * cp + c * cq;
+            // one warp per rotation, its lanes walking the rows; identity rotations
+            // are skipped by the whole warp
+            for (int k = tid >> 5; k < h; k += nt >> 5) {
+                const int p = pp_[k], q = qq_[k];
+                const double s = rs[k];
+                if (q >= n || s == 0.0) continue;
+                const double c = rc[k];
+                for (int row = tid & 31; row < n; row += 32) {
+                    // in shared memory C is column-major (conflict-free row walks);
+                    // in global memory it stays row-major for the in-place final permutation
+                    const size_t ip = C_SMEM ? (size_t)p * n + row : (size_t)row * n + p;
+                    const size_t iq = C_SMEM ? (size_t)q * n + row : (size_t)row * n + q;
+                    const double cp = C[ip], cq = C[iq];
+                    C[ip] = c * cp - s * cq;
+                    C[iq] = s * cp + c * cq;
+                }
             }
             __syncthreads();
         }
