@@ -52,6 +52,9 @@ def parse():
                     help="length of the Poisson request stream for the latency figures (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-nwp", default="32,64,128")
+    ap.add_argument("--mi-interp", type=int, default=32,
+                    help="MI comparison method: interpolation energies (0 = skip the MI leg)")
+    ap.add_argument("--mi-quad", type=int, default=96, help="MI momentum grid points per l-block")
     return ap.parse_args()
 
 
@@ -321,6 +324,38 @@ def run_wpcd(args, ws, rank, lrank):
                     "max_sigma_err_mb": float(np.abs(s[:k].cpu().numpy() - s64.cpu().numpy()).max()),
                     "reference": "FP64 path on the same GPU"}
 
+    # the paper's comparison method on the same GPU: MI solves at Chebyshev
+    # interpolation energies, phases interpolated in T_lab (Sec. 2.1, Sec. 6)
+    mi = None
+    if args.mi_interp > 0:
+        mid = ctx.mi_prepare(wl.channels, wl.gen, wl.gen_params, wl.n_terms, n_quad=args.mi_quad)
+        e_int = torch.tensor(W.chebyshev_energies(args.mi_interp), dtype=torch.float64, device=dev)
+        dmi = torch.empty((S, nch, nE, 3), dtype=torch.float64, device=dev)
+        smi = torch.empty((S, nE), dtype=torch.float64, device=dev)
+        ctx.mi_solve(mid, cf, S, e_int, e, None, dmi, smi)  # warm-up
+        ctx.sync()
+        mi_ms = []
+        for _ in range(2):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.mi_solve(mid, cf, S, e_int, e, None, dmi, smi)
+            b.record(stream)
+            torch.cuda.synchronize()
+            mi_ms.append(a.elapsed_time(b))
+        ctx.sync()
+        ctx.release(mid)
+        dd = np.abs((dmi.cpu().numpy() - d.cpu().numpy() + 90.0) % 180.0 - 90.0)[..., :2]
+        sel = wl.e_lab > 5.0
+        rel_s = np.abs(smi.cpu().numpy() - s.cpu().numpy())[:, sel] / np.abs(s.cpu().numpy()[:, sel])
+        mi_t = statistics.mean(mi_ms)
+        mi = {"method": "matrix inversion (Sec. 2.1) at Chebyshev interpolation energies, linear in T_lab (Sec. 6)",
+              "n_interp": args.mi_interp, "n_quad": args.mi_quad, "ms_per_step": mi_t,
+              "value": S * nch / (mi_t * 1e-3), "unit": UNIT,
+              "max_phase_diff_to_wpcd_deg": float(dd[:, :, sel].max()),
+              "max_sigma_rel_diff_to_wpcd": float(rel_s.max()),
+              "note": "method difference (WPCD N_WP 40-100 vs MI N_Q grid and interpolation), not an error bound"}
+
     sum_n3 = sum((n * (2 if ch.coupled else 1)) ** 3 for n, ch in zip(wl.nwp, wl.channels))
     eig_ms, eig_n = prof["eigen"]
     ref_ms, ref_n = prof["refine"]
@@ -377,6 +412,8 @@ def run_wpcd(args, ws, rank, lrank):
             "accuracy_vs_fp64": accuracy,
             "clocks": clocks,
         }
+        if mi is not None:
+            line["mi_comparison"] = mi
         if args.serve_seconds > 0:
             line["latency"] = serve_latency(args, lrank, prec)
         if not args.no_cpu_baseline:

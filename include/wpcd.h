@@ -233,7 +233,40 @@ wpcd_status wpcd_solve_host(wpcd_ctx *ctx, int vset_id, const double *coeffs_hos
                             const double *e_lab_host, int n_E, wpcd_precision prec, wpcd_resolvent res,
                             double *t_out_host, double *delta_host, double *sigma_host);
 
-/* Free a mesh, vset or eig handle.  Errors: WPCD_ERR_HANDLE. */
+/* ---- MI comparison method: Sec. 2.1 (matrix inversion), Sec. 6 (interpolation) ---------------------
+ * The LS equation solved directly on a momentum grid: N_Q Gauss-Legendre
+ * points mapped by k = c tan(pi (1 + x) / 4) plus the on-shell point p, with
+ * the Haftel-Tabakin pole subtraction
+ *   D_j = w_j k_j^2 2 mu / (p^2 - k_j^2),  D_N = -2 mu p^2 sum_j w_j / (p^2 - k_j^2),
+ *   (1 - V D) K = V,  T = (1 + i pi mu p K)^-1 K,  S = 1 - 2 pi i mu p T.
+ * wpcd_mi_prepare evaluates the built-in potential's terms (generator_id
+ * WPCD_GEN_YAMAGUCHI or WPCD_GEN_YUKAWA, parameters as for wpcd_project) on
+ * the grid for the channels; n_quad = N_Q in [4, 100] (both l-blocks of a
+ * coupled channel, 2 (N_Q + 1) rows, are factorised in one CTA's shared
+ * memory), c_map_fm = c > 0.  Errors: WPCD_ERR_ARG, WPCD_ERR_NOMEM,
+ * WPCD_ERR_BUDGET, WPCD_ERR_CUDA.  The handle is freed by wpcd_release. */
+wpcd_status wpcd_mi_prepare(wpcd_ctx *ctx, const wpcd_channel *channels, int n_ch, int generator_id,
+                            const double *gen_params_host, int n_gen_params, int n_terms, int n_quad,
+                            double c_map_fm, int *mi_id);
+
+/* Solve at the n_I >= 2 interpolation energies e_int_dev (MeV, ascending,
+ * device) for every sample (coeffs_dev [n_samples][n_terms-1], device) and
+ * channel, then interpolate the phase shifts linearly in T_lab to the requested
+ * energies e_lab_dev [n_E] (the end segments extended; delta moved by
+ * multiples of 180 deg to within 90 deg of the segment start) and form the np
+ * total cross section as wpcd_observables does.  Each system is factorised in
+ * FP32 (partial pivoting) and its solution refined with FP64 residuals until
+ * the correction is below 1e-13 of the solution.  Outputs (device, any may be
+ * NULL but not all): k_out_dev [n_samples][n_ch][n_I][2][2] the on-shell K
+ * (fm^2, uncoupled channels in [0][0]); delta_dev [n_samples][n_ch][n_E][3]
+ * degrees; sigma_dev [n_samples][n_E] mb.  A system whose refinement does not
+ * converge is reported by wpcd_sync as WPCD_ERR_NOCONVERGE.  Errors:
+ * WPCD_ERR_ARG, WPCD_ERR_HANDLE, WPCD_ERR_NOMEM, WPCD_ERR_BUDGET, WPCD_ERR_CUDA. */
+wpcd_status wpcd_mi_solve(wpcd_ctx *ctx, int mi_id, const double *coeffs_dev, int n_samples, const double *e_int_dev,
+                          int n_I, const double *e_lab_dev, int n_E, double *k_out_dev, double *delta_dev,
+                          double *sigma_dev);
+
+/* Free a mesh, vset, eig or MI handle.  Errors: WPCD_ERR_HANDLE. */
 wpcd_status wpcd_release(wpcd_ctx *ctx, int id);
 
 /* ---- tracing ---------------------------------------------------------------------------------
@@ -247,7 +280,8 @@ enum {
     WPCD_PHASE_GATHER = 5,      /* T at the requested energies */
     WPCD_PHASE_OBSERVABLES = 6, /* interpolation and cross section */
     WPCD_PHASE_REFINE = 7,      /* FP64 refinement of the mixed path's eigenpairs */
-    WPCD_PHASE_COUNT = 8
+    WPCD_PHASE_MI = 8,          /* the MI comparison method */
+    WPCD_PHASE_COUNT = 9
 };
 
 /* Batched square products C_b = op(A_b) B_b (op(A) = A^T if trans_a) for `items`

@@ -71,6 +71,8 @@ def lib():
                 "or_sigma_prefactor_mb": (d, [d]),
                 "or_mi_kmatrix": (i, [i, _dp, i, i, i, i, i, i, i, _dp, i, d, d, _dp]),
                 "or_S_from_K": (None, [i, d, _dp, _dp]),
+                "or_interp_phase_tlab": (None, [i, _dp, _dp, i, d, _dp]),
+                "or_mi_batch": (i, [i, _ip, i, _dp, i, i, _dp, i, d, i, _dp, i, _dp, _dp, _dp, _dp, i]),
                 "or_batch": (i, [i, _ip, _ip, _lp, _dp, i, i, _lp, _dp, i, _dp, i, _dp, i, _dp, _dp, _dp, i]),
                 "or_max_threads": (i, []),
             }
@@ -327,6 +329,33 @@ def batch(channels, meshes, Vts, coeffs, e_lab, wp_kind=0, n_threads=0, mode=AVG
                         vt_off.ctypes.data_as(_lp), _d(vt_all), S, _d(coeffs), nE, _d(e_lab), int(mode),
                         t_out.ctypes.data_as(_dp), _d(delta), _d(sigma), int(n_threads))
     return t_out, delta, sigma, rc
+
+
+def interp_phase_tlab(e_int, ph, K, e):
+    e_int = _f64(e_int)
+    ph = _f64(ph)
+    out = np.zeros(3)
+    lib().or_interp_phase_tlab(e_int.shape[0], _d(e_int), _d(ph), K, float(e), _d(out))
+    return out
+
+
+def mi_batch(channels, gen, gp, n_terms, coeffs, e_int, e_lab, NQ=96, cmap=1.0, n_threads=0):
+    """MI at the interpolation energies e_int (MeV) for every (sample, channel),
+    phases interpolated linearly in T_lab to e_lab, and sigma_tot.
+    Returns (K [S,ch,n_I,2,2], delta [S,ch,E,3] deg, sigma [S,E] mb, rc)."""
+    n_ch = len(channels)
+    chdesc = np.ascontiguousarray(np.array(channels, dtype=np.int32).reshape(n_ch, 6))
+    coeffs = _f64(np.asarray(coeffs).reshape(-1, max(n_terms - 1, 1)))
+    S = coeffs.shape[0]
+    e_int = _f64(e_int)
+    e_lab = _f64(e_lab)
+    nI, nE = e_int.shape[0], e_lab.shape[0]
+    k_out = np.zeros((S, n_ch, nI, 2, 2))
+    delta = np.zeros((S, n_ch, nE, 3))
+    sigma = np.zeros((S, nE))
+    rc = lib().or_mi_batch(n_ch, _i(chdesc), int(gen), _d(_f64(gp)), n_terms, S, _d(coeffs), NQ, float(cmap), nI,
+                           _d(e_int), nE, _d(e_lab), _d(k_out), _d(delta), _d(sigma), int(n_threads))
+    return k_out, delta, sigma, rc
 
 
 def max_threads() -> int:

@@ -1038,6 +1038,93 @@ int or_batch(int n_ch, const int *chdesc /* n_ch x 6 */, const int *nwp, const l
     return err;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Sec. 6 (method performance): the MI method solves the LS equation at n_I   */
+/* energies of a Chebyshev distribution and interpolates the phase shifts     */
+/* linearly between them.  Reading: linear in T_lab on the segment of         */
+/* consecutive interpolation energies around the requested energy, the end    */
+/* segments extended; delta moved by multiples of 180 deg to within 90 deg of  */
+/* the segment's first value before interpolating (as for the midpoints).    */
+/* e_int [n_I] ascending MeV; ph [n_I][3] degrees.                            */
+/* ------------------------------------------------------------------------- */
+void or_interp_phase_tlab(int n_I, const double *e_int, const double *ph, int K, double e, double *out)
+{
+    int j = -1;
+    for (int i = 0; i < n_I; ++i)
+        if (e_int[i] <= e) j = i;
+    if (j < 0) j = 0;
+    if (j > n_I - 2) j = n_I - 2;
+    double w = (e - e_int[j]) / (e_int[j + 1] - e_int[j]);
+    int ncomp = (K == 2) ? 2 : 1;
+    for (int c = 0; c < ncomp; ++c) {
+        double d0 = ph[3 * j + c], d1 = ph[3 * (j + 1) + c];
+        d1 += 180.0 * round((d0 - d1) / 180.0);
+        out[c] = wrap90(d0 + w * (d1 - d0));
+    }
+    if (K == 2) {
+        out[2] = ph[3 * j + 2] + w * (ph[3 * (j + 1) + 2] - ph[3 * j + 2]);
+    } else {
+        out[1] = 0.0;
+        out[2] = 0.0;
+    }
+}
+
+/* MI batch: for every (sample, channel) the on-shell K at each interpolation */
+/* energy (or_mi_kmatrix), S and the phases there, then the phases and the np */
+/* total cross section at the requested energies by the interpolation above.  */
+/* k_out [S][n_ch][n_I][2][2] (may be NULL), delta_out [S][n_ch][n_E][3],     */
+/* sigma_out [S][n_E].  OpenMP over (sample, channel).  Returns 0 or the      */
+/* first error code.                                                          */
+int or_mi_batch(int n_ch, const int *chdesc, int gen, const double *gp, int n_terms, int n_samples,
+                const double *coeffs, int NQ, double cmap, int n_I, const double *e_int, int n_E,
+                const double *e_lab, double *k_out, double *delta_out, double *sigma_out, int n_threads)
+{
+    int err = 0;
+    double *ph_all = (double *)malloc(sizeof(double) * (size_t)n_samples * n_ch * n_I * 3);
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic) collapse(2)
+#endif
+    for (int smp = 0; smp < n_samples; ++smp)
+        for (int c = 0; c < n_ch; ++c) {
+            const int *d = chdesc + 6 * c;
+            int K = d[4] ? 2 : 1;
+            for (int e = 0; e < n_I; ++e) {
+                double p = or_p_of_tlab(e_int[e]), Km[4];
+                double complex S[4];
+                int rc = or_mi_kmatrix(gen, gp, d[0], d[1], d[2], d[3], d[4], d[5], n_terms,
+                                       coeffs + (size_t)smp * (n_terms - 1), NQ, cmap, p, Km);
+                if (rc != 0) {
+#ifdef _OPENMP
+#pragma omp critical(or_err)
+#endif
+                    if (!err) err = -5;
+                }
+                if (k_out) {
+                    double *ko = k_out + (((size_t)smp * n_ch + c) * n_I + e) * 4;
+                    for (int ab = 0; ab < 4; ++ab) ko[ab] = 0.0;
+                    for (int a = 0; a < K; ++a)
+                        for (int b = 0; b < K; ++b) ko[a * 2 + b] = Km[a * K + b];
+                }
+                or_S_from_K(K, p, Km, S);
+                or_phases_from_S(K, S, ph_all + (((size_t)smp * n_ch + c) * n_I + e) * 3);
+            }
+        }
+    for (int smp = 0; smp < n_samples; ++smp)
+        for (int e = 0; e < n_E; ++e) {
+            double acc = 0.0;
+            for (int c = 0; c < n_ch; ++c) {
+                int K = chdesc[6 * c + 4] ? 2 : 1;
+                double *dout = delta_out + (((size_t)smp * n_ch + c) * n_E + e) * 3;
+                or_interp_phase_tlab(n_I, e_int, ph_all + ((size_t)smp * n_ch + c) * n_I * 3, K, e_lab[e], dout);
+                if (chdesc[6 * c + 5] == 0) acc += or_sigma_term(chdesc[6 * c + 1], K, dout);
+            }
+            sigma_out[(size_t)smp * n_E + e] = or_sigma_prefactor_mb(or_p_of_tlab(e_lab[e])) * acc;
+        }
+    free(ph_all);
+    return err;
+}
+
 int or_max_threads(void)
 {
 #ifdef _OPENMP

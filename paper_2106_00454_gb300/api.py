@@ -108,7 +108,7 @@ class Context:
     def bytes_in_use(self) -> int:
         return self.lib.wpcd_bytes_in_use(self.h)
 
-    PHASES = ["mesh", "project", "eigen", "plan", "tmatrix", "gather", "observables", "refine"]
+    PHASES = ["mesh", "project", "eigen", "plan", "tmatrix", "gather", "observables", "refine", "mi"]
 
     def kernel_launches(self) -> int:
         return int(self.lib.wpcd_kernel_launches(self.h))
@@ -194,6 +194,23 @@ class Context:
               res=AVG_FREE_BIN):
         _ck(self.lib.wpcd_solve(self.h, vset_id, _ptr(coeffs), n_samples, _ptr(e_lab), e_lab.numel(), prec,
                                 res, _ptr(t_out), _ptr(delta), _ptr(sigma)), "wpcd_solve")
+
+    # ------------------------------------------------------------------ MI comparison method
+    def mi_prepare(self, channels, gen, gen_params, n_terms, n_quad=96, c_map=1.0) -> int:
+        n = len(channels)
+        arr = (_lib.wpcd_channel * n)(*[_lib.wpcd_channel(*c.astuple()) if hasattr(c, "astuple")
+                                        else _lib.wpcd_channel(*c) for c in channels])
+        gp = np.ascontiguousarray(gen_params, dtype=np.float64)
+        mid = ctypes.c_int()
+        _ck(self.lib.wpcd_mi_prepare(self.h, arr, n, gen, _ptr(gp), gp.size, n_terms, n_quad, float(c_map),
+                                     ctypes.byref(mid)), "wpcd_mi_prepare")
+        return mid.value
+
+    def mi_solve(self, mi_id, coeffs, n_samples, e_int, e_lab, k_out=None, delta=None, sigma=None):
+        """MI at the interpolation energies e_int (device tensor, MeV) and the
+        phases / cross sections interpolated to e_lab (device tensor)."""
+        _ck(self.lib.wpcd_mi_solve(self.h, mi_id, _ptr(coeffs), n_samples, _ptr(e_int), e_int.numel(), _ptr(e_lab),
+                                   e_lab.numel(), _ptr(k_out), _ptr(delta), _ptr(sigma)), "wpcd_mi_solve")
 
     def solve_host(self, vset_id, coeffs, n_samples, e_lab, t_out=None, delta=None, sigma=None, prec=PREC_FP64,
                    res=AVG_FREE_BIN):

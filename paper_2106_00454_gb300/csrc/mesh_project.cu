@@ -3,6 +3,7 @@
 // potential matrix identity").  FP64 on the CUDA cores.
 #include <math.h>
 
+#include "potential.cuh"
 #include "wpcd_internal.cuh"
 
 namespace wpcd {
@@ -108,30 +109,10 @@ cudaError_t launch_mesh(int N, int kind, double alpha, double t, double kmax, in
 // V[(b,j),(a,i)] = V[(a,i),(b,j)] are written together (v^{l'l}(p',p) =
 // v^{ll'}(p,p')).
 // ---------------------------------------------------------------------------------------------
-constexpr int kLmaxReg = 10;  // angle integrals kept in registers: L = 0..10 (J <= 8)
-
 __device__ __forceinline__ double wp_f(int wp_kind, double k) { return wp_kind == 0 ? 1.0 : sqrt(k / kMu); }
 __device__ __forceinline__ double wp_norm(int wp_kind, double a, double b)
 {
     return wp_kind == 0 ? (b - a) : (b * b - a * a) / (2.0 * kMu);
-}
-
-__device__ __forceinline__ double ls_factor(int s, int J, int l)
-{
-    return 0.5 * (J * (J + 1.0) - l * (l + 1.0) - s * (s + 1.0));
-}
-
-__device__ __forceinline__ double s12_factor(int s, int J, int lp, int l)
-{
-    if (s != 1) return 0.0;
-    if (lp == l) {
-        if (l == J) return 2.0;
-        if (l == J - 1) return -2.0 * (J - 1.0) / (2.0 * J + 1.0);
-        if (l == J + 1) return -2.0 * (J + 2.0) / (2.0 * J + 1.0);
-        return 0.0;
-    }
-    if ((lp == J - 1 && l == J + 1) || (lp == J + 1 && l == J - 1)) return 6.0 * sqrt(J * (J + 1.0)) / (2.0 * J + 1.0);
-    return 0.0;
 }
 
 // Sum over the CTA (blockDim <= 1024, multiple of 32).  Every thread gets the total.
@@ -165,18 +146,7 @@ __global__ void __launch_bounds__(256) k_project(const ChanDev *chans, const int
     __shared__ double red[8];
     const int Lm = (Lmax < kLmaxReg) ? Lmax : kLmaxReg;
     if (GEN == WPCD_GEN_YUKAWA) {
-        for (int x = threadIdx.x; x < kAngleQ; x += blockDim.x) {
-            double xv = angx[x], p0 = 1.0, p1 = xv;
-            ax[x] = xv;
-            wpl[x][0] = angw[x];
-            if (Lm >= 1) wpl[x][1] = angw[x] * xv;
-            for (int L = 2; L <= Lm; ++L) {
-                double p2 = ((2.0 * L - 1.0) * xv * p1 - (L - 1.0) * p0) / L;
-                p0 = p1;
-                p1 = p2;
-                wpl[x][L] = angw[x] * p2;
-            }
-        }
+        angle_tables(angx, angw, Lm, wpl, ax);
         __syncthreads();
     }
 
@@ -193,32 +163,7 @@ __global__ void __launch_bounds__(256) k_project(const ChanDev *chans, const int
 
     double I1[kLmaxReg + 1], I2[kLmaxReg + 1], I3[kLmaxReg + 1];
     double R = 0.0;
-    if (GEN == WPCD_GEN_YUKAWA) {
-        const double m1 = gp[0], m2 = gp[1], m3 = gp[2], Lam = gp[3];
-#pragma unroll
-        for (int L = 0; L <= kLmaxReg; ++L) I1[L] = I2[L] = I3[L] = 0.0;
-        const double A0 = pp * pp + p * p, B = 2.0 * pp * p;
-        for (int x = 0; x < kAngleQ; ++x) {
-            double d = A0 - B * ax[x];
-            double F1 = 1.0 / (d + m1 * m1), F2 = 1.0 / (d + m2 * m2), F3 = 1.0 / (d + m3 * m3);
-#pragma unroll
-            for (int L = 0; L <= kLmaxReg; ++L) {
-                if (L <= Lm) {
-                    double wv = wpl[x][L];
-                    I1[L] = fma(wv, F1, I1[L]);
-                    I2[L] = fma(wv, F2, I2[L]);
-                    I3[L] = fma(wv, F3, I3[L]);
-                }
-            }
-        }
-#pragma unroll
-        for (int L = 0; L <= kLmaxReg; ++L) {
-            I1[L] *= 2.0 * kPi;
-            I2[L] *= 2.0 * kPi;
-            I3[L] *= 2.0 * kPi;
-        }
-        R = exp(-(pp * pp + p * p) / (Lam * Lam));
-    }
+    if (GEN == WPCD_GEN_YUKAWA) yukawa_angle_integrals(gp, wpl, ax, Lm, pp, p, I1, I2, I3, R);
 
     for (int g = 0; g < n_group; ++g) {
         const int cidx = group[g];
@@ -229,44 +174,7 @@ __global__ void __launch_bounds__(256) k_project(const ChanDev *chans, const int
                 const int lp = ch.coupled ? (al == 0 ? ch.J - 1 : ch.J + 1) : ch.l;
                 const int l = ch.coupled ? (be == 0 ? ch.J - 1 : ch.J + 1) : ch.l;
                 double tv[kMaxTerms];
-#pragma unroll
-                for (int t = 0; t < kMaxTerms; ++t) tv[t] = 0.0;
-                if (GEN == WPCD_GEN_YAMAGUCHI) {
-                    if (lp == 0 && l == 0) tv[0] = gp[0] / ((pp * pp + gp[1] * gp[1]) * (p * p + gp[1] * gp[1]));
-                } else {
-                    const int s = ch.s, J = ch.J;
-                    double u[kYukTerms];
-#pragma unroll
-                    for (int k = 0; k < kYukTerms; ++k) u[k] = 0.0;
-                    const bool diag = (lp == l);
-                    if (diag) {
-                        u[0] = I1[l];
-                        u[1] = (2.0 * s * (s + 1.0) - 3.0) * I1[l];
-                        u[2] = I2[l];
-                        double ilm1 = (l >= 1) ? I2[l - 1] : 0.0;
-                        u[3] = ls_factor(s, J, l) * pp * p * (I2[l + 1] - ilm1) / (2.0 * l + 1.0);
-                    }
-                    u[4] = s12_factor(s, J, lp, l) * I3[(l + lp) / 2];
-                    if (diag && l == 0 && s == 0) { u[5] = 1.0; u[7] = p * p + pp * pp; }
-                    if (diag && l == 0 && s == 1) { u[6] = 1.0; u[8] = p * p + pp * pp; }
-                    if (diag && l == 1 && s == 1 && J == 0) u[9] = pp * p;
-                    if (diag && l == 1 && s == 0 && J == 1) u[10] = pp * p;
-                    if (diag && l == 1 && s == 1 && J == 1) u[11] = pp * p;
-                    if (diag && l == 1 && s == 1 && J == 2) u[12] = pp * p;
-                    if (s == 1 && J == 1 && lp == 2 && l == 0) u[13] = pp * pp;
-                    if (s == 1 && J == 1 && lp == 0 && l == 2) u[13] = p * p;
-                    double v0 = 0.0;
-#pragma unroll
-                    for (int k = 0; k < kYukTerms; ++k) {
-                        u[k] *= R;
-                        v0 = fma(gp[4 + k], u[k], v0);
-                    }
-                    if (s == 0 && l == 0 && lp == 0 && ch.tz != 0) v0 += gp[18] * R;
-                    tv[0] = v0;
-#pragma unroll
-                    for (int k = 0; k < kYukTerms; ++k)
-                        if (k + 1 < kMaxTerms) tv[k + 1] = u[k];
-                }
+                potential_terms<GEN>(gp, ch.s, ch.J, ch.tz, lp, l, pp, p, I1, I2, I3, R, tv);
                 for (int t = 0; t < n_terms; ++t) {
                     double v = cta_sum(live ? om * tv[t] : 0.0, red);
                     if (threadIdx.x == 0) {

@@ -71,13 +71,25 @@ struct Exec {
     EigH eig;
 };
 
-enum Kind { kMesh = 1, kVSet = 2, kEig = 3 };
+// MI set: the momentum grid, the channels and their grid potential terms.
+struct MiH {
+    int n_ch = 0, NQ = 0, n_terms = 0, gen = 0, Lmax = 0, n_gp = 0;
+    double cmap = 1.0;
+    std::vector<MiChanDev> ch;
+    MiChanDev *ch_dev = nullptr;
+    double *kg = nullptr, *wg = nullptr, *gp = nullptr, *Vg = nullptr;
+    int *work_dev[2] = {nullptr, nullptr};  // channels with K = 1, 2
+    int n_work[2] = {0, 0};
+};
+
+enum Kind { kMesh = 1, kVSet = 2, kEig = 3, kMi = 4 };
 
 struct Handle {
     Kind kind;
     std::unique_ptr<MeshH> mesh;
     std::unique_ptr<VSetH> vset;
     std::unique_ptr<EigH> eig;
+    std::unique_ptr<MiH> mi;
 };
 
 }  // namespace
@@ -266,6 +278,17 @@ void free_vset(wpcd_ctx *c, VSetH &v)
     dfree(c, v.cd_dev);
     dfree(c, v.ident_dev);
     for (auto &kv : v.bucket_dev) dfree(c, kv.second);
+}
+
+void free_mi(wpcd_ctx *c, MiH &m)
+{
+    dfree(c, m.ch_dev);
+    dfree(c, m.kg);
+    dfree(c, m.wg);
+    dfree(c, m.gp);
+    dfree(c, m.Vg);
+    dfree(c, m.work_dev[0]);
+    dfree(c, m.work_dev[1]);
 }
 
 void free_mesh(wpcd_ctx *c, MeshH &m)
@@ -559,6 +582,7 @@ void wpcd_destroy(wpcd_ctx *c)
         if (kv.second.mesh) free_mesh(c, *kv.second.mesh);
         if (kv.second.vset) free_vset(c, *kv.second.vset);
         if (kv.second.eig) free_eig(c, *kv.second.eig);
+        if (kv.second.mi) free_mi(c, *kv.second.mi);
     }
     serve_shutdown(c);
     free_eig(c, c->main.eig);
@@ -1072,7 +1096,150 @@ wpcd_status wpcd_release(wpcd_ctx *c, int id)
     if (it->second.mesh) free_mesh(c, *it->second.mesh);
     if (it->second.vset) free_vset(c, *it->second.vset);
     if (it->second.eig) free_eig(c, *it->second.eig);
+    if (it->second.mi) free_mi(c, *it->second.mi);
     c->handles.erase(it);
+    return WPCD_OK;
+}
+
+// ---- MI comparison method (Sec. 2.1, Sec. 6) ---------------------------------------------------
+wpcd_status wpcd_mi_prepare(wpcd_ctx *c, const wpcd_channel *channels, int n_ch, int generator_id,
+                            const double *gp_host, int n_gp, int n_terms, int n_quad, double c_map_fm, int *mi_id)
+{
+    const int gen = generator_id;
+    if (!c || !channels || n_ch < 1 || !mi_id || n_quad < 4 || n_quad > kMiMaxNQ || !(c_map_fm > 0) || !gp_host)
+        return WPCD_ERR_ARG;
+    if (gen == WPCD_GEN_YAMAGUCHI && (n_terms != 1 || n_gp < 2)) return WPCD_ERR_ARG;
+    if (gen == WPCD_GEN_YUKAWA && (n_terms < 1 || n_terms > kYukTerms + 1 || n_gp < kYukParams)) return WPCD_ERR_ARG;
+    if (gen != WPCD_GEN_YAMAGUCHI && gen != WPCD_GEN_YUKAWA) return WPCD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaSetDevice(c->device));
+    auto m = std::make_unique<MiH>();
+    m->n_ch = n_ch;
+    m->NQ = n_quad;
+    m->n_terms = n_terms;
+    m->gen = gen;
+    m->cmap = c_map_fm;
+    m->n_gp = n_gp;
+    const int M = n_quad + 1;
+    size_t vlen = 0;
+    int maxJ = 0;
+    std::vector<int> work[2];
+    for (int k = 0; k < n_ch; ++k) {
+        const wpcd_channel &ch = channels[k];
+        if (ch.J < 0 || ch.J > kMaxJ || (ch.s != 0 && ch.s != 1)) return WPCD_ERR_ARG;
+        if (ch.coupled && (ch.s != 1 || ch.J < 1 || ch.l != ch.J - 1 || ch.lp != ch.J + 1)) return WPCD_ERR_ARG;
+        if (!ch.coupled && ch.l != ch.lp) return WPCD_ERR_ARG;
+        if (gen == WPCD_GEN_YAMAGUCHI && (ch.coupled || ch.l != 0)) return WPCD_ERR_ARG;
+        if (gen == WPCD_GEN_YUKAWA && ch.J > 8) return WPCD_ERR_ARG;
+        MiChanDev d;
+        memset(&d, 0, sizeof(d));
+        d.s = ch.s;
+        d.J = ch.J;
+        d.l = ch.l;
+        d.lp = ch.lp;
+        d.coupled = ch.coupled ? 1 : 0;
+        d.tz = ch.tz;
+        d.K = ch.coupled ? 2 : 1;
+        d.n = d.K * M;
+        d.vg_off = (long long)vlen;
+        vlen += (size_t)n_terms * d.n * d.n;
+        m->ch.push_back(d);
+        work[d.K - 1].push_back(k);
+        maxJ = std::max(maxJ, ch.J);
+    }
+    m->Lmax = maxJ + 2;
+    wpcd_status st;
+    if ((st = dalloc(c, &m->ch_dev, (size_t)n_ch)) || (st = dalloc(c, &m->kg, (size_t)n_quad)) ||
+        (st = dalloc(c, &m->wg, (size_t)n_quad)) || (st = dalloc(c, &m->gp, (size_t)n_gp)) ||
+        (st = dalloc(c, &m->Vg, vlen))) {
+        free_mi(c, *m);
+        return st;
+    }
+    for (int K = 0; K < 2; ++K) {
+        m->n_work[K] = (int)work[K].size();
+        if (work[K].empty()) continue;
+        if ((st = dalloc(c, &m->work_dev[K], work[K].size()))) {
+            free_mi(c, *m);
+            return st;
+        }
+        CK(cudaMemcpyAsync(m->work_dev[K], work[K].data(), sizeof(int) * work[K].size(), cudaMemcpyHostToDevice,
+                           c->main.stream));
+    }
+    CK(cudaMemcpyAsync(m->ch_dev, m->ch.data(), sizeof(MiChanDev) * n_ch, cudaMemcpyHostToDevice, c->main.stream));
+    CK(cudaMemcpyAsync(m->gp, gp_host, sizeof(double) * n_gp, cudaMemcpyHostToDevice, c->main.stream));
+    double *glx, *glw, *angx = nullptr, *angw = nullptr;
+    if ((st = gl_rule(c, n_quad, &glx, &glw))) return st;
+    if (gen == WPCD_GEN_YUKAWA && (st = gl_rule(c, kAngleQ, &angx, &angw))) return st;
+    {
+        Launch L(c, c->main, WPCD_PHASE_MI);
+        CK(launch_mi_grid(n_quad, c_map_fm, glx, glw, m->kg, m->wg, c->main.stream));
+    }
+    {
+        Launch L(c, c->main, WPCD_PHASE_MI);
+        CK(launch_mi_pot(gen, m->ch_dev, n_ch, n_quad, m->kg, m->Lmax, m->gp, angx, angw, n_terms, m->Vg,
+                         c->main.stream));
+    }
+    CK(cudaStreamSynchronize(c->main.stream));
+    const int id = c->next_id++;
+    Handle h;
+    h.kind = kMi;
+    h.mi = std::move(m);
+    c->handles.emplace(id, std::move(h));
+    *mi_id = id;
+    return WPCD_OK;
+}
+
+wpcd_status wpcd_mi_solve(wpcd_ctx *c, int mi_id, const double *coeffs, int S, const double *e_int, int n_I,
+                          const double *e_lab, int n_E, double *k_out, double *delta, double *sigma)
+{
+    if (!c || S < 1 || !e_int || n_I < 2 || !e_lab || n_E < 1 || (!k_out && !delta && !sigma)) return WPCD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    Handle *h = find(c, mi_id, kMi);
+    if (!h) return WPCD_ERR_HANDLE;
+    MiH &m = *h->mi;
+    if (m.n_terms > 1 && !coeffs) return WPCD_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    if (!c->n_sm) cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    Exec &X = c->main;
+    const int M = m.NQ + 1;
+    // on-shell columns [ch][n_I][n_terms][K][K][M], phases [S][ch][n_I][3], status [S][ch]
+    size_t von_len = 0;
+    for (auto &d : m.ch) {
+        d.von_off = (long long)von_len;
+        von_len += (size_t)n_I * m.n_terms * d.K * d.K * M;
+    }
+    wpcd_status st;
+    const size_t ph_len = (size_t)S * m.n_ch * n_I * 3;
+    if ((st = ws_reserve(c, X, X.ws_tbin, (von_len + ph_len) * sizeof(double)))) return st;
+    if ((st = ws_reserve(c, X, X.ws_plan_i, (size_t)S * m.n_ch * sizeof(int)))) return st;
+    double *Von = static_cast<double *>(X.ws_tbin.p), *ph = Von + von_len;
+    int *status = static_cast<int *>(X.ws_plan_i.p);
+    CK(cudaMemcpyAsync(m.ch_dev, m.ch.data(), sizeof(MiChanDev) * m.n_ch, cudaMemcpyHostToDevice, X.stream));
+    double *angx = nullptr, *angw = nullptr;
+    if (m.gen == WPCD_GEN_YUKAWA && (st = gl_rule(c, kAngleQ, &angx, &angw))) return st;
+    {
+        Launch L(c, X, WPCD_PHASE_MI);
+        CK(launch_mi_onshell(m.gen, m.ch_dev, m.n_ch, m.NQ, m.kg, n_I, e_int, m.Lmax, m.gp, angx, angw, m.n_terms, Von,
+                             X.stream));
+    }
+    const double *cf = m.n_terms > 1 ? coeffs : nullptr;
+    for (int K = 1; K <= 2; ++K) {
+        const int nw = m.n_work[K - 1];
+        if (!nw) continue;
+        const int n = K * M;
+        const int per_sm = mi_slots_per_sm(n, m.NQ);
+        if (per_sm < 1) return WPCD_ERR_ARG;
+        const int items = S * nw;
+        const int slots = std::max(1, std::min(items, per_sm * c->n_sm));
+        if ((st = ws_reserve(c, X, X.ws_ref, (size_t)slots * n * n * sizeof(double)))) return st;
+        Launch L(c, X, WPCD_PHASE_MI);
+        CK(launch_mi_solve(m.ch_dev, m.work_dev[K - 1], nw, n, m.n_ch, S, m.NQ, m.kg, m.wg, m.n_terms, cf, m.Vg, Von,
+                           n_I, e_int, static_cast<double *>(X.ws_ref.p), slots, ph, k_out, status, X.err, X.stream));
+    }
+    if (delta || sigma) {
+        Launch L(c, X, WPCD_PHASE_MI);
+        CK(launch_mi_observables(m.ch_dev, m.n_ch, S, n_I, e_int, ph, n_E, e_lab, delta, sigma, X.stream));
+    }
     return WPCD_OK;
 }
 

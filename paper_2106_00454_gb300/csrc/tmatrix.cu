@@ -121,30 +121,6 @@ __device__ __forceinline__ void warp_sum_to(double *v, double *red /* [32][6] */
 // Output, 8 doubles (complex 2 x 2) and 3 phases per item: modes 0, 1 at
 // [S][n_ch][stride = maxN][bin], mode 2 at [S][n_ch][stride = n_E][energy].
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ void phases_of_T(int K, double q, const double *T, double *po)
-{
-    // S = 1 - 2 pi i mu q T
-    const double g = 2.0 * kPi * kMu * q;
-    const double deg = 180.0 / kPi;
-    if (K == 1) {
-        const double sre = 1.0 + g * T[1], sim = -g * T[0];
-        po[0] = 0.5 * atan2(sim, sre) * deg;
-        po[1] = 0.0;
-        po[2] = 0.0;
-    } else {
-        const double s11r = 1.0 + g * T[1], s11i = -g * T[0];
-        const double s22r = 1.0 + g * T[7], s22i = -g * T[6];
-        const double s12r = g * T[3], s12i = -g * T[2];
-        const double dm = 0.5 * atan2(s11i, s11r), dp = 0.5 * atan2(s22i, s22r);
-        const double ph = dm + dp;
-        double x = s12i * cos(ph) - s12r * sin(ph);  // Re(-i S12 e^{-i ph})
-        x = x > 1.0 ? 1.0 : (x < -1.0 ? -1.0 : x);
-        po[0] = dm * deg;
-        po[1] = dp * deg;
-        po[2] = 0.5 * asin(x) * deg;
-    }
-}
-
 template <bool VCID, int MODE>
 __global__ void __launch_bounds__(kTThreads) k_tmat(const ChanDev *chans, int n_ch, int n_terms, const double *coeffs,
                                                     const double *eps_all, const double *C_all, PlanDev plan,

@@ -36,6 +36,14 @@ enum DevErr : int {
 };
 
 // One channel of a projected potential set, as the kernels see it.
+// Channel of an MI set: its grid potential terms Vg [n_terms][n][n] start at
+// vg_off, its on-shell columns Von [n_I][n_terms][K][K][N_Q+1] at von_off;
+// n = K (N_Q + 1).
+struct MiChanDev {
+    int s, J, l, lp, coupled, tz, K, n;
+    long long vg_off, von_off;
+};
+
 struct ChanDev {
     int s, J, l, lp, coupled, tz;
     int N;              // N_WP of its mesh
@@ -75,6 +83,35 @@ __device__ __forceinline__ unsigned dyn_smem_bytes()
     unsigned r;
     asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
     return r;
+}
+
+// S = 1 - 2 pi i mu q T from the continuum T (complex K x K, re/im interleaved,
+// row-major in a 2 x 2 frame) and the phases in degrees: uncoupled delta =
+// arg(S)/2; coupled (Stapp) delta_-, delta_+ = arg(S_11), arg(S_22) / 2 and
+// eps_J = asin(Re[-i S_12 e^{-i(delta_- + delta_+)}]) / 2.  po: {delta or
+// delta_-, delta_+, eps_J}.
+__device__ __forceinline__ void phases_of_T(int K, double q, const double *T, double *po)
+{
+    // S = 1 - 2 pi i mu q T
+    const double g = 2.0 * kPi * kMu * q;
+    const double deg = 180.0 / kPi;
+    if (K == 1) {
+        const double sre = 1.0 + g * T[1], sim = -g * T[0];
+        po[0] = 0.5 * atan2(sim, sre) * deg;
+        po[1] = 0.0;
+        po[2] = 0.0;
+    } else {
+        const double s11r = 1.0 + g * T[1], s11i = -g * T[0];
+        const double s22r = 1.0 + g * T[7], s22i = -g * T[6];
+        const double s12r = g * T[3], s12i = -g * T[2];
+        const double dm = 0.5 * atan2(s11i, s11r), dp = 0.5 * atan2(s22i, s22r);
+        const double ph = dm + dp;
+        double x = s12i * cos(ph) - s12r * sin(ph);  // Re(-i S12 e^{-i ph})
+        x = x > 1.0 ? 1.0 : (x < -1.0 ? -1.0 : x);
+        po[0] = dm * deg;
+        po[1] = dp * deg;
+        po[2] = 0.5 * asin(x) * deg;
+    }
 }
 
 // Shared-memory layouts (doubles) of the kernels, used by kernel and launcher alike.
@@ -174,6 +211,24 @@ cudaError_t launch_plan(const ChanDev *chans_dev, int n_ch, int maxN, const doub
 cudaError_t launch_tbin(const ChanDev *chans_dev, int n_ch, int n_samples, int n_terms, const double *coeffs,
                         const double *eps_all, const double *C_all, PlanDev plan, int maxN, int n_E, double *tout,
                         double *phout, int *err, cudaStream_t st, bool vc_identity, int mode);
+constexpr int kMiMaxNQ = 100;  // MI grid points per l-block: 2 (N_Q + 1) rows fit one CTA's shared memory in FP32
+cudaError_t launch_mi_grid(int NQ, double cmap, const double *glx, const double *glw, double *k, double *w,
+                           cudaStream_t st);
+cudaError_t launch_mi_pot(int gen, const MiChanDev *chans_dev, int n_ch, int NQ, const double *kg, int Lmax,
+                          const double *gp_dev, const double *angx, const double *angw, int n_terms, double *Vg,
+                          cudaStream_t st);
+cudaError_t launch_mi_onshell(int gen, const MiChanDev *chans_dev, int n_ch, int NQ, const double *kg, int n_I,
+                              const double *e_int, int Lmax, const double *gp_dev, const double *angx,
+                              const double *angw, int n_terms, double *Von, cudaStream_t st);
+cudaError_t launch_mi_solve(const MiChanDev *chans_dev, const int *work_dev, int n_work, int n, int n_ch_total,
+                            int n_samples, int NQ, const double *kg, const double *wg, int n_terms,
+                            const double *coeffs, const double *Vg, const double *Von, int n_I, const double *e_int,
+                            double *Vs, int slots, double *ph, double *k_out, int *status, int *err,
+                            cudaStream_t st);
+int mi_slots_per_sm(int n, int NQ);
+cudaError_t launch_mi_observables(const MiChanDev *chans_dev, int n_ch, int n_samples, int n_I, const double *e_int,
+                                  const double *ph, int n_E, const double *e_lab, double *delta, double *sigma,
+                                  cudaStream_t st);
 cudaError_t launch_gather_t(const ChanDev *chans_dev, int n_ch, int n_samples, int n_E, int maxN, PlanDev plan,
                             const double *tbin, double *t_out, cudaStream_t st, bool direct = false);
 cudaError_t launch_observables(const ChanDev *chans_dev, int n_ch, int n_samples, int n_E, int maxN, PlanDev plan,

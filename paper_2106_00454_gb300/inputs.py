@@ -117,6 +117,14 @@ def lab_energies(n: int, lo: float = 1.0, hi: float = 350.0) -> np.ndarray:
     return np.linspace(lo, hi, n)
 
 
+def chebyshev_energies(n: int, e_max: float = 350.0) -> np.ndarray:
+    """n lab energies of a Chebyshev distribution on (0, e_max] (MeV, ascending):
+    e_max (1 - cos((2k - 1) pi / (2n))) / 2, k = 1..n -- the interpolation
+    energies of the MI comparison."""
+    k = np.arange(1, n + 1)
+    return 0.5 * e_max * (1.0 - np.cos((2 * k - 1) * np.pi / (2 * n)))
+
+
 def coefficient_samples(n_samples: int, seed: int = SEED, scaled: bool = True) -> np.ndarray:
     """(n_samples, 14) coefficients c_a * s_a with c ~ N(0, I_14)."""
     rng = np.random.default_rng(seed)
