@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--mi-interp", type=int, default=32,
                     help="MI comparison method: interpolation energies (0 = skip the MI leg)")
     ap.add_argument("--mi-quad", type=int, default=96, help="MI momentum grid points per l-block")
+    ap.add_argument("--angles", type=int, default=32,
+                    help="spin observables (Saclay amplitudes, dsigma/dOmega) at this many angles (0 = skip)")
     return ap.parse_args()
 
 
@@ -356,6 +358,31 @@ def run_wpcd(args, ws, rank, lrank):
               "max_sigma_rel_diff_to_wpcd": float(rel_s.max()),
               "note": "method difference (WPCD N_WP 40-100 vs MI N_Q grid and interpolation), not an error bound"}
 
+    # spin observables (App. A) from the step's phases: M-matrix, Saclay amplitudes, dsigma/dOmega
+    spin = None
+    if args.angles > 0:
+        th = torch.linspace(0.0, np.pi, args.angles, dtype=torch.float64, device=dev)
+        ab = torch.empty((S, nE, args.angles, 5, 2), dtype=torch.float64, device=dev)
+        dsg = torch.empty((S, nE, args.angles), dtype=torch.float64, device=dev)
+        ctx.saclay(wl.channels, d, S, e, th, ab, dsg)  # warm-up
+        sp_ms = []
+        for _ in range(3):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.saclay(wl.channels, d, S, e, th, ab, dsg)
+            b.record(stream)
+            torch.cuda.synchronize()
+            sp_ms.append(a.elapsed_time(b))
+        sp_t = statistics.mean(sp_ms)
+        # optical theorem against the step's sigma_tot: (2 pi / p) Im(a + b)(0) [fm^2 -> mb]
+        p_e = np.sqrt(938.918309 * wl.e_lab / 2.0) / 197.3269804
+        abn = ab.cpu().numpy()
+        opt = 2 * np.pi / p_e[None, :] * (abn[:, :, 0, 0, 1] + abn[:, :, 0, 1, 1]) * 10.0
+        spin = {"observables": "Saclay amplitudes a-e and dsigma/dOmega (App. A)", "angles": args.angles,
+                "ms_per_step": sp_t, "points_per_s": S * nE * args.angles / (sp_t * 1e-3),
+                "optical_theorem_max_rel_dev": float(np.max(np.abs(opt - s.cpu().numpy()) / s.cpu().numpy()))}
+
     sum_n3 = sum((n * (2 if ch.coupled else 1)) ** 3 for n, ch in zip(wl.nwp, wl.channels))
     eig_ms, eig_n = prof["eigen"]
     ref_ms, ref_n = prof["refine"]
@@ -414,6 +441,8 @@ def run_wpcd(args, ws, rank, lrank):
         }
         if mi is not None:
             line["mi_comparison"] = mi
+        if spin is not None:
+            line["spin_observables"] = spin
         if args.serve_seconds > 0:
             line["latency"] = serve_latency(args, lrank, prec)
         if not args.no_cpu_baseline:

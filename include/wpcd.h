@@ -233,6 +233,26 @@ wpcd_status wpcd_solve_host(wpcd_ctx *ctx, int vset_id, const double *coeffs_hos
                             const double *e_lab_host, int n_E, wpcd_precision prec, wpcd_resolvent res,
                             double *t_out_host, double *delta_host, double *sigma_host);
 
+/* ---- spin observables: App. A -----------------------------------------------------------------------
+ * From phase shifts delta_dev [n_samples][n_ch][n_E][3] (degrees, the layout
+ * wpcd_observables writes, channels as passed here) at lab energies
+ * e_lab_dev [n_E] (MeV): the M-matrix partial-wave expansion with the
+ * incoming momentum along z and phi = 0,
+ *   M^s_{m'm} = sqrt(4 pi)/(2 i p) sum_{J,l,l'} sqrt(2l+1) C(l' (m-m') s m' | J m)
+ *               C(l 0 s m | J m) (S_{l'l} - delta_{l'l}) Y_{l'}^{m-m'}(theta, 0),
+ * over the np channels (tz = 0; every channel once, S from the Stapp phases),
+ * then the Saclay amplitudes as the coefficients of
+ *   M = [(a+b) + (a-b)(s1.n)(s2.n) + (c+d)(s1.m)(s2.m) + (c-d)(s1.l)(s2.l) + e(s1+s2).n] / 2
+ * (l, m, n along p + p', p - p', p x p'; the e term along n, the parity-even
+ * form) and dsigma/dOmega = Tr(M M^+)/4 = (|a|^2+|b|^2+|c|^2+|d|^2+|e|^2)/2.
+ * theta_dev [n_theta] radians.  Outputs (device, either may be NULL):
+ * abcde_dev [n_samples][n_E][n_theta][5] complex (re, im) in fm;
+ * dsig_dev [n_samples][n_E][n_theta] mb/sr.  Synchronises.  Errors:
+ * WPCD_ERR_ARG, WPCD_ERR_NOMEM, WPCD_ERR_CUDA. */
+wpcd_status wpcd_saclay(wpcd_ctx *ctx, const wpcd_channel *channels, int n_ch, const double *delta_dev,
+                        int n_samples, const double *e_lab_dev, int n_E, const double *theta_dev, int n_theta,
+                        double *abcde_dev, double *dsig_dev);
+
 /* ---- MI comparison method: Sec. 2.1 (matrix inversion), Sec. 6 (interpolation) ---------------------
  * The LS equation solved directly on a momentum grid: N_Q Gauss-Legendre
  * points mapped by k = c tan(pi (1 + x) / 4) plus the on-shell point p, with
@@ -256,15 +276,21 @@ wpcd_status wpcd_mi_prepare(wpcd_ctx *ctx, const wpcd_channel *channels, int n_c
  * multiples of 180 deg to within 90 deg of the segment start) and form the np
  * total cross section as wpcd_observables does.  Each system is factorised in
  * FP32 (partial pivoting) and its solution refined with FP64 residuals until
- * the correction is below 1e-13 of the solution.  Outputs (device, any may be
+ * it converges (below).  Outputs (device, any may be
  * NULL but not all): k_out_dev [n_samples][n_ch][n_I][2][2] the on-shell K
  * (fm^2, uncoupled channels in [0][0]); delta_dev [n_samples][n_ch][n_E][3]
- * degrees; sigma_dev [n_samples][n_E] mb.  A system whose refinement does not
- * converge is reported by wpcd_sync as WPCD_ERR_NOCONVERGE.  Errors:
- * WPCD_ERR_ARG, WPCD_ERR_HANDLE, WPCD_ERR_NOMEM, WPCD_ERR_BUDGET, WPCD_ERR_CUDA. */
+ * degrees; sigma_dev [n_samples][n_E] mb; status_dev (may be NULL)
+ * [n_samples][n_ch] int, the most refinement steps any energy of that
+ * (sample, channel) took (31: solved by the FP64 fallback below), or -1.  A
+ * system whose refinement neither reaches a correction below 1e-14 of the
+ * solution nor stagnates below 1e-9 of it (the accuracy floor of an FP64
+ * factorisation, ~cond u_64) within 30 steps is solved again by FP64
+ * Gauss-Jordan elimination with partial pivoting; only an exactly singular
+ * system is reported, by wpcd_sync, as WPCD_ERR_NOCONVERGE.  Errors: WPCD_ERR_ARG,
+ * WPCD_ERR_HANDLE, WPCD_ERR_NOMEM, WPCD_ERR_BUDGET, WPCD_ERR_CUDA. */
 wpcd_status wpcd_mi_solve(wpcd_ctx *ctx, int mi_id, const double *coeffs_dev, int n_samples, const double *e_int_dev,
                           int n_I, const double *e_lab_dev, int n_E, double *k_out_dev, double *delta_dev,
-                          double *sigma_dev);
+                          double *sigma_dev, int *status_dev);
 
 /* Free a mesh, vset, eig or MI handle.  Errors: WPCD_ERR_HANDLE. */
 wpcd_status wpcd_release(wpcd_ctx *ctx, int id);

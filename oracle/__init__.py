@@ -73,6 +73,9 @@ def lib():
                 "or_S_from_K": (None, [i, d, _dp, _dp]),
                 "or_interp_phase_tlab": (None, [i, _dp, _dp, i, d, _dp]),
                 "or_mi_batch": (i, [i, _ip, i, _dp, i, i, _dp, i, d, i, _dp, i, _dp, _dp, _dp, _dp, i]),
+                "or_cg": (d, [i, i, i, i, i, i]),
+                "or_ylm": (d, [i, i, d]),
+                "or_saclay": (None, [i, _ip, _dp, d, i, _dp, _dp, _dp, _dp]),
                 "or_batch": (i, [i, _ip, _ip, _lp, _dp, i, i, _lp, _dp, i, _dp, i, _dp, i, _dp, _dp, _dp, i]),
                 "or_max_threads": (i, []),
             }
@@ -356,6 +359,31 @@ def mi_batch(channels, gen, gp, n_terms, coeffs, e_int, e_lab, NQ=96, cmap=1.0, 
     rc = lib().or_mi_batch(n_ch, _i(chdesc), int(gen), _d(_f64(gp)), n_terms, S, _d(coeffs), NQ, float(cmap), nI,
                            _d(e_int), nE, _d(e_lab), _d(k_out), _d(delta), _d(sigma), int(n_threads))
     return k_out, delta, sigma, rc
+
+
+def cg(j1, m1, j2, m2, J, M) -> float:
+    return lib().or_cg(j1, m1, j2, m2, J, M)
+
+
+def ylm(l, m, theta) -> float:
+    return lib().or_ylm(l, m, float(theta))
+
+
+def saclay(channels, ph, p, theta, want_m=False):
+    """Saclay amplitudes [n_theta, 5] complex (fm), dsigma/dOmega [n_theta]
+    (mb/sr) and optionally the 4 x 4 M-matrices, from the phases ph [n_ch, 3]
+    (degrees) of the np channels at momentum p."""
+    n_ch = len(channels)
+    chdesc = np.ascontiguousarray(np.array(channels, dtype=np.int32).reshape(n_ch, 6))
+    ph = _f64(ph)
+    theta = _f64(np.atleast_1d(theta))
+    nt = theta.shape[0]
+    ab = np.zeros((nt, 5), dtype=np.complex128)
+    ds = np.zeros(nt)
+    M = np.zeros((nt, 4, 4), dtype=np.complex128) if want_m else None
+    lib().or_saclay(n_ch, _i(chdesc), _d(ph), float(p), nt, _d(theta), ab.ctypes.data_as(_dp), _d(ds),
+                    M.ctypes.data_as(_dp) if want_m else None)
+    return (ab, ds, M) if want_m else (ab, ds)
 
 
 def max_threads() -> int:

@@ -1125,6 +1125,197 @@ int or_mi_batch(int n_ch, const int *chdesc, int gen, const double *gp, int n_te
     return err;
 }
 
+/* ------------------------------------------------------------------------- */
+/* App. A: spin observables of np scattering.  The M-matrix of Eq. "M-matrix */
+/* PWE" with the incoming momentum along z, phi = 0 and momentum-space        */
+/* partial waves (no i^(l-l') phase, consistent with the real symmetric K of  */
+/* Sec. 2.1 and the Stapp S with its factor i in S_12), every np channel once */
+/* (reading: the printed factor [1 - (-1)^(l+s+T_Z)] belongs to identical     */
+/* nucleons; for np it would drop 1S0 and 3S1):                               */
+/*   M^s_{m'm} = sqrt(4 pi)/(2 i p) sum_{J,l,l'} sqrt(2l+1)                   */
+/*               C(l' (m-m') s m' | J m) C(l 0 s m | J m) (S_{l'l} - d_{l'l}) */
+/*               Y_{l'}^{m-m'}(theta, 0).                                     */
+/* The Saclay amplitudes a..e are the coefficients of M in the operator basis */
+/* of Eq. "M matrix in terms of saclay amplitudes" (unit vectors l, m, n of   */
+/* Eq. "kinematics vectors"), obtained by traces over the 4 x 4 two-nucleon    */
+/* spin space; dsigma/dOmega = Tr(M M^dag)/4.  Reading: the e term is taken   */
+/* along n, e (sigma_1 + sigma_2) . n -- the printed "m" would make it parity  */
+/* odd (m is polar, n = p x p' axial), and only the n form completes the      */
+/* basis of a parity-conserving M.                                            */
+/* ------------------------------------------------------------------------- */
+static double or_lfact(int n) { return lgamma((double)n + 1.0); }
+
+/* Clebsch-Gordan <j1 m1 j2 m2 | J M> for integer spins (Racah's formula). */
+double or_cg(int j1, int m1, int j2, int m2, int J, int M)
+{
+    if (m1 + m2 != M || abs(m1) > j1 || abs(m2) > j2 || abs(M) > J || J < abs(j1 - j2) || J > j1 + j2) return 0.0;
+    double pre = 0.5 * (log(2.0 * J + 1.0) + or_lfact(J + j1 - j2) + or_lfact(J - j1 + j2) + or_lfact(j1 + j2 - J) -
+                        or_lfact(j1 + j2 + J + 1) + or_lfact(J + M) + or_lfact(J - M) + or_lfact(j1 - m1) +
+                        or_lfact(j1 + m1) + or_lfact(j2 - m2) + or_lfact(j2 + m2));
+    double sum = 0.0;
+    for (int k = 0; k <= j1 + j2 - J; ++k) {
+        int a = j1 + j2 - J - k, b = j1 - m1 - k, c = j2 + m2 - k, d = J - j2 + m1 + k, e = J - j1 - m2 + k;
+        if (a < 0 || b < 0 || c < 0 || d < 0 || e < 0) continue;
+        double t = exp(pre - or_lfact(k) - or_lfact(a) - or_lfact(b) - or_lfact(c) - or_lfact(d) - or_lfact(e));
+        sum += (k & 1) ? -t : t;
+    }
+    return sum;
+}
+
+/* Y_l^m(theta, phi = 0) with the Condon-Shortley phase. */
+double or_ylm(int l, int m, double theta)
+{
+    int am = abs(m);
+    if (am > l) return 0.0;
+    double x = cos(theta), s = sin(theta);
+    /* P_l^am without the Condon-Shortley phase by the upward recurrences */
+    double pmm = 1.0;
+    for (int i = 1; i <= am; ++i) pmm *= (2.0 * i - 1.0) * s;
+    double plm = pmm;
+    if (l > am) {
+        double pm1 = x * (2.0 * am + 1.0) * pmm, pm0 = pmm;
+        plm = pm1;
+        for (int ll = am + 2; ll <= l; ++ll) {
+            double pn = ((2.0 * ll - 1.0) * x * pm1 - (ll + am - 1.0) * pm0) / (ll - am);
+            pm0 = pm1;
+            pm1 = pn;
+            plm = pn;
+        }
+    }
+    double norm = sqrt((2.0 * l + 1.0) / (4.0 * OR_PI) * exp(or_lfact(l - am) - or_lfact(l + am)));
+    double y = norm * plm * ((am & 1) ? -1.0 : 1.0); /* (-1)^m for m >= 0 */
+    if (m < 0 && (am & 1)) y = -y;                    /* Y_l^{-m} = (-1)^m Y_l^m at phi = 0 */
+    return y;
+}
+
+/* Partial-wave S of one channel from its (Stapp) phases, K x K. */
+static void or_S_of_phases(int K, const double *phdeg, double complex *S)
+{
+    const double r = OR_PI / 180.0;
+    if (K == 1) {
+        S[0] = cexp(2.0 * I * phdeg[0] * r);
+        return;
+    }
+    double dm = phdeg[0] * r, dp = phdeg[1] * r, e2 = 2.0 * phdeg[2] * r;
+    S[0] = cos(e2) * cexp(2.0 * I * dm);
+    S[3] = cos(e2) * cexp(2.0 * I * dp);
+    S[1] = S[2] = I * sin(e2) * cexp(I * (dm + dp));
+}
+
+static void pauli_dot(const double *v, double complex out[2][2])
+{
+    out[0][0] = v[2];
+    out[0][1] = v[0] - I * v[1];
+    out[1][0] = v[0] + I * v[1];
+    out[1][1] = -v[2];
+}
+
+static void kron2(double complex a[2][2], double complex b[2][2], double complex out[4][4])
+{
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+            for (int k = 0; k < 2; ++k)
+                for (int l = 0; l < 2; ++l) out[2 * i + k][2 * j + l] = a[i][j] * b[k][l];
+}
+
+static double complex trace_prod(double complex A[4][4], double complex B[4][4])
+{
+    double complex t = 0.0;
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 4; ++k) t += A[i][k] * B[k][i];
+    return t;
+}
+
+/* For every angle: the Saclay amplitudes abcde[t][5] (fm) and dsig[t]       */
+/* (mb/sr) at momentum p from the phases ph [n_ch][3] (degrees) of the np     */
+/* channels (tz = 0; others are skipped).  Also returns the M-matrix if       */
+/* M_out is given: [t][4][4] in the product basis (up-up, up-down, down-up,   */
+/* down-down).                                                                */
+void or_saclay(int n_ch, const int *chdesc, const double *ph, double p, int n_th, const double *theta,
+               double complex *abcde, double *dsig, double complex *M_out)
+{
+    for (int t = 0; t < n_th; ++t) {
+        const double th = theta[t];
+        double complex M0 = 0.0, M1[3][3]; /* M1[m'+1][m+1] */
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) M1[a][b] = 0.0;
+        for (int c = 0; c < n_ch; ++c) {
+            const int *d = chdesc + 6 * c;
+            if (d[5] != 0) continue;
+            int s = d[0], J = d[1], K = d[4] ? 2 : 1;
+            int ls[2];
+            ls[0] = d[4] ? J - 1 : d[2];
+            ls[1] = d[4] ? J + 1 : d[2];
+            double complex S[4];
+            or_S_of_phases(K, ph + 3 * c, S);
+            for (int ip = 0; ip < K; ++ip)
+                for (int il = 0; il < K; ++il) {
+                    int lp = ls[ip], l = ls[il];
+                    double complex amp = S[ip * K + il] - (ip == il ? 1.0 : 0.0);
+                    for (int m = -s; m <= s; ++m)
+                        for (int mp = -s; mp <= s; ++mp) {
+                            double w = sqrt(4.0 * OR_PI) * sqrt(2.0 * l + 1.0) * or_cg(lp, m - mp, s, mp, J, m) *
+                                       or_cg(l, 0, s, m, J, m) * or_ylm(lp, m - mp, th);
+                            if (w == 0.0) continue;
+                            double complex v = w * amp / (2.0 * I * p);
+                            if (s == 0) M0 += v;
+                            else M1[mp + 1][m + 1] += v;
+                        }
+                }
+        }
+        /* to the product basis: |1,1> = uu, |1,0> = (ud+du)/sqrt2, |1,-1> = dd, |0,0> = (ud-du)/sqrt2 */
+        double complex U[4][4] = {{0}}; /* columns: coupled states (1,1),(1,0),(1,-1),(0,0) */
+        const double h = 1.0 / sqrt(2.0);
+        U[0][0] = 1.0;
+        U[1][1] = h;
+        U[2][1] = h;
+        U[3][2] = 1.0;
+        U[1][3] = h;
+        U[2][3] = -h;
+        double complex Mc[4][4] = {{0}}, M[4][4];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) Mc[2 - a][2 - b] = M1[a][b]; /* coupled index 0 <-> m = +1 */
+        Mc[3][3] = M0;
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                double complex acc = 0.0;
+                for (int k = 0; k < 4; ++k)
+                    for (int l = 0; l < 4; ++l) acc += U[i][k] * Mc[k][l] * conj(U[j][l]);
+                M[i][j] = acc;
+            }
+        /* unit vectors: l along p + p', m along p - p', n along p x p' */
+        double lv[3] = {sin(0.5 * th), 0.0, cos(0.5 * th)}, mv[3] = {-cos(0.5 * th), 0.0, sin(0.5 * th)},
+               nv[3] = {0.0, 1.0, 0.0};
+        double complex sl[2][2], sm[2][2], sn[2][2], id[2][2] = {{1, 0}, {0, 1}};
+        pauli_dot(lv, sl);
+        pauli_dot(mv, sm);
+        pauli_dot(nv, sn);
+        double complex NN[4][4], MM[4][4], LL[4][4], S1[4][4], S2[4][4];
+        kron2(sn, sn, NN);
+        kron2(sm, sm, MM);
+        kron2(sl, sl, LL);
+        kron2(sn, id, S1); /* (sigma_1 + sigma_2) . n: the parity-even spin-orbit form (reading) */
+        kron2(id, sn, S2);
+        double complex trM = 0.0;
+        for (int i = 0; i < 4; ++i) trM += M[i][i];
+        double complex apb = 0.5 * trM, amb = 0.5 * trace_prod(M, NN), cpd = 0.5 * trace_prod(M, MM),
+                       cmd = 0.5 * trace_prod(M, LL), e = 0.25 * (trace_prod(M, S1) + trace_prod(M, S2));
+        double complex *o = abcde + (size_t)t * 5;
+        o[0] = 0.5 * (apb + amb);
+        o[1] = 0.5 * (apb - amb);
+        o[2] = 0.5 * (cpd + cmd);
+        o[3] = 0.5 * (cpd - cmd);
+        o[4] = e;
+        double tr = 0.0;
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) tr += creal(M[i][j] * conj(M[i][j]));
+        dsig[t] = 0.25 * tr * 10.0; /* fm^2 -> mb */
+        if (M_out)
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) M_out[(size_t)t * 16 + i * 4 + j] = M[i][j];
+    }
+}
+
 int or_max_threads(void)
 {
 #ifdef _OPENMP

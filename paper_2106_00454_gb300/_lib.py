@@ -20,7 +20,7 @@ EXPORTED = [
     "wpcd_release", "wpcd_kernel_launches", "wpcd_profile", "wpcd_profile_read",
     "wpcd_channel_solve_noalloc", "wpcd_serve_start", "wpcd_serve_stop", "wpcd_submit", "wpcd_poll", "wpcd_wait",
     "wpcd_release_result", "wpcd_serve_stats", "wpcd_batched_dgemm", "wpcd_tuning", "wpcd_mi_prepare",
-    "wpcd_mi_solve",
+    "wpcd_mi_solve", "wpcd_saclay",
 ]
 
 
@@ -64,8 +64,9 @@ _SIG = {
     "wpcd_tmatrix": (_i, [_vp, _i, _vp, _i, _i, _vp]),
     "wpcd_observables": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
     "wpcd_observables_res": (_i, [_vp, _i, _vp, _i, _i, _vp, _vp]),
+    "wpcd_saclay": (_i, [_vp, _vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _vp]),
     "wpcd_mi_prepare": (_i, [_vp, _vp, _i, _i, _vp, _i, _i, _i, ctypes.c_double, _vp]),
-    "wpcd_mi_solve": (_i, [_vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _vp, _vp]),
+    "wpcd_mi_solve": (_i, [_vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _vp, _vp, _vp]),
     "wpcd_solve": (_i, [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp, _vp, _vp]),
     "wpcd_solve_host": (_i, [_vp, _i, _vp, _i, _vp, _i, _i, _i, _vp, _vp, _vp]),
     "wpcd_release": (_i, [_vp, _i]),

@@ -195,6 +195,17 @@ class Context:
         _ck(self.lib.wpcd_solve(self.h, vset_id, _ptr(coeffs), n_samples, _ptr(e_lab), e_lab.numel(), prec,
                                 res, _ptr(t_out), _ptr(delta), _ptr(sigma)), "wpcd_solve")
 
+    # ------------------------------------------------------------------ spin observables
+    def saclay(self, channels, delta, n_samples, e_lab, theta, abcde=None, dsig=None):
+        """Saclay amplitudes (abcde: float64 device tensor [S, n_E, n_theta, 5, 2])
+        and dsigma/dOmega (dsig: [S, n_E, n_theta] mb/sr) from the phases delta
+        [S, n_ch, n_E, 3] of the channels, at angles theta (radians)."""
+        n = len(channels)
+        arr = (_lib.wpcd_channel * n)(*[_lib.wpcd_channel(*c.astuple()) if hasattr(c, "astuple")
+                                        else _lib.wpcd_channel(*c) for c in channels])
+        _ck(self.lib.wpcd_saclay(self.h, arr, n, _ptr(delta), n_samples, _ptr(e_lab), e_lab.numel(), _ptr(theta),
+                                 theta.numel(), _ptr(abcde), _ptr(dsig)), "wpcd_saclay")
+
     # ------------------------------------------------------------------ MI comparison method
     def mi_prepare(self, channels, gen, gen_params, n_terms, n_quad=96, c_map=1.0) -> int:
         n = len(channels)
@@ -206,11 +217,13 @@ class Context:
                                      ctypes.byref(mid)), "wpcd_mi_prepare")
         return mid.value
 
-    def mi_solve(self, mi_id, coeffs, n_samples, e_int, e_lab, k_out=None, delta=None, sigma=None):
+    def mi_solve(self, mi_id, coeffs, n_samples, e_int, e_lab, k_out=None, delta=None, sigma=None, status=None):
         """MI at the interpolation energies e_int (device tensor, MeV) and the
-        phases / cross sections interpolated to e_lab (device tensor)."""
+        phases / cross sections interpolated to e_lab (device tensor); status
+        (int32 device tensor [S, n_ch]) receives the refinement step counts."""
         _ck(self.lib.wpcd_mi_solve(self.h, mi_id, _ptr(coeffs), n_samples, _ptr(e_int), e_int.numel(), _ptr(e_lab),
-                                   e_lab.numel(), _ptr(k_out), _ptr(delta), _ptr(sigma)), "wpcd_mi_solve")
+                                   e_lab.numel(), _ptr(k_out), _ptr(delta), _ptr(sigma), _ptr(status)),
+            "wpcd_mi_solve")
 
     def solve_host(self, vset_id, coeffs, n_samples, e_lab, t_out=None, delta=None, sigma=None, prec=PREC_FP64,
                    res=AVG_FREE_BIN):
@@ -305,3 +318,10 @@ class Model:
     @property
     def n_ch(self):
         return len(self.wl.channels)
+
+    def release(self):
+        """Free the projected set and the meshes."""
+        self.ctx.release(self.vset)
+        for mid in self.mesh_of_n.values():
+            self.ctx.release(mid)
+        self.mesh_of_n = {}

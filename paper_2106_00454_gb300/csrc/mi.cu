@@ -17,9 +17,10 @@
 // set (k_mi_pot_grid) and the on-shell rows once per energy list
 // (k_mi_pot_onshell); k_mi_solve runs persistent CTAs, each owning a slot of
 // FP64 scratch for one (sample, channel) matrix V = V0 + sum_a c_a V_a, and for
-// every energy factorises 1 - V D in FP32 in shared memory (partial pivoting;
-// FP32 issues at 58x the FP64 rate) and refines the solution to FP64 accuracy
-// with FP64 residuals r = b - (x - V (D x)) (classical iterative refinement).
+// every energy inverts 1 - V D in FP32 in shared memory (Gauss-Jordan, partial
+// pivoting; FP32 issues at 58x the FP64 rate) and refines the solution to FP64
+// accuracy with FP64 residuals r = b - (x - V (D x)) (classical iterative
+// refinement: every step is two matrix-vector products).
 #include <math.h>
 
 #include "potential.cuh"
@@ -27,8 +28,8 @@
 
 namespace wpcd {
 
-constexpr int kMiThreads = 256;
-constexpr int kMiMaxRefine = 10;
+constexpr int kMiThreads = 512;  // one CTA per SM for coupled systems: 16 warps to hide latency
+constexpr int kMiMaxRefine = 30;
 
 // ------------------------------------------------------------------------------------- grid
 __global__ void k_mi_grid(int NQ, double cmap, const double *glx, const double *glw, double *k, double *w)
@@ -162,25 +163,30 @@ cudaError_t launch_mi_onshell(int gen, const MiChanDev *chans_dev, int n_ch, int
 }
 
 // ------------------------------------------------------------------------------------- solve
-// Shared memory of one CTA for matrices up to n: A float [n][n] | D double [M] |
+// Shared memory of one CTA for matrices up to n: A float [n][ld] | D double [M] |
 // b, x, r double [2][n] | y float [2][n] | perm int [n, even] | reduction double [64].
+__host__ __device__ inline int mi_ld(int n) { return (n + 3) & ~3; }  // rows padded to 16 bytes (float4 access)
+
 __host__ __device__ inline size_t mi_smem(int n, int M)
 {
-    size_t a = (size_t)n * n * 4;
-    a = (a + 7) & ~(size_t)7;
+    size_t a = (size_t)n * mi_ld(n) * 4;
+    a = (a + 15) & ~(size_t)15;
     return a + (size_t)M * 8 + 3 * (size_t)2 * n * 8 + (size_t)2 * n * 4 + (size_t)(n + (n & 1)) * 4 + 64 * 8;
 }
 
 size_t mi_smem_bytes(int n, int M) { return mi_smem(n, M); }
 
+// Maximum over the CTA that propagates NaN (fmax would drop it).
+__device__ __forceinline__ double nan_max(double a, double b) { return (b > a || b != b) ? b : a; }
+
 __device__ __forceinline__ double mi_block_max(double v, double *red)
 {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, o));
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = nan_max(t, red[w]);
     return t;
 }
 
@@ -212,17 +218,18 @@ __global__ void __launch_bounds__(kMiThreads) k_mi_solve(const MiChanDev *chans,
         if (tid == 0) record_error(err, kDevBadSize);
         return;
     }
-    extern __shared__ double mi_sm[];
+    extern __shared__ __align__(16) double mi_sm[];
     unsigned char *sb = reinterpret_cast<unsigned char *>(mi_sm);
     const int n0 = chans[work_ch[0]].n;  // every work channel of a launch has the same n
-    size_t off = ((size_t)n0 * n0 * 4 + 7) & ~(size_t)7;
+    const int ld = mi_ld(n0);
+    size_t off = ((size_t)n0 * ld * 4 + 15) & ~(size_t)15;
     float *A = reinterpret_cast<float *>(sb);
     double *D = reinterpret_cast<double *>(sb + off);
     double *bv = D + M, *xv = bv + 2 * n0, *rv = xv + 2 * n0;
     float *yv = reinterpret_cast<float *>(rv + 2 * n0);
     int *perm = reinterpret_cast<int *>(yv + 2 * n0);
     double *red = reinterpret_cast<double *>(perm + n0 + (n0 & 1));
-    double *Vs = Vs_all + (size_t)blockIdx.x * n0 * n0;
+    double *Vs = Vs_all + (size_t)blockIdx.x * 2 * n0 * n0;  // V, then the FP64 fallback matrix
 
     for (int item = blockIdx.x; item < n_samples * n_work; item += gridDim.x) {
         const int smp = item / n_work, cidx = work_ch[item - smp * n_work];
@@ -262,7 +269,7 @@ __global__ void __launch_bounds__(kMiThreads) k_mi_solve(const MiChanDev *chans,
             // A = 1 - V D (FP32), right-hand sides b_bb = V[:, (bb, N)] (FP64)
             for (int e = tid; e < n * n; e += nt) {
                 const int r = e / n, c = e - r * n;
-                A[e] = (float)((r == c ? 1.0 : 0.0) - Vs[e] * D[c % M]);
+                A[(size_t)r * ld + c] = (float)((r == c ? 1.0 : 0.0) - Vs[e] * D[c % M]);
             }
             for (int e = tid; e < K * n; e += nt) {
                 const int bb = e / n, r = e - bb * n;
@@ -270,15 +277,20 @@ __global__ void __launch_bounds__(kMiThreads) k_mi_solve(const MiChanDev *chans,
                 xv[bb * n0 + r] = 0.0;
                 rv[bb * n0 + r] = bv[bb * n0 + r];
             }
-            for (int r = tid; r < n; r += nt) perm[r] = r;
+            for (int r = tid; r < n; r += nt) {
+                perm[r] = r;
+                for (int c = n; c < ld; ++c) A[(size_t)r * ld + c] = 0.0f;
+            }
             __syncthreads();
-            // LU with partial pivoting (rows swapped in place, perm[] tracks them)
+            // In-place Gauss-Jordan inversion with partial pivoting (rows swapped
+            // in place, perm[] tracks them): afterwards A holds W with
+            // W (P r) = (1 - V D)^-1 r, (P r)_k = r_perm[k].
             for (int k = 0; k < n; ++k) {
                 if (warp == 0) {
                     float best = -1.0f;
                     int bi = k;
                     for (int r = k + lane; r < n; r += 32) {
-                        const float v = fabsf(A[(size_t)r * n + k]);
+                        const float v = fabsf(A[(size_t)r * ld + k]);
                         if (v > best) { best = v; bi = r; }
                     }
                     for (int o = 16; o > 0; o >>= 1) {
@@ -286,90 +298,163 @@ __global__ void __launch_bounds__(kMiThreads) k_mi_solve(const MiChanDev *chans,
                         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
                     }
-                    if (lane == 0) reinterpret_cast<int *>(red)[0] = bi;
+                    if (lane == 0) {
+                        reinterpret_cast<int *>(red)[0] = bi;
+                        reinterpret_cast<float *>(red)[1] = A[(size_t)bi * ld + k];  // the pivot
+                    }
                 }
                 __syncthreads();
                 const int pr = reinterpret_cast<int *>(red)[0];
+                const float rinv = 1.0f / reinterpret_cast<float *>(red)[1];
                 if (pr != k) {
                     for (int c = tid; c < n; c += nt) {
-                        const float t = A[(size_t)k * n + c];
-                        A[(size_t)k * n + c] = A[(size_t)pr * n + c];
-                        A[(size_t)pr * n + c] = t;
+                        const float t = A[(size_t)k * ld + c];
+                        A[(size_t)k * ld + c] = A[(size_t)pr * ld + c];
+                        A[(size_t)pr * ld + c] = t;
                     }
                     if (tid == 0) {
                         const int t = perm[k];
                         perm[k] = perm[pr];
                         perm[pr] = t;
                     }
+                    __syncthreads();
                 }
+                // the other rows' column-k entries, then row k divided by the pivot
+                for (int r = tid; r < n; r += nt) yv[r] = r == k ? 0.0f : A[(size_t)r * ld + k];
+                for (int c = tid; c < n; c += nt) A[(size_t)k * ld + c] = c == k ? rinv : A[(size_t)k * ld + c] * rinv;
                 __syncthreads();
-                const float piv = A[(size_t)k * n + k];
-                const float rinv = piv != 0.0f ? 1.0f / piv : 0.0f;
-                // trailing update, one warp per row: the multiplier l = a_rk / a_kk,
-                // a_rc -= l a_kc, then l stored in place of a_rk by the same warp
-                for (int r = k + 1 + warp; r < n; r += nw) {
-                    const float l = A[(size_t)r * n + k] * rinv;
-                    for (int c = k + 1 + lane; c < n; c += 32) A[(size_t)r * n + c] -= l * A[(size_t)k * n + c];
-                    __syncwarp();
-                    if (lane == 0) A[(size_t)r * n + k] = l;
+                // eliminate column k from every other row (one warp per row); the
+                // column-k entry becomes -f / pivot (the in-place inverse column)
+                // (four columns per lane: the padding columns n..ld-1 stay finite and unused)
+                const float4 *Ak4 = reinterpret_cast<const float4 *>(A + (size_t)k * ld);
+                for (int r = warp; r < n; r += nw) {
+                    if (r == k) continue;
+                    const float f = yv[r];
+                    float4 *Ar4 = reinterpret_cast<float4 *>(A + (size_t)r * ld);
+                    for (int c = lane; c < (ld >> 2); c += 32) {
+                        const float4 a = Ar4[c], b = Ak4[c];
+                        Ar4[c] = make_float4(fmaf(-f, b.x, a.x), fmaf(-f, b.y, a.y), fmaf(-f, b.z, a.z), fmaf(-f, b.w, a.w));
+                    }
+                    __syncwarp();  // the lane that updated column k has written it
+                    if (lane == 0) A[(size_t)r * ld + k] = -f * A[(size_t)k * ld + k];
                 }
                 __syncthreads();
             }
-            // iterative refinement: y = (LU)^-1 P r in FP32, x += y, r = b - (x - V D x) in FP64
+            // iterative refinement: y = W (P r) in FP32, x += y, r = b - (x - V D x) in FP64
             bool conv = false;
             int it = 0;
+            double ym_prev = 0.0;
             for (; it < kMiMaxRefine && !conv; ++it) {
-                for (int e = tid; e < K * n; e += nt) {
-                    const int bb = e / n, r = e - bb * n;
-                    yv[bb * n0 + r] = (float)rv[bb * n0 + perm[r]];
-                }
-                __syncthreads();
-                for (int j = 0; j < n; ++j) {  // forward, unit lower
-                    const float y0 = yv[j], y1 = K == 2 ? yv[n0 + j] : 0.0f;
-                    for (int r = j + 1 + tid; r < n; r += nt) {
-                        const float l = A[(size_t)r * n + j];
-                        yv[r] -= l * y0;
-                        if (K == 2) yv[n0 + r] -= l * y1;
+                double ym = 0.0, xm = 0.0;  // NaN-propagating maxima: a NaN never passes as converged
+                for (int r = warp; r < n; r += nw)
+                    for (int bb = 0; bb < K; ++bb) {
+                        float acc = 0.0f;
+                        for (int c = lane; c < n; c += 32)
+                            acc = fmaf(A[(size_t)r * ld + c], (float)rv[bb * n0 + perm[c]], acc);
+                        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                        if (lane == 0) {
+                            const double y = (double)acc, xn = xv[bb * n0 + r] + y;
+                            xv[bb * n0 + r] = xn;
+                            const double ay = fabs(y), ax = fabs(xn);
+                            ym = (ay > ym || ay != ay) ? ay : ym;
+                            xm = (ax > xm || ax != ax) ? ax : xm;
+                        }
                     }
-                    __syncthreads();
-                }
-                for (int j = n - 1; j >= 0; --j) {  // backward, upper
-                    const float u = A[(size_t)j * n + j];
-                    const float y0 = yv[j] / u, y1 = K == 2 ? yv[n0 + j] / u : 0.0f;
-                    __syncthreads();  // every thread has read y_j before it is overwritten
-                    if (tid == 0) {
-                        yv[j] = y0;
-                        if (K == 2) yv[n0 + j] = y1;
-                    }
-                    for (int r = tid; r < j; r += nt) {
-                        const float a = A[(size_t)r * n + j];
-                        yv[r] -= a * y0;
-                        if (K == 2) yv[n0 + r] -= a * y1;
-                    }
-                    __syncthreads();
-                }
-                double ym = 0.0, xm = 0.0;
-                for (int e = tid; e < K * n; e += nt) {
-                    const int bb = e / n, r = e - bb * n;
-                    xv[bb * n0 + r] += (double)yv[bb * n0 + r];
-                    ym = fmax(ym, fabs((double)yv[bb * n0 + r]));
-                    xm = fmax(xm, fabs(xv[bb * n0 + r]));
-                }
                 ym = mi_block_max(ym, red);
                 xm = mi_block_max(xm, red + 32);
-                conv = ym <= 1e-13 * xm;  // the correction is at the level of the FP64 residual
+                // done when the correction is negligible, or when it has stopped
+                // shrinking at the accuracy floor of the FP64 residual (about
+                // cond(A) u_64, the accuracy of an FP64 factorisation too)
+                conv = ym <= 1e-14 * xm || (it > 0 && ym > 0.25 * ym_prev && ym <= 1e-9 * xm);
+                ym_prev = ym;
+                if (conv) break;  // (uniform: conv comes from CTA-wide maxima)
                 // r = b - x + V (D x): one warp per row, lanes over the columns
                 for (int r = warp; r < n; r += nw)
                     for (int bb = 0; bb < K; ++bb) {
                         double acc = 0.0;
-                        for (int c = lane; c < n; c += 32) acc = fma(Vs[(size_t)r * n + c] * D[c % M], xv[bb * n0 + c], acc);
+                        const double *Vr = Vs + (size_t)r * n;
+                        double acc2 = 0.0;  // two chains keep two loads in flight
+                        int c = lane;
+                        for (; c + 32 < n; c += 64) {
+                            const int c1 = c + 32;
+                            acc = fma(Vr[c] * D[c < M ? c : c - M], xv[bb * n0 + c], acc);
+                            acc2 = fma(Vr[c1] * D[c1 < M ? c1 : c1 - M], xv[bb * n0 + c1], acc2);
+                        }
+                        if (c < n) acc = fma(Vr[c] * D[c < M ? c : c - M], xv[bb * n0 + c], acc);
+                        acc += acc2;
                         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                         if (lane == 0) rv[bb * n0 + r] = bv[bb * n0 + r] - xv[bb * n0 + r] + acc;
                     }
                 __syncthreads();
             }
+            int steps = conv ? it + 1 : it;  // the loop left by break on convergence
+            if (!conv) {
+                // The FP32 inverse is too inexact for refinement to converge
+                // (cond(A) u_32 ~ 1): solve this system by FP64 Gauss-Jordan
+                // elimination with partial pivoting in the slot's second FP64
+                // matrix (global memory; rare, so plain), right-hand sides
+                // carried along.
+                double *G = Vs + (size_t)n0 * n0;
+                for (int e = tid; e < n * n; e += nt) {
+                    const int r = e / n, c = e - r * n;
+                    G[e] = (r == c ? 1.0 : 0.0) - Vs[e] * D[c < M ? c : c - M];
+                }
+                for (int e = tid; e < K * n; e += nt) xv[(e / n) * n0 + e % n] = bv[(e / n) * n0 + e % n];
+                __syncthreads();
+                bool ok = true;
+                for (int k = 0; k < n; ++k) {
+                    if (warp == 0) {
+                        double best = -1.0;
+                        int bi = k;
+                        for (int r = k + lane; r < n; r += 32) {
+                            const double v = fabs(G[(size_t)r * n + k]);
+                            if (v > best) { best = v; bi = r; }
+                        }
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                        }
+                        if (lane == 0) reinterpret_cast<int *>(red)[0] = bi;
+                    }
+                    __syncthreads();
+                    const int pr = reinterpret_cast<int *>(red)[0];
+                    if (pr != k) {
+                        for (int c = tid; c < n; c += nt) {
+                            const double t = G[(size_t)k * n + c];
+                            G[(size_t)k * n + c] = G[(size_t)pr * n + c];
+                            G[(size_t)pr * n + c] = t;
+                        }
+                        if (tid < K) {
+                            const double t = xv[tid * n0 + k];
+                            xv[tid * n0 + k] = xv[tid * n0 + pr];
+                            xv[tid * n0 + pr] = t;
+                        }
+                    }
+                    __syncthreads();
+                    const double piv = G[(size_t)k * n + k];
+                    if (piv == 0.0) ok = false;
+                    const double rinv = piv != 0.0 ? 1.0 / piv : 0.0;
+                    __syncthreads();  // every thread holds the pivot before row k is rescaled
+                    for (int c = tid; c < n; c += nt) G[(size_t)k * n + c] *= rinv;
+                    if (tid < K) xv[tid * n0 + k] *= rinv;
+                    __syncthreads();
+                    for (int r = warp; r < n; r += nw) {
+                        if (r == k) continue;
+                        const double f = G[(size_t)r * n + k];
+                        __syncwarp();
+                        for (int c = lane; c < n; c += 32) G[(size_t)r * n + c] -= f * G[(size_t)k * n + c];
+                        if (lane < K) xv[lane * n0 + r] -= f * xv[lane * n0 + k];
+                    }
+                    __syncthreads();
+                }
+                if (ok) {
+                    conv = true;
+                    steps = kMiMaxRefine + 1;  // marks the FP64 fallback in the status
+                }
+            }
             if (!conv) worst = -1;
-            else if (worst >= 0 && it > worst) worst = it;
+            else if (worst >= 0 && steps > worst) worst = steps;
             if (tid == 0) {
                 // on-shell K, T = (1 + i pi mu p K)^-1 K, phases
                 double Km[4] = {0, 0, 0, 0};

@@ -175,24 +175,40 @@ __device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned &r0, unsigned &r
 constexpr int kOzStages = 3;                 // cp.async ring depth
 constexpr int kOzStageElems = 2 * 64 * kOzLd;  // A and B tiles of one step (bf16)
 
-// C[b] = A[b] B[b] from row slices of A and column slices of B.  64 x 64
+// C[b] = A[b] B[b] from row slices of A and column slices of B, with the digit
+// pairs p + q <= dmax (dmax = P - 1: every pair of weight >= 2^-40; a smaller
+// dmax truncates the product to about 8 (dmax + 1) - 2 bits).  64 x 64
 // output tile per CTA, 4 warps of 32 x 32.  The (digit pair, k-chunk) steps
 // run as one sequence through a 3-stage cp.async ring, so the loads of step
 // t + 2 overlap the tensor-core work of step t; fragments come from shared
-// memory through ldmatrix.
-__global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, const __nv_bfloat16 *A_s, const int *ea_all,
-                                                 const __nv_bfloat16 *B_s, const int *eb_all, double *C_all)
+// memory through ldmatrix.  sym: the product is known to be symmetric (X^T X,
+// X^T H X); only tiles on and above the diagonal are formed, each written with
+// its mirror.
+__global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, int dmax, bool sym, const __nv_bfloat16 *A_s,
+                                                 const int *ea_all, const __nv_bfloat16 *B_s, const int *eb_all,
+                                                 double *C_all)
 {
     __shared__ __align__(128) __nv_bfloat16 ring[kOzStages * kOzStageElems];
     const int b = blockIdx.z;
-    const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+    int tr = blockIdx.y, tc = blockIdx.x;
+    if (sym) {  // a symmetric product: blockIdx.x enumerates the tiles tr <= tc only
+        const int T = (n + 63) / 64;
+        int e = blockIdx.x;
+        tr = 0;
+        while (e >= T - tr) {
+            e -= T - tr;
+            ++tr;
+        }
+        tc = tr + e;
+    }
+    const int row0 = tr * 64, col0 = tc * 64;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g4 = lane >> 2, t = lane & 3;
     const int wr = (warp >> 1) * 32, wc = (warp & 1) * 32;
     const __nv_bfloat16 *Ab = A_s + (size_t)b * kOzP * n * Kp;
     const __nv_bfloat16 *Bb = B_s + (size_t)b * kOzP * n * Kp;
     const int nk = Kp / kOzKC;                           // k-chunks per digit pair
-    const int n_steps = nk * (kOzP * (kOzP + 1) / 2);    // 21 pairs (p + q <= P - 1)
+    const int n_steps = nk * ((dmax + 1) * (dmax + 2) / 2);  // pairs p + q <= dmax (21 for dmax = P - 1)
     const unsigned ring_s = smem_u32(ring);
 
     // issue cursor: the (d, p, chunk) of the next step to load
@@ -253,7 +269,9 @@ __global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, const __nv_bfloa
         const unsigned sA = ring_s + (unsigned)((st % kOzStages) * kOzStageElems) * 2u;
         const unsigned sB = sA + 64u * kOzLd * 2u;
 #pragma unroll
-        for (int ks = 0; ks < kOzKC; ks += 16) {
+        // a warp tile wholly past the matrix edge has nothing to compute
+        const bool live = row0 + wr < n && col0 + wc < n;
+        for (int ks = 0; ks < kOzKC && live; ks += 16) {
             unsigned af[2][4], bf[4][2];
 #pragma unroll
             for (int i = 0; i < 2; ++i) {  // rows wr + 16 i + (lane & 15), k ks + 8 (lane >> 4)
@@ -305,7 +323,11 @@ __global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, const __nv_bfloa
             for (int u = 0; u < 4; ++u) {
                 const int r = row0 + wr + i * 16 + g4 + (u >= 2 ? 8 : 0);
                 const int c = col0 + wc + j * 8 + 2 * t + (u & 1);
-                if (r < n && c < n) C[(size_t)r * n + c] = i64_times_pow2(acc[i][j][u], ea[r] + eb[c] - 50);
+                if (r < n && c < n) {
+                    const double v = i64_times_pow2(acc[i][j][u], ea[r] + eb[c] - 50);
+                    C[(size_t)r * n + c] = v;
+                    if (sym && tr != tc) C[(size_t)c * n + r] = v;  // the mirrored tile
+                }
             }
 }
 
@@ -328,10 +350,15 @@ cudaError_t launch_oz_split(int n, int items, bool cols, const double *M, __nv_b
 
 // C = A B from the row slices of A and the column slices of B.
 cudaError_t launch_oz_gemm_slices(int n, int items, const __nv_bfloat16 *sa, const int *ea, const __nv_bfloat16 *sb,
-                                  const int *eb, double *C, cudaStream_t st)
+                                  const int *eb, double *C, cudaStream_t st, int digits, bool sym)
 {
+    if (digits < 1 || digits > kOzP) return cudaErrorInvalidValue;
     const int tiles = (n + 63) / 64;
-    k_oz_gemm<<<dim3(tiles, tiles, items), 128, 0, st>>>(n, oz_kpad(n), sa, ea, sb, eb, C);
+    if (sym)
+        k_oz_gemm<<<dim3(tiles * (tiles + 1) / 2, 1, items), 128, 0, st>>>(n, oz_kpad(n), digits - 1, true, sa, ea, sb,
+                                                                            eb, C);
+    else
+        k_oz_gemm<<<dim3(tiles, tiles, items), 128, 0, st>>>(n, oz_kpad(n), digits - 1, false, sa, ea, sb, eb, C);
     return cudaGetLastError();
 }
 

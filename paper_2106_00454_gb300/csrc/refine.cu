@@ -230,12 +230,17 @@ cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_s
     double *x = Xs, *xn = Y;
     if (engine == 0) CKR(launch_oz_split(n, items, false, H, sH, eH, st));  // rows of H, reused
     for (int it = 0; it < iters; ++it) {
+        // all 6 digits on every iteration: errors of S = X^T H X are divided by
+        // eigenvalue gaps (~1e-6 of ||H||) in E, so even the first iteration
+        // needs FP64-accurate products (4 digits cost 100x in phase accuracy)
+        const int dg = 6;
         if (engine == 0) {
-            CKR(launch_oz_split(n, items, true, x, sXc, eXc, st));               // columns of X
-            CKR(launch_oz_gemm_slices(n, items, sH, eH, sXc, eXc, xn, st));       // Y = H X
-            CKR(launch_oz_split(n, items, true, xn, sYc, eYc, st));              // columns of Y
-            CKR(launch_oz_gemm_slices(n, items, sXc, eXc, sYc, eYc, W1, st));     // S = X^T Y
-            CKR(launch_oz_gemm_slices(n, items, sXc, eXc, sXc, eXc, W2, st));     // G = X^T X
+            CKR(launch_oz_split(n, items, true, x, sXc, eXc, st));                   // columns of X
+            CKR(launch_oz_gemm_slices(n, items, sH, eH, sXc, eXc, xn, st, dg));       // Y = H X
+            CKR(launch_oz_split(n, items, true, xn, sYc, eYc, st));                  // columns of Y
+            // S = X^T H X and G = X^T X are symmetric: upper tiles, mirrored
+            CKR(launch_oz_gemm_slices(n, items, sXc, eXc, sYc, eYc, W1, st, dg, true));  // S = X^T Y
+            CKR(launch_oz_gemm_slices(n, items, sXc, eXc, sXc, eXc, W2, st, dg, true));  // G = X^T X
         } else {
             k_bgemm64<false><<<gg, 256, 0, st>>>(n, H, x, xn);
             k_bgemm64<true><<<gg, 256, 0, st>>>(n, x, xn, W1);
@@ -245,7 +250,7 @@ cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_s
         if (engine == 0) {
             CKR(launch_oz_split(n, items, false, x, sXr, eXr, st));              // rows of X
             CKR(launch_oz_split(n, items, true, W2, sEc, eEc, st));              // columns of I + E
-            CKR(launch_oz_gemm_slices(n, items, sXr, eXr, sEc, eEc, xn, st));     // X (I + E)
+            CKR(launch_oz_gemm_slices(n, items, sXr, eXr, sEc, eEc, xn, st, dg)); // X (I + E)
         } else {
             k_bgemm64<false><<<gg, 256, 0, st>>>(n, x, W2, xn);
         }

@@ -3,6 +3,7 @@
 // Every numerical step runs in the kernels of the other translation units;
 // this file only allocates, validates, orders launches and copies.
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -1101,6 +1102,72 @@ wpcd_status wpcd_release(wpcd_ctx *c, int id)
     return WPCD_OK;
 }
 
+// ---- spin observables (App. A) ---------------------------------------------------------------------
+namespace {
+// Clebsch-Gordan <j1 m1 j2 m2 | J M> for integer spins, Racah's closed form.
+double cg_racah(int j1, int m1, int j2, int m2, int J, int M)
+{
+    if (m1 + m2 != M || std::abs(m1) > j1 || std::abs(m2) > j2 || std::abs(M) > J || J < std::abs(j1 - j2) ||
+        J > j1 + j2)
+        return 0.0;
+    auto lf = [](int n) { return std::lgamma((double)n + 1.0); };
+    const double pre = 0.5 * (std::log(2.0 * J + 1.0) + lf(J + j1 - j2) + lf(J - j1 + j2) + lf(j1 + j2 - J) -
+                              lf(j1 + j2 + J + 1) + lf(J + M) + lf(J - M) + lf(j1 - m1) + lf(j1 + m1) + lf(j2 - m2) +
+                              lf(j2 + m2));
+    double sum = 0.0;
+    for (int k = 0; k <= j1 + j2 - J; ++k) {
+        const int a = j1 + j2 - J - k, b = j1 - m1 - k, c = j2 + m2 - k, d = J - j2 + m1 + k, e = J - j1 - m2 + k;
+        if (a < 0 || b < 0 || c < 0 || d < 0 || e < 0) continue;
+        const double t = std::exp(pre - lf(k) - lf(a) - lf(b) - lf(c) - lf(d) - lf(e));
+        sum += (k & 1) ? -t : t;
+    }
+    return sum;
+}
+}  // namespace
+
+wpcd_status wpcd_saclay(wpcd_ctx *c, const wpcd_channel *channels, int n_ch, const double *delta, int S,
+                        const double *e_lab, int n_E, const double *theta, int n_theta, double *abcde, double *dsig)
+{
+    if (!c || !channels || n_ch < 1 || !delta || S < 1 || !e_lab || n_E < 1 || !theta || n_theta < 1 ||
+        (!abcde && !dsig))
+        return WPCD_ERR_ARG;
+    std::vector<SacChanDev> tab(n_ch);
+    for (int k = 0; k < n_ch; ++k) {
+        const wpcd_channel &ch = channels[k];
+        if (ch.J < 0 || ch.J > kMaxJ || (ch.s != 0 && ch.s != 1)) return WPCD_ERR_ARG;
+        if (ch.coupled && (ch.s != 1 || ch.J < 1 || ch.l != ch.J - 1 || ch.lp != ch.J + 1)) return WPCD_ERR_ARG;
+        if (!ch.coupled && ch.l != ch.lp) return WPCD_ERR_ARG;
+        SacChanDev &d = tab[k];
+        memset(&d, 0, sizeof(d));
+        d.s = ch.s;
+        d.J = ch.J;
+        d.tz = ch.tz;
+        d.K = ch.coupled ? 2 : 1;
+        d.l[0] = ch.coupled ? ch.J - 1 : ch.l;
+        d.l[1] = ch.coupled ? ch.J + 1 : ch.l;
+        for (int ip = 0; ip < d.K; ++ip)
+            for (int il = 0; il < d.K; ++il)
+                for (int mp = -ch.s; mp <= ch.s; ++mp)
+                    for (int m = -ch.s; m <= ch.s; ++m) {
+                        const int lp = d.l[ip], l = d.l[il];
+                        d.tab[((ip * 2 + il) * 3 + mp + 1) * 3 + m + 1] =
+                            std::sqrt(4.0 * kPi) * std::sqrt(2.0 * l + 1.0) *
+                            cg_racah(lp, m - mp, ch.s, mp, ch.J, m) * cg_racah(l, 0, ch.s, m, ch.J, m);
+                    }
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaSetDevice(c->device));
+    Exec &X = c->main;
+    wpcd_status st = ws_reserve(c, X, X.ws_in, sizeof(SacChanDev) * n_ch);
+    if (st) return st;
+    CK(cudaMemcpyAsync(X.ws_in.p, tab.data(), sizeof(SacChanDev) * n_ch, cudaMemcpyHostToDevice, X.stream));
+    Launch L(c, X, WPCD_PHASE_OBSERVABLES);
+    CK(launch_saclay(static_cast<SacChanDev *>(X.ws_in.p), n_ch, S, n_E, e_lab, delta, n_theta, theta, abcde, dsig,
+                     X.stream));
+    CK(cudaStreamSynchronize(X.stream));  // the channel table lives in a reusable workspace
+    return WPCD_OK;
+}
+
 // ---- MI comparison method (Sec. 2.1, Sec. 6) ---------------------------------------------------
 wpcd_status wpcd_mi_prepare(wpcd_ctx *c, const wpcd_channel *channels, int n_ch, int generator_id,
                             const double *gp_host, int n_gp, int n_terms, int n_quad, double c_map_fm, int *mi_id)
@@ -1190,7 +1257,7 @@ wpcd_status wpcd_mi_prepare(wpcd_ctx *c, const wpcd_channel *channels, int n_ch,
 }
 
 wpcd_status wpcd_mi_solve(wpcd_ctx *c, int mi_id, const double *coeffs, int S, const double *e_int, int n_I,
-                          const double *e_lab, int n_E, double *k_out, double *delta, double *sigma)
+                          const double *e_lab, int n_E, double *k_out, double *delta, double *sigma, int *status_dev)
 {
     if (!c || S < 1 || !e_int || n_I < 2 || !e_lab || n_E < 1 || (!k_out && !delta && !sigma)) return WPCD_ERR_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
@@ -1213,7 +1280,7 @@ wpcd_status wpcd_mi_solve(wpcd_ctx *c, int mi_id, const double *coeffs, int S, c
     if ((st = ws_reserve(c, X, X.ws_tbin, (von_len + ph_len) * sizeof(double)))) return st;
     if ((st = ws_reserve(c, X, X.ws_plan_i, (size_t)S * m.n_ch * sizeof(int)))) return st;
     double *Von = static_cast<double *>(X.ws_tbin.p), *ph = Von + von_len;
-    int *status = static_cast<int *>(X.ws_plan_i.p);
+    int *status = status_dev ? status_dev : static_cast<int *>(X.ws_plan_i.p);
     CK(cudaMemcpyAsync(m.ch_dev, m.ch.data(), sizeof(MiChanDev) * m.n_ch, cudaMemcpyHostToDevice, X.stream));
     double *angx = nullptr, *angw = nullptr;
     if (m.gen == WPCD_GEN_YUKAWA && (st = gl_rule(c, kAngleQ, &angx, &angw))) return st;
@@ -1231,7 +1298,8 @@ wpcd_status wpcd_mi_solve(wpcd_ctx *c, int mi_id, const double *coeffs, int S, c
         if (per_sm < 1) return WPCD_ERR_ARG;
         const int items = S * nw;
         const int slots = std::max(1, std::min(items, per_sm * c->n_sm));
-        if ((st = ws_reserve(c, X, X.ws_ref, (size_t)slots * n * n * sizeof(double)))) return st;
+        // two FP64 n x n matrices per slot: V, and the rarely used FP64 elimination fallback
+        if ((st = ws_reserve(c, X, X.ws_ref, (size_t)slots * 2 * n * n * sizeof(double)))) return st;
         Launch L(c, X, WPCD_PHASE_MI);
         CK(launch_mi_solve(m.ch_dev, m.work_dev[K - 1], nw, n, m.n_ch, S, m.NQ, m.kg, m.wg, m.n_terms, cf, m.Vg, Von,
                            n_I, e_int, static_cast<double *>(X.ws_ref.p), slots, ph, k_out, status, X.err, X.stream));

@@ -44,6 +44,15 @@ struct MiChanDev {
     long long vg_off, von_off;
 };
 
+// Channel of the spin-observable kernel: spin, J, T_z, K, its l values and the
+// coupling products sqrt(4 pi) sqrt(2l+1) C(l' (m-m') s m' | J m) C(l 0 s m | J m)
+// at tab[((l' block * 2 + l block) * 3 + m' + 1) * 3 + m + 1].
+struct SacChanDev {
+    int s, J, tz, K;
+    int l[2];
+    double tab[36];
+};
+
 struct ChanDev {
     int s, J, l, lp, coupled, tz;
     int N;              // N_WP of its mesh
@@ -198,7 +207,7 @@ cudaError_t launch_oz_gemm(int n, int items, bool ta, const double *A, const dou
                            __nv_bfloat16 *sa, __nv_bfloat16 *sb, int *ea, int *eb, cudaStream_t st);
 cudaError_t launch_oz_split(int n, int items, bool cols, const double *M, __nv_bfloat16 *S, int *e, cudaStream_t st);
 cudaError_t launch_oz_gemm_slices(int n, int items, const __nv_bfloat16 *sa, const int *ea, const __nv_bfloat16 *sb,
-                                  const int *eb, double *C, cudaStream_t st);
+                                  const int *eb, double *C, cudaStream_t st, int digits = 6, bool sym = false);
 size_t refine_scratch_per_item(int n, int engine);
 cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_samples, int sample0, int n,
                           int n_terms, const double *coeffs, void *scratch, double *eps_all, double *X_all,
@@ -211,6 +220,9 @@ cudaError_t launch_plan(const ChanDev *chans_dev, int n_ch, int maxN, const doub
 cudaError_t launch_tbin(const ChanDev *chans_dev, int n_ch, int n_samples, int n_terms, const double *coeffs,
                         const double *eps_all, const double *C_all, PlanDev plan, int maxN, int n_E, double *tout,
                         double *phout, int *err, cudaStream_t st, bool vc_identity, int mode);
+cudaError_t launch_saclay(const SacChanDev *chans_dev, int n_ch, int n_samples, int n_E, const double *e_lab,
+                          const double *delta, int n_th, const double *theta, double *abcde, double *dsig,
+                          cudaStream_t st);
 constexpr int kMiMaxNQ = 100;  // MI grid points per l-block: 2 (N_Q + 1) rows fit one CTA's shared memory in FP32
 cudaError_t launch_mi_grid(int NQ, double cmap, const double *glx, const double *glw, double *k, double *w,
                            cudaStream_t st);
