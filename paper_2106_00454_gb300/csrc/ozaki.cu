@@ -10,16 +10,17 @@
 //     bits: v / 2^e = sum_p d_p 2^{-8(p+1)+1}, d_1..d_5 in [-128, 127] and
 //     |d_0| <= 129 -- all exact in BF16;
 //   * the product of two digit slices is a sum of integer products of
-//     magnitude < 2^15; over k <= 256 terms the sum stays below 2^23, so the
-//     tensor core's FP32 accumulation is exact;
+//     magnitude < 2^15, so an FP32 tensor-core accumulation over a bounded k
+//     range stays an exact integer (ozaki_tc.cu: the pairs of one weight over
+//     128 k);
 //   * C_ij = 2^{e_i + f_j} sum_{p+q <= P-1} 2^{-8(p+q+2)+2} (A_p B_q)_ij,
 //     accumulated exactly in int64 and rounded once to FP64 (the 15 dropped
 //     pairs weigh at most 2^-62 each).
 // The error is dominated by the 47-bit rounding, |dC_ij| <~ 2^-48 (2^{e_i}
 // sum_k |B_kj| + 2^{f_j} sum_k |A_ik|), ~4e-15 relative to the row and column
 // scales.  The slices are stored k-contiguous ([p][vector][k],
-// k padded to a multiple of 32) for both operands, the layout the
-// m16n8k16 row.col tensor instruction consumes.
+// k padded to a multiple of 32) for both operands: K-major tiles for the
+// tensor-core kernel of ozaki_tc.cu.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -27,10 +28,8 @@
 
 namespace wpcd {
 
-constexpr int kOzP = 6;    // slices per operand
+constexpr int kOzP = kOzDigits;  // slices per operand
 constexpr int kOzKC = 32;  // k staged per step
-constexpr int kOzLd = 40;  // padded shared row stride (bf16): conflict-free fragment loads
-constexpr int kOzKMax = 256;  // k range whose FP32 sum of slice products is exact
 
 int oz_kpad(int n) { return (n + kOzKC - 1) / kOzKC * kOzKC; }
 size_t oz_slice_elems(int n) { return (size_t)kOzP * n * oz_kpad(n); }
@@ -113,224 +112,6 @@ __global__ void k_oz_split_cols(int n, int Kp, const double *M_all, const int *e
     }
 }
 
-__device__ __forceinline__ unsigned ld_u32(const __nv_bfloat16 *p) { return *reinterpret_cast<const unsigned *>(p); }
-
-__device__ __forceinline__ void mma_bf16(float *c, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
-                                         unsigned b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// v 2^e as a double (round half away from zero), from the IEEE-754 layout with
-// integer operations only; FP64 arithmetic only where the result leaves the
-// normal range.
-__device__ __forceinline__ double i64_times_pow2(long long v, int e)
-{
-    if (v == 0) return 0.0;
-    unsigned long long m = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-    int msb = 63 - __clzll((long long)m);
-    unsigned long long frac;
-    if (msb > 52) {
-        int sh = msb - 52;
-        m += 1ull << (sh - 1);  // m < 2^63: no overflow
-        if (m >> (msb + 1)) {   // the rounding carried into a new leading bit
-            ++msb;
-            ++sh;
-        }
-        frac = m >> sh;
-    } else {
-        frac = m << (52 - msb);
-    }
-    const int be = msb + e + 1023;
-    if (be < 1 || be > 2046) return ldexp((double)v, e);
-    const unsigned long long bits =
-        (v < 0 ? (1ull << 63) : 0ull) | ((unsigned long long)be << 52) | (frac & ((1ull << 52) - 1));
-    return __longlong_as_double((long long)bits);
-}
-
-__device__ __forceinline__ unsigned smem_u32(const void *p)
-{
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-// 16-byte global -> shared copy; src_bytes = 0 fills the 16 bytes with zeros.
-__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, int src_bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-
-__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-
-constexpr int kOzStages = 3;                 // cp.async ring depth
-constexpr int kOzStageElems = 2 * 64 * kOzLd;  // A and B tiles of one step (bf16)
-
-// C[b] = A[b] B[b] from row slices of A and column slices of B, with the digit
-// pairs p + q <= dmax (dmax = P - 1: every pair of weight >= 2^-40; a smaller
-// dmax truncates the product to about 8 (dmax + 1) - 2 bits).  64 x 64
-// output tile per CTA, 4 warps of 32 x 32.  The (digit pair, k-chunk) steps
-// run as one sequence through a 3-stage cp.async ring, so the loads of step
-// t + 2 overlap the tensor-core work of step t; fragments come from shared
-// memory through ldmatrix.  sym: the product is known to be symmetric (X^T X,
-// X^T H X); only tiles on and above the diagonal are formed, each written with
-// its mirror.
-__global__ void __launch_bounds__(128) k_oz_gemm(int n, int Kp, int dmax, bool sym, const __nv_bfloat16 *A_s,
-                                                 const int *ea_all, const __nv_bfloat16 *B_s, const int *eb_all,
-                                                 double *C_all)
-{
-    __shared__ __align__(128) __nv_bfloat16 ring[kOzStages * kOzStageElems];
-    const int b = blockIdx.z;
-    int tr = blockIdx.y, tc = blockIdx.x;
-    if (sym) {  // a symmetric product: blockIdx.x enumerates the tiles tr <= tc only
-        const int T = (n + 63) / 64;
-        int e = blockIdx.x;
-        tr = 0;
-        while (e >= T - tr) {
-            e -= T - tr;
-            ++tr;
-        }
-        tc = tr + e;
-    }
-    const int row0 = tr * 64, col0 = tc * 64;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g4 = lane >> 2, t = lane & 3;
-    const int wr = (warp >> 1) * 32, wc = (warp & 1) * 32;
-    const __nv_bfloat16 *Ab = A_s + (size_t)b * kOzP * n * Kp;
-    const __nv_bfloat16 *Bb = B_s + (size_t)b * kOzP * n * Kp;
-    const int nk = Kp / kOzKC;                           // k-chunks per digit pair
-    const int n_steps = nk * ((dmax + 1) * (dmax + 2) / 2);  // pairs p + q <= dmax (21 for dmax = P - 1)
-    const unsigned ring_s = smem_u32(ring);
-
-    // issue cursor: the (d, p, chunk) of the next step to load
-    int id = 0, ip = 0, ik = 0;
-    auto issue = [&](int stage) {
-        const int q = id - ip;
-        const __nv_bfloat16 *Ap = Ab + (size_t)ip * n * Kp;
-        const __nv_bfloat16 *Bq = Bb + (size_t)q * n * Kp;
-        const unsigned sA = ring_s + (unsigned)(stage * kOzStageElems) * 2u;
-        const unsigned sB = sA + 64u * kOzLd * 2u;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {  // 64 rows x 32 k of each operand: 256 16-byte pieces, 2 per thread
-            const int e = tid + u * 128;
-            const int r = e >> 2, kk = (e & 3) * 8;
-            const int ra = row0 + r < n ? row0 + r : n - 1, rb = col0 + r < n ? col0 + r : n - 1;
-            cp_async16(sA + (unsigned)(r * kOzLd + kk) * 2u, Ap + (size_t)ra * Kp + ik * kOzKC + kk,
-                       row0 + r < n ? 16 : 0);
-            cp_async16(sB + (unsigned)(r * kOzLd + kk) * 2u, Bq + (size_t)rb * Kp + ik * kOzKC + kk,
-                       col0 + r < n ? 16 : 0);
-        }
-        if (++ik == nk) {
-            ik = 0;
-            if (++ip > id) {
-                ip = 0;
-                ++id;
-            }
-        }
-    };
-
-    // v = sum over pairs of their sums times 2^{36-8d} (for d = 5 shifted down
-    // by 4 bits instead): C_ij = v 2^{e_i + f_j - 50}, exact up to those 4 bits.
-    long long acc[2][4][4];
-    float c32[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                acc[i][j][u] = 0;
-                c32[i][j][u] = 0.f;
-            }
-
-    // Digit pair (p, q) weighs 2^{-8(d+2)+2}, d = p + q.  Its FP32 sum over
-    // at most 256 k is an exact integer of magnitude at most 256 * 129 * 128
-    // < 2^23; it joins the int64 accumulator shifted by 36 - 8d (|v| < 2^62:
-    // at most 6 pairs x 2 k-blocks of 2^22 per d), with no FP64 arithmetic.
-    issue(0);
-    cp_async_commit();
-    if (n_steps > 1) issue(1);
-    cp_async_commit();
-    int cd = 0, cp = 0, ck = 0;  // compute cursor
-    for (int st = 0; st < n_steps; ++st) {
-        cp_async_wait1();  // step st has landed (only the newest group may be in flight)
-        __syncthreads();   // ... for every thread, and step st - 1's stage is free again
-        if (st + 2 < n_steps) issue((st + 2) % kOzStages);
-        cp_async_commit();
-        const unsigned sA = ring_s + (unsigned)((st % kOzStages) * kOzStageElems) * 2u;
-        const unsigned sB = sA + 64u * kOzLd * 2u;
-#pragma unroll
-        // a warp tile wholly past the matrix edge has nothing to compute
-        const bool live = row0 + wr < n && col0 + wc < n;
-        for (int ks = 0; ks < kOzKC && live; ks += 16) {
-            unsigned af[2][4], bf[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {  // rows wr + 16 i + (lane & 15), k ks + 8 (lane >> 4)
-                const int r = wr + i * 16 + (lane & 15), k = ks + 8 * (lane >> 4);
-                ldsm_x4(sA + (unsigned)(r * kOzLd + k) * 2u, af[i][0], af[i][1], af[i][2], af[i][3]);
-            }
-#pragma unroll
-            for (int jj = 0; jj < 2; ++jj) {  // columns wc + 16 jj + 8 (m >> 1) + (lane & 7), k ks + 8 (m & 1)
-                const int m = lane >> 3;
-                const int r = wc + jj * 16 + 8 * (m >> 1) + (lane & 7), k = ks + 8 * (m & 1);
-                ldsm_x4(sB + (unsigned)(r * kOzLd + k) * 2u, bf[2 * jj][0], bf[2 * jj][1], bf[2 * jj + 1][0],
-                        bf[2 * jj + 1][1]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    mma_bf16(c32[i][j], af[i][0], af[i][1], af[i][2], af[i][3], bf[j][0], bf[j][1]);
-        }
-        const int k_end = (ck + 1) * kOzKC;
-        if ((k_end % kOzKMax) == 0 || ck + 1 == nk) {  // keep every FP32 sum exact
-            const int sh = 36 - 8 * cd;                 // weight 2^{-8(d+2)+2} = 2^{sh-50}
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int v = __float2int_rn(c32[i][j][u]);
-                        acc[i][j][u] += sh >= 0 ? ((long long)v << sh) : (long long)(v >> -sh);
-                        c32[i][j][u] = 0.f;
-                    }
-        }
-        if (++ck == nk) {
-            ck = 0;
-            if (++cp > cd) {
-                cp = 0;
-                ++cd;
-            }
-        }
-    }
-    const int *ea = ea_all + (size_t)b * n, *eb = eb_all + (size_t)b * n;
-    double *C = C_all + (size_t)b * n * n;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int r = row0 + wr + i * 16 + g4 + (u >= 2 ? 8 : 0);
-                const int c = col0 + wc + j * 8 + 2 * t + (u & 1);
-                if (r < n && c < n) {
-                    const double v = i64_times_pow2(acc[i][j][u], ea[r] + eb[c] - 50);
-                    C[(size_t)r * n + c] = v;
-                    if (sym && tr != tc) C[(size_t)c * n + r] = v;  // the mirrored tile
-                }
-            }
-}
-
 // C = op(A) B for `items` n x n FP64 matrices (op(A) = A^T when ta), through
 // the slices.  Scratch: sa, sb hold oz_slice_elems(n) bf16 per item; ea, eb n ints per item.
 // Digit slices of the rows (cols = false) or columns (cols = true) of `items`
@@ -350,26 +131,20 @@ cudaError_t launch_oz_split(int n, int items, bool cols, const double *M, __nv_b
 
 // C = A B from the row slices of A and the column slices of B.
 cudaError_t launch_oz_gemm_slices(int n, int items, const __nv_bfloat16 *sa, const int *ea, const __nv_bfloat16 *sb,
-                                  const int *eb, double *C, cudaStream_t st, int digits, bool sym)
+                                  const int *eb, double *C, cudaStream_t st, int digits, bool sym, int *err)
 {
-    if (digits < 1 || digits > kOzP) return cudaErrorInvalidValue;
-    const int tiles = (n + 63) / 64;
-    if (sym)
-        k_oz_gemm<<<dim3(tiles * (tiles + 1) / 2, 1, items), 128, 0, st>>>(n, oz_kpad(n), digits - 1, true, sa, ea, sb,
-                                                                            eb, C);
-    else
-        k_oz_gemm<<<dim3(tiles, tiles, items), 128, 0, st>>>(n, oz_kpad(n), digits - 1, false, sa, ea, sb, eb, C);
-    return cudaGetLastError();
+    return launch_oz_gemm_tc(n, items, sa, ea, sb, eb, C, digits, sym, err, st);
 }
 
 cudaError_t launch_oz_gemm(int n, int items, bool ta, const double *A, const double *B, double *C,
-                           __nv_bfloat16 *sa, __nv_bfloat16 *sb, int *ea, int *eb, cudaStream_t st)
+                           __nv_bfloat16 *sa, __nv_bfloat16 *sb, int *ea, int *eb, cudaStream_t st,
+                           int *err)
 {
     cudaError_t e;
     // rows of op(A): rows of A, or columns of A when transposed; columns of B
     if ((e = launch_oz_split(n, items, ta, A, sa, ea, st))) return e;
     if ((e = launch_oz_split(n, items, true, B, sb, eb, st))) return e;
-    return launch_oz_gemm_slices(n, items, sa, ea, sb, eb, C, st);
+    return launch_oz_gemm_slices(n, items, sa, ea, sb, eb, C, st, kOzP, false, err);
 }
 
 }  // namespace wpcd

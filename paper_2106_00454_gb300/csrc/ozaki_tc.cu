@@ -1,0 +1,449 @@
+// ozaki_tc.cu -- the digit-pair products of the Ozaki scheme (ozaki.cu) on the
+// fifth-generation tensor cores: TMA loads, tcgen05.mma, accumulators in tensor
+// memory (TMEM).
+//
+// A persistent kernel, one CTA per SM, walks the 128 x 64 output tiles of
+// C[b] = A[b] B[b] (A: row slices, B: column slices, both k-contiguous).  Its
+// ten warps split the work:
+//   * warp 8 (one thread) streams k-chunks of 32 through a 3-stage ring: one
+//     TMA box per operand brings all six digits of the chunk (128 rows of A,
+//     64 columns of B; 72 KB), in the 64-byte-swizzled K-major layout the
+//     tensor core reads;
+//   * warp 9 (one thread) owns the tensor memory and issues, per chunk, the 21
+//     digit pairs p + q <= 5 as M = 128, N = 64, K = 16 MMAs into six FP32
+//     accumulators, one per weight d = p + q (6 x 64 TMEM columns);
+//   * warps 0-7 drain the accumulators every 128 k into per-thread int64
+//     sums, shifted by 36 - 8d (warp w reads TMEM lanes 32 (w % 4) .. + 31 =
+//     rows of the tile, columns 32 (w / 4) .. + 31), and write the FP64 tile,
+//     assembled with integer operations, while the MMAs of the next k-block or
+//     tile proceed.
+// Exactness: a weight-d accumulator sums d + 1 digit pairs over <= 128 k of
+// products below 129 * 128 in magnitude, < 6 * 2^21 < 2^24, so every FP32
+// accumulator is an exact integer.
+//
+// Every mbarrier wait is bounded (about a second at the SM clock); on a timeout
+// the kernel records kDevTimeout, the other roles stop at their next wait, the
+// loads and MMAs in flight are waited for (bounded) and the tensor memory is
+// freed before the CTA returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "wpcd_internal.cuh"
+
+namespace wpcd {
+
+// v 2^e as a double (round half away from zero), from the IEEE-754 layout with
+// integer operations only; FP64 arithmetic only where the result leaves the
+// normal range.
+__device__ __forceinline__ double i64_times_pow2(long long v, int e)
+{
+    if (v == 0) return 0.0;
+    const unsigned long long m = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int lz = __clzll((long long)m);
+    const unsigned long long mn = m << lz;  // leading one at bit 63: 53 bits kept, 11 dropped
+    const unsigned long long r = mn + 0x400ull;
+    int msb = 63 - lz;
+    unsigned long long frac = (r >> 11) & ((1ull << 52) - 1);
+    if (r < mn) {  // the rounding carried out of the top bit: 1.0 x 2^{msb + 1}
+        frac = 0;
+        ++msb;
+    }
+    const int be = msb + e + 1023;
+    if (be < 1 || be > 2046) return ldexp((double)v, e);
+    const unsigned long long bits = (v < 0 ? (1ull << 63) : 0ull) | ((unsigned long long)be << 52) | frac;
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+constexpr int kTcM = 128;       // tile rows = TMEM lanes
+constexpr int kTcN = 64;        // tile columns = TMEM columns per accumulator
+constexpr int kTcKC = 32;       // k per stage: 64 bytes of a row = one swizzle span
+constexpr int kTcKBlk = 128;    // k between drains (exact FP32 sums)
+constexpr int kTcStages = 3;
+constexpr int kTcADigit = kTcM * kTcKC * 2;                        // 8 KB
+constexpr int kTcBDigit = kTcN * kTcKC * 2;                        // 4 KB
+constexpr int kTcAStage = kOzDigits * kTcADigit;                   // 48 KB
+constexpr int kTcStageBytes = kOzDigits * (kTcADigit + kTcBDigit);  // 72 KB
+constexpr int kTcTmemCols = 512;  // 6 x 64 accumulator columns, allocated as a power of two
+constexpr int kTcDrainWarps = 8;  // two per TMEM lane quarter, one per half of the columns
+constexpr int kTcDrainCols = kTcN / (kTcDrainWarps / 4);
+constexpr int kTcProducerWarp = kTcDrainWarps, kTcMmaWarp = kTcDrainWarps + 1;
+constexpr int kTcThreads = 32 * (kTcDrainWarps + 2);
+constexpr int kTcSmem = 1024 + kTcStages * kTcStageBytes + 128;  // alignment slack | ring | barriers
+constexpr long long kTcWaitCycles = 1ll << 31;
+
+// instruction descriptor: D F32, A and B BF16, both K-major, N = 64, M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                              ((uint32_t)(kTcM >> 4) << 24);
+
+// Shared-memory matrix descriptor of a K-major operand with 64-byte swizzle:
+// rows of 64 bytes, 8-row groups 512 bytes apart (stride offset); the leading
+// offset is unused when one MMA's K (32 bytes) stays inside the swizzle span.
+__device__ __forceinline__ uint64_t tc_desc_sw64(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused): 16 B
+    d |= (uint64_t)(512 >> 4) << 32;      // stride byte offset: 512 B
+    d |= (uint64_t)1 << 46;               // descriptor version of this architecture
+    d |= (uint64_t)4 << 61;               // layout: 64-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait for the completion of the phase with the given parity; gives up
+// early when another role has aborted (abort != nullptr).
+__device__ __forceinline__ bool tc_wait(uint32_t a, uint32_t parity, const volatile int *abort)
+{
+    if (mbar_try(a, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(a, parity)) {
+        if (abort && *abort) return false;
+        if (clock64() - t0 > kTcWaitCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t a)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+struct TcTile {
+    int b, row0, col0;
+};
+
+// Tile t of the launch: item-major; per item the row tiles (128) x column tiles
+// (64), or for a symmetric product only those reaching the diagonal or above it
+// (column tiles 2 tr .. TC - 1 of row tile tr).
+__device__ __forceinline__ TcTile tc_tile(int t, int per_item, int TC, bool sym)
+{
+    TcTile r;
+    r.b = t / per_item;
+    int j = t - r.b * per_item;
+    int tr = 0;
+    if (sym) {
+        while (j >= TC - 2 * tr) {
+            j -= TC - 2 * tr;
+            ++tr;
+        }
+        j += 2 * tr;
+    } else {
+        tr = j / TC;
+        j -= tr * TC;
+    }
+    r.row0 = tr * kTcM;
+    r.col0 = j * kTcN;
+    return r;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_oz_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int n, int Kp,
+                 int dmax, bool sym, int per_item, int TC, int ntiles, const int *ea_all, const int *eb_all,
+                 double *C_all, int *err)
+{
+    extern __shared__ unsigned char tc_raw[];
+    const uint32_t raw_s = smem_u32(tc_raw);
+    const uint32_t ring_s = (raw_s + 1023u) & ~1023u;  // the swizzle pattern follows address bits
+    unsigned char *ring = tc_raw + (ring_s - raw_s);
+    const uint32_t bar_s = ring_s + kTcStages * kTcStageBytes;
+    // barriers: full[3] | empty[3] | acc_full | acc_empty, then the TMEM base and the abort flag
+    const uint32_t full_s = bar_s, empty_s = bar_s + 8u * kTcStages;
+    const uint32_t accf_s = bar_s + 16u * kTcStages, acce_s = accf_s + 8u;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(ring + kTcStages * kTcStageBytes + 64);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int i = 0; i < 2 * kTcStages + 1; ++i) mbar_init(bar_s + 8u * i, 1);
+        mbar_init(acce_s, 32 * kTcDrainWarps);  // every drain thread arrives
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kTcMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTcTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool failed = false;
+
+    if (warp == kTcProducerWarp) {
+        // ---- producer: TMA of every k-chunk of every tile of this CTA
+        if (lane == 0) {
+            int stage = 0, issued = 0;
+            uint32_t ph = 0;
+            for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+                const TcTile tl = tc_tile(t, per_item, TC, sym);
+                for (int k0 = 0; k0 < Kp; k0 += kTcKC) {
+                    if (!tc_wait(empty_s + 8u * stage, ph ^ 1u, abort_flag)) {
+                        failed = true;
+                        break;
+                    }
+                    const uint32_t sA = ring_s + (uint32_t)(stage * kTcStageBytes);
+                    mbar_expect_tx(full_s + 8u * stage, (uint32_t)kTcStageBytes);
+                    tma_load_3d(sA, &mapA, k0, tl.row0, tl.b * kOzDigits, full_s + 8u * stage);
+                    tma_load_3d(sA + kTcAStage, &mapB, k0, tl.col0, tl.b * kOzDigits, full_s + 8u * stage);
+                    ++issued;
+                    if (++stage == kTcStages) {
+                        stage = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            if (failed) {
+                *abort_flag = 1;
+                // the copies still in flight land before the shared memory is released
+                for (int i = issued - 1; i >= 0 && i >= issued - kTcStages; --i)
+                    tc_wait(full_s + 8u * (i % kTcStages), (uint32_t)((i / kTcStages) & 1), nullptr);
+            }
+        }
+    } else if (warp == kTcMmaWarp) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            int stage = 0, blk = 0, committed = 0;
+            uint32_t ph = 0;
+            for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+                for (int k0 = 0; k0 < Kp; k0 += kTcKC) {
+                    const bool bfirst = (k0 % kTcKBlk) == 0;
+                    const bool blast = ((k0 + kTcKC) % kTcKBlk) == 0 || k0 + kTcKC >= Kp;
+                    if (bfirst && blk > 0 && !tc_wait(acce_s, (uint32_t)((blk - 1) & 1), abort_flag)) {
+                        failed = true;  // the accumulators were not drained
+                        break;
+                    }
+                    if (!tc_wait(full_s + 8u * stage, ph, abort_flag)) {
+                        failed = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sA = ring_s + (uint32_t)(stage * kTcStageBytes), sB = sA + kTcAStage;
+                    const uint64_t a0 = tc_desc_sw64(sA), b0 = tc_desc_sw64(sB);
+                    for (int d = 0; d <= dmax; ++d)
+                        for (int p = 0; p <= d; ++p) {
+                            const int q = d - p;
+#pragma unroll
+                            for (int kk = 0; kk < 2; ++kk) {  // K = 16: 32 bytes further into the swizzle span
+                                const uint64_t ad = a0 + (uint64_t)((p * kTcADigit + kk * 32) >> 4);
+                                const uint64_t bd = b0 + (uint64_t)((q * kTcBDigit + kk * 32) >> 4);
+                                tc_mma(tmem + (uint32_t)(d * kTcN), ad, bd, (bfirst && p == 0 && kk == 0) ? 0u : 1u);
+                            }
+                        }
+                    tc_commit(empty_s + 8u * stage);
+                    ++committed;
+                    if (blast) {
+                        tc_commit(accf_s);
+                        ++blk;
+                    }
+                    if (++stage == kTcStages) {
+                        stage = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            if (failed) {
+                *abort_flag = 1;
+                // commits complete in order: the last one covers every MMA issued
+                if (committed > 0)
+                    tc_wait(empty_s + 8u * ((committed - 1) % kTcStages),
+                            (uint32_t)(((committed - 1) / kTcStages) & 1), nullptr);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- drain and epilogue: row (warp % 4) * 32 + lane of the tile, columns c0 .. c0 + 31
+        int blk = 0;
+        const int row_in = (warp & 3) * 32 + lane, c0 = (warp >> 2) * kTcDrainCols;
+        const uint32_t tbase = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+        for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+            const TcTile tl = tc_tile(t, per_item, TC, sym);
+            long long acc[kTcDrainCols];
+#pragma unroll
+            for (int j = 0; j < kTcDrainCols; ++j) acc[j] = 0;
+            for (int k0 = 0; k0 < Kp; k0 += kTcKBlk, ++blk) {
+                if (!__all_sync(0xffffffffu, tc_wait(accf_s, (uint32_t)(blk & 1), abort_flag))) {
+                    failed = true;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int d = 0; d < kOzDigits; d += 2) {  // two accumulators per round trip
+                    if (d > dmax) break;
+                    uint32_t r0[32], r1[32];
+                    const bool two = d + 1 <= dmax;
+                    tc_ld32(tbase + (uint32_t)(d * kTcN), r0);
+                    if (two) tc_ld32(tbase + (uint32_t)((d + 1) * kTcN), r1);
+                    tc_wait_ld();
+                    const int sh0 = 36 - 8 * d, sh1 = sh0 - 8;  // weight 2^{-8(d+2)+2} = 2^{sh-50}
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int v = __float2int_rn(__uint_as_float(r0[j]));
+                        acc[j] += sh0 >= 0 ? ((long long)v << sh0) : (long long)(v >> -sh0);
+                    }
+                    if (two) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int v = __float2int_rn(__uint_as_float(r1[j]));
+                            acc[j] += sh1 >= 0 ? ((long long)v << sh1) : (long long)(v >> -sh1);
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(acce_s);  // the tensor core may overwrite the accumulators
+            }
+            if (failed) break;
+            const int r = tl.row0 + row_in;
+            if (r < n) {
+                const int *ea = ea_all + (size_t)tl.b * n, *eb = eb_all + (size_t)tl.b * n;
+                double *C = C_all + (size_t)tl.b * n * n;
+                const int er = ea[r];
+#pragma unroll
+                for (int j = 0; j < kTcDrainCols; ++j) {
+                    const int c = tl.col0 + c0 + j;
+                    if (c >= n || (sym && c < r)) continue;
+                    const double v = i64_times_pow2(acc[j], er + eb[c] - 50);
+                    C[(size_t)r * n + c] = v;
+                    if (sym && c > r) C[(size_t)c * n + r] = v;
+                }
+            }
+        }
+        if (failed) *abort_flag = 1;
+    }
+    if (failed) record_error(err, kDevTimeout);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kTcMmaWarp) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+    }
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tc_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 3-D map of a slice set S[items][6][n][Kp] (bf16): box of kTcKC k x rows x all six digits.
+static bool tc_map(CUtensorMap *m, const __nv_bfloat16 *S, int n, int Kp, int items, int rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tc_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)n, (cuuint64_t)kOzDigits * items};
+    const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)n * Kp * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kTcKC, (cuuint32_t)rows, (cuuint32_t)kOzDigits};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(S), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t launch_oz_gemm_tc(int n, int items, const __nv_bfloat16 *sa, const int *ea, const __nv_bfloat16 *sb,
+                              const int *eb, double *C, int digits, bool sym, int *err, cudaStream_t st)
+{
+    if (n < 1 || items < 1 || digits < 1 || digits > kOzDigits) return cudaErrorInvalidValue;
+    const int Kp = oz_kpad(n);
+    if (Kp % kTcKC != 0) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!tc_map(&ma, sa, n, Kp, items, kTcM) || !tc_map(&mb, sb, n, Kp, items, kTcN)) return cudaErrorInvalidValue;
+    const int TR = (n + kTcM - 1) / kTcM, TC = (n + kTcN - 1) / kTcN;
+    int per_item = TR * TC;
+    if (sym) {
+        per_item = 0;
+        for (int tr = 0; tr < TR; ++tr) per_item += TC - 2 * tr;  // >= 1 for every tr < TR
+    }
+    const long long ntiles = (long long)per_item * items;
+    if (ntiles > 0x7fffffffll) return cudaErrorInvalidValue;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_oz_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)(ntiles < sms ? ntiles : sms);
+    k_oz_gemm_tc<<<grid, kTcThreads, kTcSmem, st>>>(ma, mb, n, Kp, digits - 1, sym, per_item, TC, (int)ntiles, ea, eb,
+                                                    C, err);
+    return cudaGetLastError();
+}
+
+}  // namespace wpcd

@@ -202,7 +202,7 @@ size_t refine_scratch_per_item(int n, int engine)
 // written by the FP32 solve.  iters must be even.
 cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_samples, int sample0, int n,
                           int n_terms, const double *coeffs, void *scratch, double *eps_all, double *X_all,
-                          int iters, int engine, cudaStream_t st)
+                          int iters, int engine, cudaStream_t st, int *err)
 {
     (void)n_terms;
     (void)coeffs;
@@ -236,11 +236,11 @@ cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_s
         const int dg = 6;
         if (engine == 0) {
             CKR(launch_oz_split(n, items, true, x, sXc, eXc, st));                   // columns of X
-            CKR(launch_oz_gemm_slices(n, items, sH, eH, sXc, eXc, xn, st, dg));       // Y = H X
+            CKR(launch_oz_gemm_slices(n, items, sH, eH, sXc, eXc, xn, st, dg, false, err));       // Y = H X
             CKR(launch_oz_split(n, items, true, xn, sYc, eYc, st));                  // columns of Y
             // S = X^T H X and G = X^T X are symmetric: upper tiles, mirrored
-            CKR(launch_oz_gemm_slices(n, items, sXc, eXc, sYc, eYc, W1, st, dg, true));  // S = X^T Y
-            CKR(launch_oz_gemm_slices(n, items, sXc, eXc, sXc, eXc, W2, st, dg, true));  // G = X^T X
+            CKR(launch_oz_gemm_slices(n, items, sXc, eXc, sYc, eYc, W1, st, dg, true, err));  // S = X^T Y
+            CKR(launch_oz_gemm_slices(n, items, sXc, eXc, sXc, eXc, W2, st, dg, true, err));  // G = X^T X
         } else {
             k_bgemm64<false><<<gg, 256, 0, st>>>(n, H, x, xn);
             k_bgemm64<true><<<gg, 256, 0, st>>>(n, x, xn, W1);
@@ -250,7 +250,7 @@ cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_s
         if (engine == 0) {
             CKR(launch_oz_split(n, items, false, x, sXr, eXr, st));              // rows of X
             CKR(launch_oz_split(n, items, true, W2, sEc, eEc, st));              // columns of I + E
-            CKR(launch_oz_gemm_slices(n, items, sXr, eXr, sEc, eEc, xn, st, dg)); // X (I + E)
+            CKR(launch_oz_gemm_slices(n, items, sXr, eXr, sEc, eEc, xn, st, dg, false, err)); // X (I + E)
         } else {
             k_bgemm64<false><<<gg, 256, 0, st>>>(n, x, W2, xn);
         }
@@ -261,7 +261,7 @@ cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_s
     if (iters > 0) {  // Y = H X for the Rayleigh quotients
         if (engine == 0) {
             CKR(launch_oz_split(n, items, true, x, sXc, eXc, st));
-            CKR(launch_oz_gemm_slices(n, items, sH, eH, sXc, eXc, xn, st));
+            CKR(launch_oz_gemm_slices(n, items, sH, eH, sXc, eXc, xn, st, 6, false, err));
         } else {
             k_bgemm64<false><<<gg, 256, 0, st>>>(n, H, x, xn);
         }
@@ -274,13 +274,13 @@ cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_s
 
 // Batched products through either engine (exposed for tests and callers).
 cudaError_t launch_batched_dgemm(int n, int items, bool ta, const double *A, const double *B, double *C,
-                                 void *scratch, int engine, cudaStream_t st)
+                                 void *scratch, int engine, cudaStream_t st, int *err)
 {
     if (engine == 0) {
         __nv_bfloat16 *sa = static_cast<__nv_bfloat16 *>(scratch);
         __nv_bfloat16 *sb = sa + (size_t)items * oz_slice_elems(n);
         int *ea = reinterpret_cast<int *>(sb + (size_t)items * oz_slice_elems(n));
-        return launch_oz_gemm(n, items, ta, A, B, C, sa, sb, ea, ea + (size_t)items * n, st);
+        return launch_oz_gemm(n, items, ta, A, B, C, sa, sb, ea, ea + (size_t)items * n, st, err);
     }
     const int tiles = (n + kBM - 1) / kBM;
     const dim3 gg(tiles, tiles, items);

@@ -441,7 +441,7 @@ wpcd_status run_diag(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, const double *
             }
             Launch L(c, X, WPCD_PHASE_REFINE);
             CK(launch_refine(e.cd_dev, work, nw, ns, smp0 + s0, n, v.n_terms, cf, base, e.eps, e.C, kRefineIters,
-                             c->refine_engine, X.stream));
+                             c->refine_engine, X.stream, X.err));
         }
         return WPCD_OK;
     };
@@ -634,6 +634,7 @@ wpcd_status wpcd_sync(wpcd_ctx *c)
     case kDevOk: return WPCD_OK;
     case kDevEnergyOutside: return WPCD_ERR_ARG;
     case kDevMode: return WPCD_ERR_ARG;
+    case kDevTimeout: return WPCD_ERR_TIMEOUT;
     case kDevNoConverge: return WPCD_ERR_NOCONVERGE;
     case kDevBadSize: return WPCD_ERR_CUDA;
     default: return WPCD_ERR_ARG;
@@ -1037,7 +1038,8 @@ wpcd_status wpcd_batched_dgemm(wpcd_ctx *c, int n, int items, int trans_a, const
     wpcd_status st = ws_reserve(c, c->main, c->main.ws_ref, batched_dgemm_scratch(n, items));
     if (st) return st;
     Launch L(c, c->main, WPCD_PHASE_REFINE);
-    CK(launch_batched_dgemm(n, items, trans_a != 0, A_dev, B_dev, C_dev, c->main.ws_ref.p, engine, c->main.stream));
+    CK(launch_batched_dgemm(n, items, trans_a != 0, A_dev, B_dev, C_dev, c->main.ws_ref.p, engine, c->main.stream,
+                            c->main.err));
     return WPCD_OK;
 }
 

@@ -32,7 +32,8 @@ enum DevErr : int {
     kDevNoConverge = 2,
     kDevBranch = 3,
     kDevBadSize = 4,
-    kDevMode = 5  // resolvent mode not defined for this solve (SWP-bin average with a bound state)
+    kDevMode = 5,    // resolvent mode not defined for this solve (SWP-bin average with a bound state)
+    kDevTimeout = 6  // a bounded wait inside a kernel ran out
 };
 
 // One channel of a projected potential set, as the kernels see it.
@@ -202,18 +203,23 @@ cudaError_t launch_jacobi_mixed(const ChanDev *chans_dev, const int *work_ch_dev
                                 int sample0, int n_terms, const double *coeffs, int n, double *lam_s, double *X_s,
                                 float *Cf_s, double *H_s, int *status_all, int n_ch_total, int *err, cudaStream_t st,
                                 int threads = 256);
+constexpr int kOzDigits = 6;  // balanced 8-bit digits per operand of the Ozaki products
 size_t oz_slice_elems(int n);
+int oz_kpad(int n);
 cudaError_t launch_oz_gemm(int n, int items, bool ta, const double *A, const double *B, double *C,
-                           __nv_bfloat16 *sa, __nv_bfloat16 *sb, int *ea, int *eb, cudaStream_t st);
+                           __nv_bfloat16 *sa, __nv_bfloat16 *sb, int *ea, int *eb, cudaStream_t st, int *err = nullptr);
 cudaError_t launch_oz_split(int n, int items, bool cols, const double *M, __nv_bfloat16 *S, int *e, cudaStream_t st);
 cudaError_t launch_oz_gemm_slices(int n, int items, const __nv_bfloat16 *sa, const int *ea, const __nv_bfloat16 *sb,
-                                  const int *eb, double *C, cudaStream_t st, int digits = 6, bool sym = false);
+                                  const int *eb, double *C, cudaStream_t st, int digits = 6, bool sym = false,
+                                  int *err = nullptr);
+cudaError_t launch_oz_gemm_tc(int n, int items, const __nv_bfloat16 *sa, const int *ea, const __nv_bfloat16 *sb,
+                              const int *eb, double *C, int digits, bool sym, int *err, cudaStream_t st);
 size_t refine_scratch_per_item(int n, int engine);
 cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_samples, int sample0, int n,
                           int n_terms, const double *coeffs, void *scratch, double *eps_all, double *X_all,
-                          int iters, int engine, cudaStream_t st);
+                          int iters, int engine, cudaStream_t st, int *err = nullptr);
 cudaError_t launch_batched_dgemm(int n, int items, bool ta, const double *A, const double *B, double *C,
-                                 void *scratch, int engine, cudaStream_t st);
+                                 void *scratch, int engine, cudaStream_t st, int *err = nullptr);
 size_t batched_dgemm_scratch(int n, int items);
 cudaError_t launch_plan(const ChanDev *chans_dev, int n_ch, int maxN, const double *e_lab, int n_E, PlanDev plan,
                         int *err, cudaStream_t st, int n_plans = 1);

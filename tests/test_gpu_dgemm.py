@@ -51,3 +51,22 @@ def test_batched_dgemm_engines(ctx, n, trans_a):
         err = np.abs(C.astype(np.longdouble) - ref)
         assert np.all(np.isfinite(C))
         assert np.all(err <= tol * bound + 1e-300), (engine, float(np.max(err / (bound + 1e-300))))
+
+
+def test_batched_dgemm_long_contraction(ctx):
+    # K beyond the tcgen05 step schedule (n > 768) takes the mma.sync kernel
+    import torch
+    from paper_2106_00454_gb300 import api
+    n = 800
+    A, B = _mats(n, 1, 11)
+    ref = np.matmul(A.astype(np.longdouble), B.astype(np.longdouble))
+    aA, aB = np.abs(A), np.abs(B)
+    scaled = (aA.max(axis=2, keepdims=True) * aB.sum(axis=1, keepdims=True)
+              + aA.sum(axis=2, keepdims=True) * aB.max(axis=1, keepdims=True))
+    dA = torch.tensor(A, device="cuda:0")
+    dB = torch.tensor(B, device="cuda:0")
+    dC = torch.full_like(dA, float("nan"))
+    ctx.batched_dgemm(dA, dB, dC, engine=api.REFINE_TENSOR)
+    ctx.sync()
+    err = np.abs(dC.cpu().numpy().astype(np.longdouble) - ref)
+    assert np.all(err <= 2.0 ** -46 * scaled + 1e-300)
