@@ -20,6 +20,7 @@ constexpr size_t kMixSmemCap = 200 * 1024;
 constexpr float kRelTol = 1.1920929e-7f;  // 2^-23
 
 __host__ __device__ inline int mpad(int n) { return (n + 1) & ~1; }
+__host__ __device__ inline int mldc(int n) { return (n + 3) & ~3; }  // column stride of C: float4 rows
 __host__ __device__ inline size_t mpacked(int n) { return (size_t)n * (n + 1) / 2; }
 
 // Index pairs (P, P2), P < P2, of the rotation slots whose 2 x 2 blocks of A
@@ -31,24 +32,46 @@ __host__ __device__ inline int mquads(int n)
     return h * (h - 1) / 2;
 }
 
-// A float packed (>= 10 n floats) | cos, sin, a_pp', a_qq' float [h] | p, q int [h] |
-// reduction double [64] | rank int [n, even] | flags int [2] | slot pairs ushort [quads, even] |
-// C float [n*n]
+__host__ __device__ inline size_t mix_a_floats(int n)
+{
+    size_t a = mpacked(mpad(n));  // the odd-n phantom row and column are kept (as zeros)
+    if (a < (size_t)10 * n) a = (size_t)10 * n;
+    return (a + 3) & ~(size_t)3;  // the slot table after it is 16-byte aligned
+}
+
+// A float packed [npad] | slot table int4 [h] {p, q, base(p), base(q)} | rotations float2 [h] {c, s} |
+// a_pp', a_qq' float [h] each | flags int [4] | slot pairs ushort [quads, even] | (16-byte aligned)
+// C float [n][ldc] (column-major) when it is kept in shared memory
 __host__ __device__ inline size_t mix_smem(int n, bool c_in_smem)
 {
     const int h = mpad(n) / 2;
-    size_t a = mpacked(n);
-    if (a < (size_t)10 * n) a = (size_t)10 * n;
-    a = (a + 1) & ~(size_t)1;  // keep the next region 8-byte aligned
-    size_t b = a * 4 + (size_t)4 * h * 4 + (size_t)2 * h * 4;
-    b = (b + 7) & ~(size_t)7;
-    b += 64 * 8 + (size_t)mpad(n) * 4 + 2 * 4;
+    size_t b = mix_a_floats(n) * 4 + (size_t)h * (16 + 8 + 8) + 4 * 4;
     b += (size_t)((mquads(n) + 1) & ~1) * 2;
-    if (c_in_smem) b += (size_t)n * n * 4;
+    b = (b + 15) & ~(size_t)15;
+    if (c_in_smem) b += (size_t)n * mldc(n) * 4;
     return b;
 }
 
 size_t jacobi_mixed_smem_bytes(int n, bool c_in_smem) { return mix_smem(n, c_in_smem); }
+size_t jacobi_mixed_c_bytes(int n) { return (size_t)n * mldc(n) * 4; }
+
+// Rotation slot k of round r (0 <= r < M = npad - 1) of the round-robin
+// tournament: the same pairs as jac_pair_of, with the modulo reduced to one
+// conditional correction (r + k < 2M, r - k > -M).
+__device__ __forceinline__ void mix_pair(int r, int k, int M, int &p, int &q)
+{
+    int a = 0, b = 1 + r;
+    if (k != 0) {
+        a = r + k;
+        if (a >= M) a -= M;
+        ++a;
+        b = r - k;
+        if (b < 0) b += M;
+        ++b;
+    }
+    p = a < b ? a : b;
+    q = a < b ? b : a;
+}
 
 template <bool C_SMEM>
 __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *chans, const int *work_ch, int n_work_ch,
@@ -60,8 +83,8 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
     const int smp = sample0 + blockIdx.x / n_work_ch;
     const int cidx = work_ch[wc];
     const ChanDev ch = chans[cidx];
-    const int n = ch.n, N = ch.N, npad = mpad(n), h = npad / 2;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int n = ch.n, N = ch.N, npad = mpad(n), h = npad / 2, M = npad - 1, ldc = mldc(n);
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     if ((size_t)dyn_smem_bytes() < mix_smem(n, C_SMEM)) {
         if (tid == 0) {
             status_all[(size_t)smp * n_ch_total + cidx] = -1;
@@ -69,24 +92,17 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
         }
         return;
     }
-    extern __shared__ double smem_d[];
-    unsigned char *sb = reinterpret_cast<unsigned char *>(smem_d);
-    size_t alen = mpacked(n);
-    if (alen < (size_t)10 * n) alen = (size_t)10 * n;
-    alen = (alen + 1) & ~(size_t)1;
+    extern __shared__ float4 smem_f4[];
+    unsigned char *sb = reinterpret_cast<unsigned char *>(smem_f4);
     float *A = reinterpret_cast<float *>(sb);
-    float *rc = A + alen, *rs = rc + h, *dpp = rs + h, *dqq = dpp + h;
-    int *pp_ = reinterpret_cast<int *>(dqq + h), *qq_ = pp_ + h;
-    size_t off = (alen + 4 * (size_t)h) * 4 + (size_t)2 * h * 4;
-    off = (off + 7) & ~(size_t)7;
-    double *red = reinterpret_cast<double *>(sb + off);
-    int *rank = reinterpret_cast<int *>(red + 64);
-    int *flags = rank + npad;
-    unsigned short *quad = reinterpret_cast<unsigned short *>(flags + 2);
+    int4 *sl = reinterpret_cast<int4 *>(A + mix_a_floats(n));
+    float2 *cs = reinterpret_cast<float2 *>(sl + h);
+    float *dpp = reinterpret_cast<float *>(cs + h), *dqq = dpp + h;
+    int *flags = reinterpret_cast<int *>(dqq + h);  // [0] rotation in this sweep, [1..3] in this round
+    unsigned short *quad = reinterpret_cast<unsigned short *>(flags + 4);
     const int nq = mquads(n);
-    float *Cs = C_SMEM ? reinterpret_cast<float *>(quad + ((nq + 1) & ~1)) : nullptr;
-    float *Cg = Cf_s + (size_t)blockIdx.x * n * n;
-    float *C = C_SMEM ? Cs : Cg;
+    const size_t c_off = ((size_t)(reinterpret_cast<unsigned char *>(quad + ((nq + 1) & ~1)) - sb) + 15) & ~(size_t)15;
+    float *C = C_SMEM ? reinterpret_cast<float *>(sb + c_off) : Cf_s + (size_t)blockIdx.x * n * ldc;
     const double *cf = coeffs ? coeffs + (size_t)smp * (n_terms - 1) : nullptr;
 
     // ---- H in FP64, rounded to FP32; the FP64 H also goes to H_s for the refinement
@@ -103,93 +119,100 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
             Hg[(size_t)j * n + i] = v;
         }
     }
-    for (int e = tid; e < n * n; e += nt) {
-        int i = e / n, j = e - i * n;
-        C[(size_t)i * n + j] = (i == j) ? 1.0f : 0.0f;
+    if (npad > n)  // odd n: the phantom index n pairs with a zero row and column, so its rotation is the identity
+        for (int i = tid; i <= n; i += nt) A[pk(i, n)] = 0.0f;
+    for (int e = tid; e < n * ldc; e += nt) {
+        const int col = e / ldc, row = e - col * ldc;
+        C[e] = (row == col) ? 1.0f : 0.0f;  // rows n .. ldc-1 stay zero
     }
     for (int e = tid; e < h * h; e += nt) {  // slot pairs in row order of P
         const int P = e / h, P2 = e - P * h;
         if (P < P2) quad[P * h - P * (P + 1) / 2 + (P2 - P - 1)] = (unsigned short)((P << 8) | P2);
     }
+    if (tid < 4) flags[tid] = 0;
     __syncthreads();
 
-    int sweeps = 0;
+    int sweeps = 0, g3 = 0;  // g3: the round's flag, cycling over three so a reset never races a read
     bool converged = false;
     while (sweeps < kMixMaxSweeps) {
         if (tid == 0) flags[0] = 0;
         __syncthreads();
         ++sweeps;
-        for (int r = 0; r < npad - 1; ++r) {
+        for (int r = 0; r < M; ++r) {
+            const int nx3 = g3 == 2 ? 0 : g3 + 1;
+            if (tid == 0) flags[1 + nx3] = 0;  // last read two rounds ago, before this round's barrier
             for (int k = tid; k < h; k += nt) {
                 int p, q;
-                jac_pair_of(r, k, npad, p, q);
-                pp_[k] = p;
-                qq_[k] = q;
-                float c = 1.0f, s = 0.0f, app = 0.0f, aqq = 0.0f;
-                if (q < n) {
-                    app = A[pk(p, p)];
-                    aqq = A[pk(q, q)];
-                    const float apq = A[pk(p, q)];
-                    if (fabsf(apq) > kRelTol * sqrtf(fabsf(app) * fabsf(aqq))) {
-                        const float tau = (aqq - app) / (2.0f * apq);
-                        float t;
-                        if (fabsf(tau) > 1e18f) t = 0.5f / tau;
-                        else t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
-                        c = 1.0f / sqrtf(1.0f + t * t);
-                        s = t * c;
-                        app -= t * apq;
-                        aqq += t * apq;
-                        flags[0] = 1;
-                    }
+                mix_pair(r, k, M, p, q);
+                const int pb = p * (p + 1) / 2, qb = q * (q + 1) / 2;
+                float c = 1.0f, s = 0.0f, app = A[pb + p], aqq = A[qb + q];
+                const float apq = A[qb + p];
+                if (fabsf(apq) > kRelTol * sqrtf(fabsf(app) * fabsf(aqq))) {
+                    const float tau = (aqq - app) / (2.0f * apq);
+                    float t;
+                    if (fabsf(tau) > 1e18f) t = 0.5f / tau;
+                    else t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+                    c = 1.0f / sqrtf(1.0f + t * t);
+                    s = t * c;
+                    app -= t * apq;
+                    aqq += t * apq;
+                    flags[0] = 1;
+                    flags[1 + g3] = 1;
                 }
-                rc[k] = c;
-                rs[k] = s;
+                sl[k] = make_int4(p, q, pb, qb);
+                cs[k] = make_float2(c, s);
                 dpp[k] = app;
                 dqq[k] = aqq;
             }
             __syncthreads();
-            for (int e = tid; e < nq; e += nt) {
-                const unsigned pr = quad[e];
-                const int P = pr >> 8, P2 = pr & 0xFF;
-                const int p = pp_[P], q = qq_[P], p2 = pp_[P2], q2 = qq_[P2];
-                const float c = rc[P], s = rs[P], c2 = rc[P2], s2 = rs[P2];
-                if (s == 0.0f && s2 == 0.0f) continue;  // both rotations are the identity
-                const bool qv = q < n, q2v = q2 < n;
-                const float b00 = A[pk(p, p2)];
-                const float b01 = q2v ? A[pk(p, q2)] : 0.0f;
-                const float b10 = qv ? A[pk(q, p2)] : 0.0f;
-                const float b11 = (qv && q2v) ? A[pk(q, q2)] : 0.0f;
-                const float x00 = c2 * b00 - s2 * b01, x01 = s2 * b00 + c2 * b01;
-                const float x10 = c2 * b10 - s2 * b11, x11 = s2 * b10 + c2 * b11;
-                A[pk(p, p2)] = c * x00 - s * x10;
-                if (q2v) A[pk(p, q2)] = c * x01 - s * x11;
-                if (qv) A[pk(q, p2)] = s * x00 + c * x10;
-                if (qv && q2v) A[pk(q, q2)] = s * x01 + c * x11;
-            }
-            for (int k = tid; k < h; k += nt) {
-                const int p = pp_[k], q = qq_[k];
-                if (q < n && rs[k] != 0.0f) {
-                    A[pk(p, p)] = dpp[k];
-                    A[pk(q, q)] = dqq[k];
-                    A[pk(p, q)] = 0.0f;
+            if (flags[1 + g3]) {  // some slot rotates (the same value for every thread)
+                for (int e = tid; e < nq; e += nt) {
+                    const unsigned pr = quad[e];
+                    const int P = pr >> 8, P2 = pr & 0xFF;
+                    const float2 r1 = cs[P], r2 = cs[P2];
+                    if (r1.y == 0.0f && r2.y == 0.0f) continue;  // both rotations are the identity
+                    const int4 u = sl[P], v = sl[P2];
+                    // packed index of (x, y): base(max) + min
+                    const int i00 = u.x <= v.x ? v.z + u.x : u.z + v.x;
+                    const int i01 = u.x <= v.y ? v.w + u.x : u.z + v.y;
+                    const int i10 = u.y <= v.x ? v.z + u.y : u.w + v.x;
+                    const int i11 = u.y <= v.y ? v.w + u.y : u.w + v.y;
+                    const float b00 = A[i00], b01 = A[i01], b10 = A[i10], b11 = A[i11];
+                    const float c = r1.x, s = r1.y, c2 = r2.x, s2 = r2.y;
+                    const float x00 = c2 * b00 - s2 * b01, x01 = s2 * b00 + c2 * b01;
+                    const float x10 = c2 * b10 - s2 * b11, x11 = s2 * b10 + c2 * b11;
+                    A[i00] = c * x00 - s * x10;
+                    A[i01] = c * x01 - s * x11;
+                    A[i10] = s * x00 + c * x10;
+                    A[i11] = s * x01 + c * x11;
                 }
-            }
-            // C is kept column-major (column s contiguous): one warp per rotation,
-            // its lanes walking consecutive rows of the two columns; a warp
-            // skips an identity rotation as a whole
-            for (int k = tid >> 5; k < h; k += nt >> 5) {
-                const int p = pp_[k], q = qq_[k];
-                const float s = rs[k];
-                if (q >= n || s == 0.0f) continue;
-                const float c = rc[k];
-                float *Cp = C + (size_t)p * n, *Cq = C + (size_t)q * n;
-                for (int row = tid & 31; row < n; row += 32) {
-                    const float cp = Cp[row], cq = Cq[row];
-                    Cp[row] = c * cp - s * cq;
-                    Cq[row] = s * cp + c * cq;
+                for (int k = tid; k < h; k += nt) {
+                    if (cs[k].y != 0.0f) {
+                        const int4 u = sl[k];
+                        A[u.z + u.x] = dpp[k];
+                        A[u.w + u.y] = dqq[k];
+                        A[u.w + u.x] = 0.0f;
+                    }
                 }
+                // C is column-major (column s contiguous, stride ldc): one warp per
+                // rotation, each lane four consecutive rows of the two columns
+                const int nv = ldc >> 2;
+                for (int k = tid >> 5; k < h; k += nt >> 5) {
+                    const float2 r1 = cs[k];
+                    if (r1.y == 0.0f) continue;
+                    const int4 u = sl[k];
+                    float4 *Cp = reinterpret_cast<float4 *>(C + (size_t)u.x * ldc);
+                    float4 *Cq = reinterpret_cast<float4 *>(C + (size_t)u.y * ldc);
+                    const float c = r1.x, s = r1.y;
+                    for (int v = lane; v < nv; v += 32) {
+                        const float4 a = Cp[v], b = Cq[v];
+                        Cp[v] = make_float4(c * a.x - s * b.x, c * a.y - s * b.y, c * a.z - s * b.z, c * a.w - s * b.w);
+                        Cq[v] = make_float4(s * a.x + c * b.x, s * a.y + c * b.y, s * a.z + c * b.z, s * a.w + c * b.w);
+                    }
+                }
+                __syncthreads();
             }
-            __syncthreads();
+            g3 = nx3;
         }
         if (flags[0] == 0) {
             converged = true;
@@ -202,7 +225,7 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
     double *X = X_s + (size_t)blockIdx.x * n * n;  // row-major out of the column-major C
     for (int e = tid; e < n * n; e += nt) {
         const int col = e / n, row = e - col * n;
-        X[(size_t)row * n + col] = (double)C[e];
+        X[(size_t)row * n + col] = (double)C[(size_t)col * ldc + row];
     }
     for (int i = tid; i < n; i += nt) lam_s[(size_t)blockIdx.x * n + i] = (double)A[pk(i, i)];
     if (tid == 0) {

@@ -405,13 +405,14 @@ wpcd_status run_diag(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, const double *
                                          X.err, X.stream, th);
             // the FP32 solve alone, into the start of the refinement scratch
             const bool cs = jacobi_mixed_c_in_smem(n);
-            const size_t per = refine_scratch_per_item(n, c->refine_engine) + (cs ? 0 : (size_t)n * n * 4) + 256;
+            const size_t per = refine_scratch_per_item(n, c->refine_engine) + (cs ? 0 : jacobi_mixed_c_bytes(n)) + 256;
             if (ws_reserve(c, X, X.ws_ref, per * nw * ns)) return cudaErrorMemoryAllocation;
             unsigned char *base = static_cast<unsigned char *>(X.ws_ref.p);
             double *Xs = reinterpret_cast<double *>(base);
+            const size_t c_off = (refine_scratch_per_item(n, c->refine_engine) * nw * ns + 255) & ~(size_t)255;
             return launch_jacobi_mixed(e.cd_dev, work, nw, ns, smp0, v.n_terms, cf, n, Xs + (size_t)5 * ns * nw * n * n,
-                                       Xs, reinterpret_cast<float *>(base + refine_scratch_per_item(n, c->refine_engine) * nw * ns),
-                                       Xs + (size_t)ns * nw * n * n, e.status, v.n_ch, X.err, X.stream, th);
+                                       Xs, reinterpret_cast<float *>(base + c_off), Xs + (size_t)ns * nw * n * n,
+                                       e.status, v.n_ch, X.err, X.stream, th);
         });
         if (threads < 0) return WPCD_ERR_CUDA;
         if (prec == WPCD_PREC_FP64) {
@@ -422,14 +423,14 @@ wpcd_status run_diag(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, const double *
         }
         const bool c_smem = jacobi_mixed_c_in_smem(n);
         const size_t ref_item = refine_scratch_per_item(n, c->refine_engine);
-        const size_t per_item = ref_item + (c_smem ? 0 : (size_t)n * n * 4) + 256;
+        const size_t per_item = ref_item + (c_smem ? 0 : jacobi_mixed_c_bytes(n)) + 256;
         int chunk = (int)std::max<size_t>(1, kRefineScratchBytes / (per_item * nw));
         chunk = std::min(chunk, nsmp);
         wpcd_status st2 = ws_reserve(c, X, X.ws_ref, per_item * nw * chunk);
         if (st2) return st2;
         unsigned char *base = static_cast<unsigned char *>(X.ws_ref.p);
         double *Xs = reinterpret_cast<double *>(base);  // first block of the refinement scratch
-        float *Cf = reinterpret_cast<float *>(base + ref_item * nw * chunk);
+        float *Cf = reinterpret_cast<float *>(base + ((ref_item * nw * chunk + 255) & ~(size_t)255));
         for (int s0 = 0; s0 < nsmp; s0 += chunk) {
             const int ns = std::min(chunk, nsmp - s0);
             {

@@ -199,6 +199,7 @@ int jacobi_f64_occupancy(int n, int threads);
 int jacobi_mixed_occupancy(int n, int threads);
 bool jacobi_mixed_c_in_smem(int n);   // eigenvector matrix in shared memory (else global)
 size_t jacobi_mixed_smem_bytes(int n, bool c_in_smem);
+size_t jacobi_mixed_c_bytes(int n);  // global eigenvector scratch per item (C kept in global memory)
 cudaError_t launch_jacobi_mixed(const ChanDev *chans_dev, const int *work_ch_dev, int n_work_ch, int n_samples,
                                 int sample0, int n_terms, const double *coeffs, int n, double *lam_s, double *X_s,
                                 float *Cf_s, double *H_s, int *status_all, int n_ch_total, int *err, cudaStream_t st,

@@ -114,3 +114,16 @@ def test_mixed_eigenvalues_refined(ctx, orc):
     _report("eigenvalue_error_over_bin_width", {"worst": worst, "at": where, "orthogonality": orth})
     assert orth < 1e-6
     assert worst < 1e-4, where
+
+
+@pytest.mark.parametrize("n_wp", [33, 57])
+def test_mixed_odd_nwp(ctx, orc, n_wp):
+    """Odd N_WP: the uncoupled matrices have odd n (the FP32 Jacobi pairs the
+    last index with a zero phantom row), the coupled ones n = 2 N_WP."""
+    import dataclasses
+
+    from paper_2106_00454_gb300 import api
+    wl = W.workload_all_channels(n_wp=n_wp, jmax=3, n_e=41)
+    wl = dataclasses.replace(wl, coeffs=W.coefficient_samples(3))
+    md = api.Model(ctx, wl)
+    _report(f"odd_nwp{n_wp}", compare_mixed(wl, gpu_run(ctx, md, wl, prec=MIXED), oracle_run(orc, wl)))
