@@ -34,30 +34,36 @@ constexpr int kOzKC = 32;  // k staged per step
 int oz_kpad(int n) { return (n + kOzKC - 1) / kOzKC * kOzKC; }
 size_t oz_slice_elems(int n) { return (size_t)kOzP * n * oz_kpad(n); }
 
-// Exponent of every row (COLS = false) or column (COLS = true) of the n x n
-// matrices: e with max|v| < 2^e (0 for an all-zero vector).  For rows one warp
-// per row, for columns one thread per column (both read coalesced).
-template <bool COLS>
-__global__ void k_oz_exp(int n, const double *M_all, int *e_all)
+// GB300 issues FP64 at 2 operations per clock per SM, so the split works on
+// the IEEE-754 fields with integer operations.
+//
+// N = rint(x 2^{47-e}) for |x| < 2^e (round half to even): x = m 2^{E-1075}
+// with the 53-bit significand m, so N = m 2^{-s}, s = 1028 + e - E >= 6.
+__device__ __forceinline__ long long oz_scaled(double x, int e)
 {
-    const int b = blockIdx.y;
-    const double *M = M_all + (size_t)b * n * n;
-    double m = 0.0;
-    int v;
-    if (COLS) {
-        v = blockIdx.x * blockDim.x + threadIdx.x;
-        if (v >= n) return;
-        for (int k = 0; k < n; ++k) m = fmax(m, fabs(M[(size_t)k * n + v]));
-    } else {
-        v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-        if (v >= n) return;
-        for (int k = threadIdx.x & 31; k < n; k += 32) m = fmax(m, fabs(M[(size_t)v * n + k]));
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((threadIdx.x & 31) != 0) return;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E == 0 || E == 0x7FF) {  // zero, subnormal or not finite: the FP64 route
+        if ((b << 1) == 0) return 0;
+        return __double2ll_rn(ldexp(x, 47 - e));
     }
-    int ex = 0;
-    if (m > 0.0) frexp(m, &ex);  // m < 2^ex
-    e_all[(size_t)b * n + v] = ex;
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int s = 1028 + e - E;
+    unsigned long long q = 0;
+    if (s < 54) {  // for s >= 54, m 2^{-s} < 1/2
+        q = m >> s;
+        const unsigned long long rem = m & ((1ull << s) - 1), half = 1ull << (s - 1);
+        q += (rem > half || (rem == half && (q & 1))) ? 1 : 0;
+    }
+    return (b >> 63) ? -(long long)q : (long long)q;
+}
+
+// BF16 bits of a small integer (|d| < 2^8, exact): 1.5 2^23 + d as an FP32 bit
+// pattern, minus 1.5 2^23, leaves d in FP32 with a zero low half.
+__device__ __forceinline__ __nv_bfloat16 oz_bf16_of_int(int d)
+{
+    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+    return __ushort_as_bfloat16((unsigned short)(__float_as_uint(f) >> 16));
 }
 
 // The six balanced 8-bit digits of x / 2^e: N = rint(x 2^{47-e}) (|N| <= 2^47),
@@ -67,65 +73,97 @@ __global__ void k_oz_exp(int n, const double *M_all, int *e_all)
 // sum grows like sqrt(k) instead of k.
 __device__ __forceinline__ void oz_digits(double x, int e, __nv_bfloat16 *d, size_t stride)
 {
-    const int be = 1023 + 47 - e;  // biased exponent of 2^{47-e}
-    const double scale = (be >= 1 && be <= 2046) ? __hiloint2double(be << 20, 0) : ldexp(1.0, 47 - e);  // exact
-    long long N = __double2ll_rn(x * scale);
+    long long N = oz_scaled(x, e);
 #pragma unroll
     for (int p = kOzP - 1; p >= 1; --p) {
-        const long long dig = ((N + 128) & 0xFF) - 128;
-        d[(size_t)p * stride] = __float2bfloat16_rn((float)(int)dig);
+        const int dig = (int)((N + 128) & 0xFF) - 128;
+        d[(size_t)p * stride] = oz_bf16_of_int(dig);
         N = (N - dig) >> 8;  // exact: N - dig is a multiple of 256
     }
-    d[0] = __float2bfloat16_rn((float)(int)N);
+    d[0] = oz_bf16_of_int((int)N);
 }
 
-// Row slices: S[b][p][v][k] = digit p of M[v][k]; one thread per element, k
-// fastest (coalesced reads and writes); k in [n, Kp) is zero padding.
-__global__ void k_oz_split_rows(int n, int Kp, const double *M_all, const int *e_all, __nv_bfloat16 *S_all)
+// Magnitude of x as an ordered integer (the IEEE-754 bits without the sign).
+__device__ __forceinline__ unsigned long long oz_mag(double x)
 {
-    const int b = blockIdx.z, v = blockIdx.y;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= Kp) return;
-    const double x = (k < n) ? M_all[(size_t)b * n * n + (size_t)v * n + k] : 0.0;
-    oz_digits(x, e_all[(size_t)b * n + v], S_all + (size_t)b * kOzP * n * Kp + (size_t)v * Kp + k, (size_t)n * Kp);
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
 
-// Column slices: S[b][p][v][k] = digit p of M[k][v]; 32 x 32 tiles transposed
-// through shared memory so that both the reads (v fastest) and the writes (k
-// fastest) are coalesced.  Block 32 x 8.
-__global__ void k_oz_split_cols(int n, int Kp, const double *M_all, const int *e_all, __nv_bfloat16 *S_all)
+// e with max|v| < 2^e from the magnitude bits of the largest |v| (0 for an
+// all-zero vector): 2^{E-1023} <= max < 2^{E-1022}.
+__device__ __forceinline__ int oz_exp_of(unsigned long long mag)
+{
+    const int E = (int)(mag >> 52);
+    if (E != 0) return E - 1022;
+    int ex = 0;
+    if (mag != 0) frexp(__longlong_as_double((long long)mag), &ex);  // subnormal
+    return ex;
+}
+
+// Row slices: S[b][p][v][k] = digit p of M[v][k], one warp per row v: the
+// row's exponent from a warp maximum, then its digits with k fastest
+// (coalesced reads and writes); k in [n, Kp) is zero padding.
+__global__ void __launch_bounds__(256) k_oz_split_rows(int n, int Kp, const double *M_all, int *e_all,
+                                                       __nv_bfloat16 *S_all)
+{
+    const int b = blockIdx.y, v = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (v >= n) return;
+    const double *row = M_all + (size_t)b * n * n + (size_t)v * n;
+    unsigned long long m = 0;
+    for (int k = lane; k < n; k += 32) m = max(m, oz_mag(row[k]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int ex = oz_exp_of(m);
+    if (lane == 0) e_all[(size_t)b * n + v] = ex;
+    __nv_bfloat16 *S = S_all + (size_t)b * kOzP * n * Kp + (size_t)v * Kp;
+    for (int k = lane; k < Kp; k += 32) oz_digits(k < n ? row[k] : 0.0, ex, S + k, (size_t)n * Kp);
+}
+
+// Column slices: S[b][p][v][k] = digit p of M[k][v], one CTA (32 x 8) per 32
+// columns: the column maxima first (reads along v), then 32 x 32 tiles
+// transposed through shared memory so that both the reads (v fastest) and the
+// writes (k fastest) are coalesced.
+__global__ void __launch_bounds__(256) k_oz_split_cols(int n, int Kp, const double *M_all, int *e_all,
+                                                       __nv_bfloat16 *S_all)
 {
     __shared__ double tile[32][33];
-    const int b = blockIdx.z;
-    const int v0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    __shared__ unsigned long long mcol[8][32];
+    __shared__ int ecol[32];
+    const int b = blockIdx.y;
+    const int v0 = blockIdx.x * 32, tx = threadIdx.x, ty = threadIdx.y;
     const double *M = M_all + (size_t)b * n * n;
-    for (int r = threadIdx.y; r < 32; r += 8) {
-        const int k = k0 + r, v = v0 + threadIdx.x;
-        tile[r][threadIdx.x] = (k < n && v < n) ? M[(size_t)k * n + v] : 0.0;
+    unsigned long long m = 0;
+    if (v0 + tx < n)
+        for (int k = ty; k < n; k += 8) m = max(m, oz_mag(M[(size_t)k * n + v0 + tx]));
+    mcol[ty][tx] = m;
+    __syncthreads();
+    if (ty == 0) {
+        for (int r = 1; r < 8; ++r) m = max(m, mcol[r][tx]);
+        ecol[tx] = oz_exp_of(m);
+        if (v0 + tx < n) e_all[(size_t)b * n + v0 + tx] = ecol[tx];
     }
     __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += 8) {
-        const int v = v0 + r, k = k0 + threadIdx.x;
-        if (v >= n || k >= Kp) continue;
-        oz_digits(tile[threadIdx.x][r], e_all[(size_t)b * n + v],
-                  S_all + (size_t)b * kOzP * n * Kp + (size_t)v * Kp + k, (size_t)n * Kp);
+    __nv_bfloat16 *S = S_all + (size_t)b * kOzP * n * Kp;
+    for (int k0 = 0; k0 < Kp; k0 += 32) {
+        for (int r = ty; r < 32; r += 8) {
+            const int k = k0 + r, v = v0 + tx;
+            tile[r][tx] = (k < n && v < n) ? M[(size_t)k * n + v] : 0.0;
+        }
+        __syncthreads();
+        for (int r = ty; r < 32; r += 8) {
+            const int v = v0 + r, k = k0 + tx;
+            if (v < n) oz_digits(tile[tx][r], ecol[r], S + (size_t)v * Kp + k, (size_t)n * Kp);
+        }
+        __syncthreads();
     }
 }
 
-// C = op(A) B for `items` n x n FP64 matrices (op(A) = A^T when ta), through
-// the slices.  Scratch: sa, sb hold oz_slice_elems(n) bf16 per item; ea, eb n ints per item.
 // Digit slices of the rows (cols = false) or columns (cols = true) of `items`
 // n x n matrices: S [items][P][n][Kp] bf16, e [items][n].
 cudaError_t launch_oz_split(int n, int items, bool cols, const double *M, __nv_bfloat16 *S, int *e, cudaStream_t st)
 {
     const int Kp = oz_kpad(n);
-    if (cols) {
-        k_oz_exp<true><<<dim3((n + 127) / 128, items), 128, 0, st>>>(n, M, e);
-        k_oz_split_cols<<<dim3((n + 31) / 32, (Kp + 31) / 32, items), dim3(32, 8), 0, st>>>(n, Kp, M, e, S);
-    } else {
-        k_oz_exp<false><<<dim3((n + 7) / 8, items), 256, 0, st>>>(n, M, e);
-        k_oz_split_rows<<<dim3((Kp + 127) / 128, n, items), 128, 0, st>>>(n, Kp, M, e, S);
-    }
+    if (cols) k_oz_split_cols<<<dim3((n + 31) / 32, items), dim3(32, 8), 0, st>>>(n, Kp, M, e, S);
+    else k_oz_split_rows<<<dim3((n + 7) / 8, items), 256, 0, st>>>(n, Kp, M, e, S);
     return cudaGetLastError();
 }
 
@@ -136,6 +174,8 @@ cudaError_t launch_oz_gemm_slices(int n, int items, const __nv_bfloat16 *sa, con
     return launch_oz_gemm_tc(n, items, sa, ea, sb, eb, C, digits, sym, err, st);
 }
 
+// C = op(A) B for `items` n x n FP64 matrices (op(A) = A^T when ta), through
+// the slices.  Scratch: sa, sb hold oz_slice_elems(n) bf16 per item; ea, eb n ints per item.
 cudaError_t launch_oz_gemm(int n, int items, bool ta, const double *A, const double *B, double *C,
                            __nv_bfloat16 *sa, __nv_bfloat16 *sb, int *ea, int *eb, cudaStream_t st,
                            int *err)

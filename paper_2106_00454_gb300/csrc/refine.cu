@@ -92,48 +92,96 @@ __global__ void __launch_bounds__(256) k_bgemm64(int n, const double *A_all, con
     }
 }
 
+// GB300 issues FP64 at 2 operations per clock per SM; conversions between
+// FP64 and FP32 go through the bit patterns with integer operations instead.
+// f32_trunc: x truncated to 24 significant bits (relative error < 2^-23),
+// zero below the FP32 normal range.
+__device__ __forceinline__ float f32_trunc(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int fe = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+    if (fe <= 0) return 0.0f;
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+}
+
+// The FP32 value as FP64 (exact; FP32 subnormals, below 1.2e-38, become zero).
+__device__ __forceinline__ double f64_of(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned fe = (u >> 23) & 0xFF;
+    if (fe == 0) return 0.0;
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(fe - 127 + 1023) << 52) |
+                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
 // One CTA per item: lambda, the threshold delta, and I + E written over G.
+// Warp per row, lanes along the row.  Only what needs FP64 stays FP64: the
+// Rayleigh quotients, lambda_j - lambda_i and the numerator S_ij + lambda_j R_ij
+// (both cancel for close eigenvalues).  E_ij = numerator / (lambda_j - lambda_i)
+// is formed in FP32 (relative error ~2^-22): an E of size |E| then carries an
+// error ~|E| 2^-22, below 1e-15 once the second iteration's |E| ~ 1e-8.  The
+// Frobenius norms of the threshold are FP32 sums.
 __global__ void __launch_bounds__(256) k_oa_update(int n, const double *S_all, double *G_all, double *lam_all)
 {
     extern __shared__ double lam[];  // n
     __shared__ double red[32];
     const int b = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
     const size_t off = (size_t)b * n * n;
     const double *S = S_all + off;
     double *G = G_all + off;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = S[(size_t)i * n + i] / G[(size_t)i * n + i];
-    __syncthreads();
-    double sd = 0.0, rr = 0.0;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int i = e / n, j = e - i * n;
-        const double s = S[e] - (i == j ? lam[i] : 0.0);
-        const double r = (i == j ? 1.0 : 0.0) - G[e];
-        sd += s * s;
-        rr += r * r;
+    double dsd = 0.0, drr = 0.0;  // diagonal terms in FP64
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double sii = S[(size_t)i * n + i], gii = G[(size_t)i * n + i];
+        const double li = sii / gii;
+        lam[i] = li;
+        const double si = sii - li, ri = 1.0 - gii;
+        dsd = fma(si, si, dsd);
+        drr = fma(ri, ri, drr);
     }
-    sd = cta_sum64(sd, red);
-    rr = cta_sum64(rr, red);
+    __syncthreads();
+    float fsd = 0.0f, frr = 0.0f;
+    for (int i = warp; i < n; i += nwarp) {
+        const double *Si = S + (size_t)i * n, *Gi = G + (size_t)i * n;
+        for (int j = lane; j < n; j += 32) {
+            if (j == i) continue;
+            const float s = f32_trunc(Si[j]), r = f32_trunc(Gi[j]);
+            fsd = fmaf(s, s, fsd);
+            frr = fmaf(r, r, frr);
+        }
+    }
+    const double sd = cta_sum64(dsd + (double)fsd, red);
+    const double rr = cta_sum64(drr + (double)frr, red);
     // ||H||_2 estimated by the largest |lambda| (Frobenius norms bound the other two)
     double lmax = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) lmax = fmax(lmax, fabs(lam[i]));
     for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lmax;
+    if (lane == 0) red[warp] = lmax;
     __syncthreads();
     lmax = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lmax = fmax(lmax, red[w]);
-    const double delta = 2.0 * (sqrt(sd) + lmax * sqrt(rr));
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int i = e / n, j = e - i * n;
-        const double r = (i == j ? 1.0 : 0.0) - G[e];
-        double E;
-        if (i == j) {
-            E = 0.5 * r;
-        } else {
-            const double dl = lam[j] - lam[i];
-            E = (fabs(dl) > delta) ? (S[e] + lam[j] * r) / dl : 0.5 * r;
+    for (int w = 0; w < nwarp; ++w) lmax = fmax(lmax, red[w]);
+    const float delta = (float)(2.0 * (sqrt(sd) + lmax * sqrt(rr)));
+    for (int i = warp; i < n; i += nwarp) {
+        const double *Si = S + (size_t)i * n;
+        double *Gi = G + (size_t)i * n;
+        const double li = lam[i];
+        for (int j = lane; j < n; j += 32) {
+            const double g = Gi[j];
+            if (j == i) {
+                Gi[j] = 1.0 + 0.5 * (1.0 - g);
+                continue;
+            }
+            const float dl = f32_trunc(lam[j] - li);
+            float E;
+            if (fabsf(dl) > delta) E = f32_trunc(fma(lam[j], -g, Si[j])) * __frcp_rn(dl);  // R_ij = -G_ij
+            else E = -0.5f * f32_trunc(g);
+            Gi[j] = f64_of(E);
         }
-        G[e] = (i == j ? 1.0 : 0.0) + E;
     }
     double *lo = lam_all + (size_t)b * n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) lo[i] = lam[i];
