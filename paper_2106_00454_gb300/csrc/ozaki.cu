@@ -71,16 +71,39 @@ __device__ __forceinline__ __nv_bfloat16 oz_bf16_of_int(int d)
 // |d0| <= 129 -- all exact in BF16, every digit product below 2^15 in
 // magnitude, and the signs of the truncated lower products vary, so their
 // sum grows like sqrt(k) instead of k.
-__device__ __forceinline__ void oz_digits(double x, int e, __nv_bfloat16 *d, size_t stride)
+__device__ __forceinline__ void oz_digit_set(long long N, int *d)
 {
-    long long N = oz_scaled(x, e);
+    // the three low digits from the low 24 bits (unsigned), their carry into
+    // the high part, then the three high digits: 32-bit operations only
+    int t = (int)((unsigned)N & 0xFFFFFFu), hi = (int)(N >> 24);
 #pragma unroll
-    for (int p = kOzP - 1; p >= 1; --p) {
-        const int dig = (int)((N + 128) & 0xFF) - 128;
-        d[(size_t)p * stride] = oz_bf16_of_int(dig);
-        N = (N - dig) >> 8;  // exact: N - dig is a multiple of 256
+    for (int p = kOzP - 1; p >= 3; --p) {
+        d[p] = ((t + 128) & 0xFF) - 128;
+        t = (t - d[p]) >> 8;  // exact: t - d is a multiple of 256
     }
-    d[0] = oz_bf16_of_int((int)N);
+    hi += t;  // the carry, 0 or 1
+#pragma unroll
+    for (int p = 2; p >= 1; --p) {
+        d[p] = ((hi + 128) & 0xFF) - 128;
+        hi = (hi - d[p]) >> 8;
+    }
+    d[0] = hi;
+}
+
+// Two neighbouring elements (k, k + 1) of one vector: their digits as BF16
+// pairs, one 32-bit store per digit plane.
+__device__ __forceinline__ void oz_digits2(double x0, double x1, int e, __nv_bfloat16 *d, size_t stride)
+{
+    int a[kOzP], b[kOzP];
+    oz_digit_set(oz_scaled(x0, e), a);
+    oz_digit_set(oz_scaled(x1, e), b);
+#pragma unroll
+    for (int p = 0; p < kOzP; ++p) {
+        __nv_bfloat162 v;
+        v.x = oz_bf16_of_int(a[p]);
+        v.y = oz_bf16_of_int(b[p]);
+        *reinterpret_cast<__nv_bfloat162 *>(d + (size_t)p * stride) = v;
+    }
 }
 
 // Magnitude of x as an ordered integer (the IEEE-754 bits without the sign).
@@ -115,17 +138,18 @@ __global__ void __launch_bounds__(256) k_oz_split_rows(int n, int Kp, const doub
     const int ex = oz_exp_of(m);
     if (lane == 0) e_all[(size_t)b * n + v] = ex;
     __nv_bfloat16 *S = S_all + (size_t)b * kOzP * n * Kp + (size_t)v * Kp;
-    for (int k = lane; k < Kp; k += 32) oz_digits(k < n ? row[k] : 0.0, ex, S + k, (size_t)n * Kp);
+    for (int k = 2 * lane; k < Kp; k += 64)  // Kp is even: pairs (k, k + 1)
+        oz_digits2(k < n ? row[k] : 0.0, k + 1 < n ? row[k + 1] : 0.0, ex, S + k, (size_t)n * Kp);
 }
 
 // Column slices: S[b][p][v][k] = digit p of M[k][v], one CTA (32 x 8) per 32
-// columns: the column maxima first (reads along v), then 32 x 32 tiles
+// columns: the column maxima first (reads along v), then 64 x 32 tiles
 // transposed through shared memory so that both the reads (v fastest) and the
-// writes (k fastest) are coalesced.
+// writes (k fastest, two per thread) are coalesced.
 __global__ void __launch_bounds__(256) k_oz_split_cols(int n, int Kp, const double *M_all, int *e_all,
                                                        __nv_bfloat16 *S_all)
 {
-    __shared__ double tile[32][33];
+    __shared__ double tile[64][33];
     __shared__ unsigned long long mcol[8][32];
     __shared__ int ecol[32];
     const int b = blockIdx.y;
@@ -143,15 +167,15 @@ __global__ void __launch_bounds__(256) k_oz_split_cols(int n, int Kp, const doub
     }
     __syncthreads();
     __nv_bfloat16 *S = S_all + (size_t)b * kOzP * n * Kp;
-    for (int k0 = 0; k0 < Kp; k0 += 32) {
-        for (int r = ty; r < 32; r += 8) {
+    for (int k0 = 0; k0 < Kp; k0 += 64) {  // 64 k x 32 v per tile, read along v
+        for (int r = ty; r < 64; r += 8) {
             const int k = k0 + r, v = v0 + tx;
             tile[r][tx] = (k < n && v < n) ? M[(size_t)k * n + v] : 0.0;
         }
         __syncthreads();
-        for (int r = ty; r < 32; r += 8) {
-            const int v = v0 + r, k = k0 + tx;
-            if (v < n) oz_digits(tile[tx][r], ecol[r], S + (size_t)v * Kp + k, (size_t)n * Kp);
+        for (int r = ty; r < 32; r += 8) {  // column v0 + r, k pair k0 + 2 tx: written along k
+            const int v = v0 + r, k = k0 + 2 * tx;
+            if (v < n && k < Kp) oz_digits2(tile[2 * tx][r], tile[2 * tx + 1][r], ecol[r], S + (size_t)v * Kp + k, (size_t)n * Kp);
         }
         __syncthreads();
     }

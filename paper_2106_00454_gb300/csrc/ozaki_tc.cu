@@ -78,9 +78,16 @@ constexpr int kTcThreads = 32 * (kTcDrainWarps + 2);
 constexpr int kTcSmem = 1024 + kTcStages * kTcStageBytes + 128;  // alignment slack | ring | barriers
 constexpr long long kTcWaitCycles = 1ll << 31;
 
-// instruction descriptor: D F32, A and B BF16, both K-major, N = 64, M = 128
-constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                              ((uint32_t)(kTcM >> 4) << 24);
+// instruction descriptor: D F32, A and B BF16, both K-major, M = 128; N (bits
+// 17-22, N / 8) is set per tile: 64, or the last column tile's width rounded up
+// to 16, so a ragged edge costs at most 15 padded columns
+constexpr uint32_t kTcIdescBase = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ int tc_tile_n(int n, int col0)
+{
+    const int w = (n - col0 + 15) & ~15;
+    return w < kTcN ? w : kTcN;
+}
 
 // Shared-memory matrix descriptor of a K-major operand with 64-byte swizzle:
 // rows of 64 bytes, 8-row groups 512 bytes apart (stride offset); the leading
@@ -146,12 +153,13 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -274,6 +282,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             int stage = 0, blk = 0, committed = 0;
             uint32_t ph = 0;
             for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+                const TcTile tl = tc_tile(t, per_item, TC, sym);
+                const uint32_t idesc = kTcIdescBase | ((uint32_t)(tc_tile_n(n, tl.col0) >> 3) << 17);
                 for (int k0 = 0; k0 < Kp; k0 += kTcKC) {
                     const bool bfirst = (k0 % kTcKBlk) == 0;
                     const bool blast = ((k0 + kTcKC) % kTcKBlk) == 0 || k0 + kTcKC >= Kp;
@@ -293,9 +303,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             const int q = d - p;
 #pragma unroll
                             for (int kk = 0; kk < 2; ++kk) {  // K = 16: 32 bytes further into the swizzle span
+                                if (kk == 1 && k0 + 16 >= n) break;  // that half of the chunk is zero padding
                                 const uint64_t ad = a0 + (uint64_t)((p * kTcADigit + kk * 32) >> 4);
                                 const uint64_t bd = b0 + (uint64_t)((q * kTcBDigit + kk * 32) >> 4);
-                                tc_mma(tmem + (uint32_t)(d * kTcN), ad, bd, (bfirst && p == 0 && kk == 0) ? 0u : 1u);
+                                tc_mma(tmem + (uint32_t)(d * kTcN), ad, bd, idesc,
+                                       (bfirst && p == 0 && kk == 0) ? 0u : 1u);
                             }
                         }
                     tc_commit(empty_s + 8u * stage);
@@ -326,6 +338,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t tbase = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
         for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
             const TcTile tl = tc_tile(t, per_item, TC, sym);
+            const bool live = c0 < tc_tile_n(n, tl.col0);  // this warp's columns hold results
             long long acc[kTcDrainCols];
 #pragma unroll
             for (int j = 0; j < kTcDrainCols; ++j) acc[j] = 0;
@@ -337,7 +350,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 tc_fence_after();
 #pragma unroll
                 for (int d = 0; d < kOzDigits; d += 2) {  // two accumulators per round trip
-                    if (d > dmax) break;
+                    if (d > dmax || !live) break;
                     uint32_t r0[32], r1[32];
                     const bool two = d + 1 <= dmax;
                     tc_ld32(tbase + (uint32_t)(d * kTcN), r0);

@@ -137,6 +137,32 @@ __device__ __forceinline__ void record_error(int *err, int code)
     if (err) atomicCAS(err, 0, code);
 }
 
+// GB300 issues FP64 at 2 operations per clock per SM; conversions between
+// FP64 and FP32 go through the bit patterns with integer operations instead.
+// f32_trunc: x truncated to 24 significant bits (relative error < 2^-23),
+// zero below the FP32 normal range.
+__device__ __forceinline__ float f32_trunc(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int fe = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+    if (fe <= 0) return 0.0f;
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+}
+
+// The FP32 value as FP64 (exact; FP32 subnormals, below 1.2e-38, become zero).
+__device__ __forceinline__ double f64_of(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned fe = (u >> 23) & 0xFF;
+    if (fe == 0) return 0.0;
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(fe - 127 + 1023) << 52) |
+                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
 // Packed upper-triangle index (i <= j), column-major: element (i, j) at j(j+1)/2 + i.
 __device__ __forceinline__ int pk(int i, int j)
 {
