@@ -32,6 +32,7 @@ METRIC = "channel-solves/s and p50/p99 latency at <=1e-3 deg phase error vs plai
 UNIT = "channel-solves/s"
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (no measured FP64 peak in the driver's file)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA lanes x clock
+JACOBI_MIXED_DRAM_BYTES_1024 = 2.0e9  # k_jacobi_mixed, one step of the 1024-sample batched workload
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 
 
@@ -399,7 +400,7 @@ def run_wpcd(args, ws, rank, lrank):
             # Ozaki products: 6 balanced 8-bit digits per operand, the 21 digit pairs of
             # weight >= 2^-40 (p + q <= 5), each a 2 n^3 BF16 tensor-core product
             peak, src = measured_peak("bf16_tflops_sustained", 1700.0)
-            ref = {"kernel": "refinement phase (k_oz_gemm BF16 tensor-core digit products, digit splits, "
+            ref = {"kernel": "refinement phase (k_oz_gemm_tc tcgen05 BF16 digit products, digit splits, "
                              "FP64 update and Rayleigh kernels)", "bound": "tensor",
                    "flops_per_step": S * 9 * 21 * 2.0 * sum_n3,
                    "flops_note": "9 products (2 iterations x 4 + final H X) x 21 digit pairs x 2 n^3 BF16 flop",
@@ -418,6 +419,14 @@ def run_wpcd(args, ws, rank, lrank):
             r["unit"] = "TFLOP/s"
             r["frac"] = r["achieved"] / r["peak"]
             r["traffic"] = None
+    if prec == api.PREC_MIXED and jac["launches_per_step"] > 0 and wl.name.startswith("batched_"):
+        # DRAM bytes of the mixed Jacobi launches of one step of this workload, from an ncu
+        # capture at 1024 samples (dram__bytes_read.sum + dram__bytes_write.sum, all six buckets:
+        # 2.0e9 B), scaled by the channel-solves (the FP64 H and eigenvectors handed to the
+        # refinement, 16 n^2 B per solve, dominate), per launch like "achieved"
+        jac["traffic"] = JACOBI_MIXED_DRAM_BYTES_1024 * (S / 1024.0) / jac["launches_per_step"]
+        jac["traffic_note"] = "ncu capture at 1024 samples, scaled by channel-solves; bytes per launch"
+
     # the eigensolver launch is the single kernel with the largest share of the step
     dominant, secondary = jac, ref
     if rank == 0:
