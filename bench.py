@@ -402,13 +402,13 @@ def run_wpcd(args, ws, rank, lrank):
             peak, src = measured_peak("bf16_tflops_sustained", 1700.0)
             ref = {"kernel": "refinement phase (k_oz_gemm_tc tcgen05 BF16 digit products, digit splits, "
                              "FP64 update and Rayleigh kernels)", "bound": "tensor",
-                   "flops_per_step": S * 9 * 21 * 2.0 * sum_n3,
-                   "flops_note": "9 products (2 iterations x 4 + final H X) x 21 digit pairs x 2 n^3 BF16 flop",
+                   "flops_per_step": S * 8 * 21 * 2.0 * sum_n3,
+                   "flops_note": "8 products (2 iterations x 4) x 21 digit pairs x 2 n^3 BF16 flop",
                    "peak": peak, "peak_source": src}
         else:
             ref = {"kernel": "refinement phase (k_bgemm64 FP64 products and FP64 update kernels)", "bound": "alu",
-                   "flops_per_step": S * 18.0 * sum_n3,
-                   "flops_note": "two refinement iterations of 4 n^3 products plus the final H X: 18 n^3 flop",
+                   "flops_per_step": S * 16.0 * sum_n3,
+                   "flops_note": "two refinement iterations of four 2 n^3 products: 16 n^3 flop",
                    "peak": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64 rate"}
         ref.update({"ms_per_step": ref_ms / args.steps, "launches_per_step": ref_n / args.steps,
                     "timing": "CUDA events around the whole phase (several kernels per launch)"})

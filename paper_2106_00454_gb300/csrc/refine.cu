@@ -10,9 +10,10 @@
 //     E_ij = R_ij / 2                                         otherwise (and on the diagonal),
 //     delta = 2 (||S - diag(lambda)||_F + max|lambda| ||R||_F),
 //     X <- X (I + E),
-// which squares the eigenvector error.  After the last iteration every
-// eigenvalue is the FP64 Rayleigh quotient of its refined vector,
-// lambda_i = (X^T H X)_ii / (X^T X)_ii.  The FP64 H comes from the FP32 solve,
+// which squares the eigenvector error.  The eigenvalues are the last
+// iteration's FP64 Rayleigh quotients lambda_i = (X^T H X)_ii / (X^T X)_ii
+// (quadratically accurate in the eigenvector error; the last update changes
+// them below FP64 resolution).  The FP64 H comes from the FP32 solve,
 // which forms it before rounding.  The four products are batched FP64
 // GEMMs over every (sample, channel) item of one chunk of a size bucket; the
 // working matrices of item b sit contiguously at b * n^2 in scratch buffers,
@@ -161,22 +162,6 @@ __global__ void __launch_bounds__(256) k_oa_update(int n, const double *S_all, d
     for (int i = threadIdx.x; i < n; i += blockDim.x) lo[i] = lam[i];
 }
 
-// lambda_i = (X_i . Y_i) / (X_i . X_i) with Y = H X, columns i; one CTA per item.
-__global__ void __launch_bounds__(256) k_rayleigh(int n, const double *X_all, const double *Y_all, double *lam_all)
-{
-    const size_t off = (size_t)blockIdx.x * n * n;
-    const double *X = X_all + off, *Y = Y_all + off;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double num = 0.0, den = 0.0;
-        for (int r = 0; r < n; ++r) {
-            const double x = X[(size_t)r * n + i];
-            num = fma(x, Y[(size_t)r * n + i], num);
-            den = fma(x, x, den);
-        }
-        lam_all[(size_t)blockIdx.x * n + i] = num / den;
-    }
-}
-
 // Sort the eigenvalues ascending and write them, with the columns of X
 // permuted alike, into the eigen-buffer layout of their (sample, channel).
 __global__ void __launch_bounds__(256) k_sort_eig(const ChanDev *chans, const int *work, int nw, int sample0, int n,
@@ -280,15 +265,9 @@ cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_s
         x = xn;
         xn = t;
     }
-    if (iters > 0) {  // Y = H X for the Rayleigh quotients
-        if (engine == 0) {
-            CKR(launch_oz_split(n, items, true, x, sXc, eXc, st));
-            CKR(launch_oz_gemm_slices(n, items, sH, eH, sXc, eXc, xn, st, 6, false, err));
-        } else {
-            k_bgemm64<false><<<gg, 256, 0, st>>>(n, H, x, xn);
-        }
-        k_rayleigh<<<items, 256, 0, st>>>(n, x, xn, lam);
-    }
+    // lam holds the last iteration's Rayleigh quotients S_ii / G_ii of the vectors
+    // entering it; its update moves each vector by |E| ~ 1e-8 and a Rayleigh
+    // quotient by O(|E|^2 ||H||), below FP64 resolution, so no further H X is formed
 #undef CKR
     k_sort_eig<<<items, 256, sort_eig_smem(n), st>>>(chans, work, nw, sample0, n, lam, Xs, eps_all, X_all);
     return cudaGetLastError();
