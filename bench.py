@@ -401,7 +401,7 @@ def run_wpcd(args, ws, rank, lrank):
             # weight >= 2^-40 (p + q <= 5), each a 2 n^3 BF16 tensor-core product
             peak, src = measured_peak("bf16_tflops_sustained", 1700.0)
             ref = {"kernel": "refinement phase (k_oz_gemm_tc tcgen05 BF16 digit products, digit splits, "
-                             "FP64 update and Rayleigh kernels)", "bound": "tensor",
+                             "FP64 update and eigenpair sort)", "bound": "tensor",
                    "flops_per_step": S * 8 * 21 * 2.0 * sum_n3,
                    "flops_note": "8 products (2 iterations x 4) x 21 digit pairs x 2 n^3 BF16 flop",
                    "peak": peak, "peak_source": src}
