@@ -18,6 +18,15 @@ constexpr int kMixMaxThreads = 512;  // launch bound; the launch picks 64..512
 constexpr int kMixMaxSweeps = 40;
 constexpr size_t kMixSmemCap = 200 * 1024;
 constexpr float kRelTol = 1.1920929e-7f;  // 2^-23
+// Threshold Jacobi (Rutishauser) on large matrices: in the first sweeps a pair
+// rotates only if |a_pq| also exceeds kMixThreshFrac * off(A) / n, off(A) the
+// Frobenius norm of the strict upper triangle at the sweep's start.  Measured on
+// the 200 x 200 coupled blocks: the same number of sweeps with a third fewer
+// rotations; on smaller matrices it costs extra sweeps, so it is kept to
+// n >= kMixThreshN (where the eigenvector columns also live in global memory).
+constexpr int kMixThreshN = 160;
+constexpr int kMixThreshSweeps = 2;
+constexpr float kMixThreshFrac = 0.1f;
 
 __host__ __device__ inline int mpad(int n) { return (n + 1) & ~1; }
 __host__ __device__ inline int mldc(int n) { return (n + 3) & ~3; }  // column stride of C: float4 rows
@@ -137,6 +146,23 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
     while (sweeps < kMixMaxSweeps) {
         if (tid == 0) flags[0] = 0;
         __syncthreads();
+        float thr = 0.0f;
+        if (n >= kMixThreshN && sweeps < kMixThreshSweeps) {
+            float o2 = 0.0f;  // columns j and n - 1 - j per thread: balanced lengths
+            for (int j = tid; j < (n + 1) / 2; j += nt) {
+                const int jb = j * (j + 1) / 2, j2 = n - 1 - j, j2b = j2 * (j2 + 1) / 2;
+                for (int i = 0; i < j; ++i) o2 = fmaf(A[jb + i], A[jb + i], o2);
+                if (j2 != j)
+                    for (int i = 0; i < j2; ++i) o2 = fmaf(A[j2b + i], A[j2b + i], o2);
+            }
+            for (int o = 16; o > 0; o >>= 1) o2 += __shfl_xor_sync(0xffffffffu, o2, o);
+            if (lane == 0) dpp[tid >> 5] = o2;  // dpp is free until this sweep's first round
+            __syncthreads();
+            float tot = 0.0f;
+            for (int w = 0; w < (nt >> 5); ++w) tot += dpp[w];
+            thr = kMixThreshFrac * sqrtf(tot) / (float)n;
+            __syncthreads();
+        }
         ++sweeps;
         for (int r = 0; r < M; ++r) {
             const int nx3 = g3 == 2 ? 0 : g3 + 1;
@@ -147,7 +173,7 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
                 const int pb = p * (p + 1) / 2, qb = q * (q + 1) / 2;
                 float c = 1.0f, s = 0.0f, app = A[pb + p], aqq = A[qb + q];
                 const float apq = A[qb + p];
-                if (fabsf(apq) > kRelTol * sqrtf(fabsf(app) * fabsf(aqq))) {
+                if (fabsf(apq) > kRelTol * sqrtf(fabsf(app) * fabsf(aqq)) && fabsf(apq) > thr) {
                     const float tau = (aqq - app) / (2.0f * apq);
                     float t;
                     if (fabsf(tau) > 1e18f) t = 0.5f / tau;
@@ -214,7 +240,7 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
             }
             g3 = nx3;
         }
-        if (flags[0] == 0) {
+        if (flags[0] == 0 && thr == 0.0f) {  // a thresholded sweep proves nothing
             converged = true;
             break;
         }
