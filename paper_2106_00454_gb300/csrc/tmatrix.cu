@@ -74,18 +74,6 @@ cudaError_t launch_plan(const ChanDev *chans_dev, int n_ch, int maxN, const doub
 
 __device__ __forceinline__ double xlogabs(double d) { return d == 0.0 ? 0.0 : d * log(fabs(d)); }
 
-// Warp sum of v[0..NV); lane 0 writes it to red[warp * 6 + k].
-template <int NV>
-__device__ __forceinline__ void warp_sum_to(double *v, double *red /* [32][6] */)
-{
-#pragma unroll
-    for (int k = 0; k < NV; ++k)
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) red[(threadIdx.x >> 5) * 6 + k] = v[k];
-}
-
 // ---------------------------------------------------------------------------------------------
 // On-shell T.  One CTA per (sample, channel).
 //  - SWP boundaries (Eq. "pseudostate wave packet boundaries"): the positive
@@ -130,7 +118,7 @@ __global__ void __launch_bounds__(kTThreads) k_tmat(const ChanDev *chans, int n_
     const ChanDev ch = chans[c];
     const int n = ch.n, N = ch.N, K = ch.K;
     const int tid = threadIdx.x, nt = blockDim.x;
-    if ((size_t)dyn_smem_bytes() < tbin_smem_doubles(n) * sizeof(double)) {  // launch/layout mismatch
+    if ((size_t)dyn_smem_bytes() < tbin_smem_doubles(n) * sizeof(double) || nt != kTThreads) {  // launch/layout mismatch
         if (tid == 0) record_error(err, kDevBadSize);
         return;
     }
@@ -145,8 +133,9 @@ __global__ void __launch_bounds__(kTThreads) k_tmat(const ChanDev *chans, int n_
     double *XB = XA + n + 4;        // n+4  X(E_{i+1}, B)
     double *vrow = XB + n + 4;      // K x n
     double *R = vrow + 2 * n;       // K x n
-    double *red = R + 2 * n;        // 6 x 32
-    double *vd = red + 6 * 32;      // K x K diagonal V entries
+    double *red = R + 2 * n;        // 8   the six T sums
+    double *rs = red + 8;           // 6 x kTThreads  per-thread terms of the six sums
+    double *vd = rs + 6 * kTThreads;  // K x K diagonal V entries
     __shared__ int s_nb, s_bad;
 
     const double *eg = eps_all + ch.eps_off + (size_t)smp * n;
@@ -344,21 +333,26 @@ __global__ void __launch_bounds__(kTThreads) k_tmat(const ChanDev *chans, int n_
                 }
             }
         }
-        // warp sums of the warps that hold states; thread 0 adds them up
-        const int nwa = min((int)(nt >> 5), (n + 31) >> 5);
-        if ((tid >> 5) < nwa) {
-            if (K == 2) warp_sum_to<6>(acc, red);
-            else warp_sum_to<2>(acc, red);
+        // the six sums over the CTA: every thread's terms go to shared memory and
+        // warp k adds up sum k (nt/32 loads and a 5-step butterfly per thread), so
+        // the FP64 adds are ~nt per sum instead of a 6-value butterfly in every warp
+        const int nv = K == 2 ? 6 : 2;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < nv) rs[k * kTThreads + tid] = acc[k];
+        __syncthreads();
+        if ((tid >> 5) < nv) {
+            const int k = tid >> 5, ln = tid & 31;
+            double t = 0.0;
+            for (int j = ln; j < nt; j += 32) t += rs[k * kTThreads + j];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (ln == 0) red[k] = t;
         }
         __syncthreads();
         prev = i;
         if (tid == 0) {
-            for (int k = 0; k < 6; ++k) {
-                double t = 0.0;
-                if (K == 2 || k < 2)
-                    for (int w = 0; w < nwa; ++w) t += red[w * 6 + k];
-                acc[k] = t;
-            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc[k] = (k < nv) ? red[k] : 0.0;
             const double q = MODE == 2 ? p : 0.5 * (ch.kb[i] + ch.kb[i + 1]);
             const double Ni = ch.wp_kind == 0 ? (ch.kb[i + 1] - ch.kb[i])
                                               : (ch.kb[i + 1] * ch.kb[i + 1] - ch.kb[i] * ch.kb[i]) / (2.0 * kMu);

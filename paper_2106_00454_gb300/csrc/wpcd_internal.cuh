@@ -128,8 +128,9 @@ __device__ __forceinline__ void phases_of_T(int K, double q, const double *T, do
 __host__ __device__ inline size_t tbin_smem_doubles(int n)  // n = K * N of the channel
 {
     // eps n, branch members 2n, branch boundaries 2(n+1), lo/hi/inverse widths 3n, X(E, B) at the two
-    // bin edges 2(n+4), V rows 2n, R 2n, reduction 6 x 32, diagonal V entries 4
-    return (size_t)14 * n + 2 + 8 + 6 * 32 + 4;
+    // bin edges 2(n+4), V rows 2n, R 2n, the six sums 8 and their per-thread terms 6 x 256 (the T
+    // kernel's CTA size), diagonal V entries 4
+    return (size_t)14 * n + 2 + 8 + 8 + 6 * 256 + 4;
 }
 
 __device__ __forceinline__ void record_error(int *err, int code)
