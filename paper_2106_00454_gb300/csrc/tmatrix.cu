@@ -110,7 +110,7 @@ __device__ __forceinline__ double xlogabs(double d) { return d == 0.0 ? 0.0 : d 
 // [S][n_ch][stride = maxN][bin], mode 2 at [S][n_ch][stride = n_E][energy].
 // ---------------------------------------------------------------------------------------------
 template <bool VCID, int MODE>
-__global__ void __launch_bounds__(kTThreads) k_tmat(const ChanDev *chans, int n_ch, int n_terms, const double *coeffs,
+__global__ void __launch_bounds__(kTThreads, 5) k_tmat(const ChanDev *chans, int n_ch, int n_terms, const double *coeffs,
                                                     const double *eps_all, const double *C_all, PlanDev plan,
                                                     int n_E, int stride, double *tout, double *phout, int *err)
 {
@@ -136,6 +136,10 @@ __global__ void __launch_bounds__(kTThreads) k_tmat(const ChanDev *chans, int n_
     double *red = R + 2 * n;        // 8   the six T sums
     double *rs = red + 8;           // 6 x kTThreads  per-thread terms of the six sums
     double *vd = rs + 6 * kTThreads;  // K x K diagonal V entries
+    // averaged modes, per needed bin (the plan's list order): its edges, 1/dE and the
+    // continuum factor f^2 / (N_i q^2), formed once per item instead of per thread and bin
+    double *binA = vd + 4, *binB = binA + N, *binI = binB + N, *binF = binI + N;
+    int *bini = reinterpret_cast<int *>(binF + N);
     __shared__ int s_nb, s_bad;
 
     const double *eg = eps_all + ch.eps_off + (size_t)smp * n;
@@ -204,6 +208,30 @@ __global__ void __launch_bounds__(kTThreads) k_tmat(const ChanDev *chans, int n_
     }
     __syncthreads();
 
+    if (MODE != 2) {
+        for (int ii = tid; ii < cnt; ii += nt) {
+            const int i = plan.list[pc * stride + ii];
+            double a, b;
+            if (MODE == 1) {
+                a = Bb[i];
+                b = Bb[i + 1];
+            } else {
+                a = ch.kb[i] * ch.kb[i] / (2.0 * kMu);
+                b = ch.kb[i + 1] * ch.kb[i + 1] / (2.0 * kMu);
+            }
+            const double q = 0.5 * (ch.kb[i] + ch.kb[i + 1]);
+            const double Ni = ch.wp_kind == 0 ? (ch.kb[i + 1] - ch.kb[i])
+                                              : (ch.kb[i + 1] * ch.kb[i + 1] - ch.kb[i] * ch.kb[i]) / (2.0 * kMu);
+            const double f2 = ch.wp_kind == 0 ? 1.0 : q / kMu;
+            bini[ii] = i;
+            binA[ii] = a;
+            binB[ii] = b;
+            binI[ii] = 1.0 / (b - a);
+            binF[ii] = f2 / (Ni * q * q);
+        }
+        __syncthreads();
+    }
+
     const int dstride = (K == 2) ? (n >> 1) + 2 : n + 1;  // boundary slots per branch (K * dstride <= n + 4)
     int prev = -2;                                          // bin whose upper-edge X values sit in XB
     for (int ii = 0; ii < cnt; ++ii) {
@@ -214,14 +242,9 @@ __global__ void __launch_bounds__(kTThreads) k_tmat(const ChanDev *chans, int n_
             p = plan.pE[(size_t)ps * n_E + ii];
             E = p * p / (2.0 * kMu);
         } else {
-            i = plan.list[pc * stride + ii];
-            if (MODE == 1) {
-                Ea = Bb[i];
-                Ebn = Bb[i + 1];
-            } else {
-                Ea = ch.kb[i] * ch.kb[i] / (2.0 * kMu);
-                Ebn = ch.kb[i + 1] * ch.kb[i + 1] / (2.0 * kMu);
-            }
+            i = bini[ii];
+            Ea = binA[ii];
+            Ebn = binB[ii];
         }
         // this bin's eigenvector rows, first element per thread issued early so
         // that the load overlaps the logarithms below
@@ -230,6 +253,18 @@ __global__ void __launch_bounds__(kTThreads) k_tmat(const ChanDev *chans, int n_
         if (VCID && tid < n) {
             c0pre = C0[tid];
             if (K == 2) c1pre = C1[tid];
+        }
+        // the diagonal entries V_(a,i),(b,i) of V = V0 + sum_t c_t V_t: warp w < K^2
+        // forms entry w, lane l its terms l, l + 32, ... (loads in flight during the
+        // logarithms below, summed with a butterfly after them)
+        double vterm = 0.0;
+        if (VCID && (tid >> 5) < K * K) {
+            const int w = tid >> 5, a = w / K, bb = w - a * K;
+            const size_t off = (size_t)(a * N + i) * n + bb * N + i;
+            for (int t = tid & 31; t < n_terms; t += 32) {
+                const double v = ch.V[(size_t)t * n * n + off];
+                vterm += t == 0 ? v : cf[t - 1] * v;
+            }
         }
         if (MODE != 2) {
             const bool reuse = (i == prev + 1);
@@ -251,13 +286,9 @@ __global__ void __launch_bounds__(kTThreads) k_tmat(const ChanDev *chans, int n_
             }
         }
         if (VCID) {
-            // the diagonal entries V_(a,i),(b,i) of V = V0 + sum_a c_a V_a
-            if (tid < K * K) {
-                const int a = tid / K, bb = tid - a * K;
-                const size_t off = (size_t)(a * N + i) * n + bb * N + i;
-                double v = ch.V[off];
-                for (int t = 1; t < n_terms; ++t) v = fma(cf[t - 1], ch.V[(size_t)t * n * n + off], v);
-                vd[tid] = v;
+            if ((tid >> 5) < K * K) {  // warp-uniform
+                for (int o = 16; o > 0; o >>= 1) vterm += __shfl_xor_sync(0xffffffffu, vterm, o);
+                if ((tid & 31) == 0) vd[tid >> 5] = vterm;
             }
         } else {
             // rows (a, i) of V, then R = V_rows C
@@ -289,7 +320,7 @@ __global__ void __launch_bounds__(kTThreads) k_tmat(const ChanDev *chans, int n_
                 if (K == 2) { v01 = vrow[N + i]; v10 = vrow[n + i]; v11 = vrow[n + N + i]; }
             }
         }
-        const double idE = MODE == 2 ? 0.0 : 1.0 / (Ebn - Ea);
+        const double idE = MODE == 2 ? 0.0 : binI[ii];
         const double h0i = VCID ? ch.h0[i] : 0.0;
         double acc[6] = {0, 0, 0, 0, 0, 0};  // (00 re, im), (01 re, im), (11 re, im)
         for (int s = tid; s < n; s += nt) {
@@ -353,11 +384,15 @@ __global__ void __launch_bounds__(kTThreads) k_tmat(const ChanDev *chans, int n_
         if (tid == 0) {
 #pragma unroll
             for (int k = 0; k < 6; ++k) acc[k] = (k < nv) ? red[k] : 0.0;
-            const double q = MODE == 2 ? p : 0.5 * (ch.kb[i] + ch.kb[i + 1]);
-            const double Ni = ch.wp_kind == 0 ? (ch.kb[i + 1] - ch.kb[i])
-                                              : (ch.kb[i + 1] * ch.kb[i + 1] - ch.kb[i] * ch.kb[i]) / (2.0 * kMu);
-            const double f2 = ch.wp_kind == 0 ? 1.0 : q / kMu;
-            const double fac = f2 / (Ni * q * q);
+            double fac;
+            if (MODE == 2) {
+                const double Ni = ch.wp_kind == 0 ? (ch.kb[i + 1] - ch.kb[i])
+                                                  : (ch.kb[i + 1] * ch.kb[i + 1] - ch.kb[i] * ch.kb[i]) / (2.0 * kMu);
+                const double f2 = ch.wp_kind == 0 ? 1.0 : p / kMu;
+                fac = f2 / (Ni * p * p);
+            } else {
+                fac = binF[ii];
+            }
             double T[8];  // complex 2x2, row-major
             T[0] = fac * (v00 + acc[0]);
             T[1] = fac * acc[1];

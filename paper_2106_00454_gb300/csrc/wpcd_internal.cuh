@@ -129,8 +129,8 @@ __host__ __device__ inline size_t tbin_smem_doubles(int n)  // n = K * N of the 
 {
     // eps n, branch members 2n, branch boundaries 2(n+1), lo/hi/inverse widths 3n, X(E, B) at the two
     // bin edges 2(n+4), V rows 2n, R 2n, the six sums 8 and their per-thread terms 6 x 256 (the T
-    // kernel's CTA size), diagonal V entries 4
-    return (size_t)14 * n + 2 + 8 + 8 + 6 * 256 + 4;
+    // kernel's CTA size), diagonal V entries 4, per needed bin (<= n) edges, 1/dE, factor and index 4.5n
+    return (size_t)14 * n + 2 + 8 + 8 + 6 * 256 + 4 + (size_t)5 * n;
 }
 
 __device__ __forceinline__ void record_error(int *err, int code)
