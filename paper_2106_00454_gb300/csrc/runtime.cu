@@ -119,8 +119,6 @@ struct wpcd_ctx {
     // Gauss-Legendre rules cached on the device, keyed by order
     std::map<int, std::pair<double *, double *>> gl;
     Exec main;  // executor of the synchronous API (the caller's stream)
-    void *pin_in = nullptr, *pin_out = nullptr;
-    size_t pin_in_n = 0, pin_out_n = 0;
     struct Server *server = nullptr;
     // tracing: kernels launched, and (when enabled) CUDA events around each launch
     std::atomic<unsigned long long> launches{0};
@@ -594,8 +592,6 @@ void wpcd_destroy(wpcd_ctx *c)
     }
     Exec &M = c->main;
     for (auto *b : {&M.ws_plan_i, &M.ws_plan_d, &M.ws_tbin, &M.ws_phbin, &M.ws_in, &M.ws_out, &M.ws_ref}) dfree(c, b->p);
-    if (c->pin_in) cudaFreeHost(c->pin_in);
-    if (c->pin_out) cudaFreeHost(c->pin_out);
     dfree(c, c->err_dev);
     delete c;
 }
@@ -991,40 +987,32 @@ wpcd_status wpcd_solve_host(wpcd_ctx *c, int vset_id, const double *coeffs_h, in
     const size_t nt = t_h ? (size_t)S * n_ch * n_E * 8 : 0, nd = delta_h ? (size_t)S * n_ch * n_E * 3 : 0,
                  ns = sigma_h ? (size_t)S * n_E : 0;
     const size_t out_bytes = (nt + nd + ns) * sizeof(double);
-    double *din, *dout, *hin, *hout;
+    double *din, *dout;
     {
         std::lock_guard<std::mutex> lk(c->mu);
         CK(cudaSetDevice(c->device));
         if ((st = ws_reserve(c, c->main, c->main.ws_in, in_bytes)) || (st = ws_reserve(c, c->main, c->main.ws_out, out_bytes))) return st;
-        if (c->pin_in_n < in_bytes) {
-            if (c->pin_in) cudaFreeHost(c->pin_in);
-            CK(cudaMallocHost(&c->pin_in, in_bytes));
-            c->pin_in_n = in_bytes;
-        }
-        if (c->pin_out_n < out_bytes) {
-            if (c->pin_out) cudaFreeHost(c->pin_out);
-            CK(cudaMallocHost(&c->pin_out, out_bytes));
-            c->pin_out_n = out_bytes;
-        }
         din = static_cast<double *>(c->main.ws_in.p);
         dout = static_cast<double *>(c->main.ws_out.p);
-        hin = static_cast<double *>(c->pin_in);
-        hout = static_cast<double *>(c->pin_out);
-        if (nc) memcpy(hin, coeffs_h, nc * sizeof(double));
-        memcpy(hin + nc, e_lab_h, n_E * sizeof(double));
-        CK(cudaMemcpyAsync(din, hin, in_bytes, cudaMemcpyHostToDevice, c->main.stream));
+        // straight from and into the caller's buffers: a host-to-device copy from
+        // pageable memory returns once the source has been consumed, and the
+        // device-to-host copies below are waited for before this call returns
+        if (nc) CK(cudaMemcpyAsync(din, coeffs_h, nc * sizeof(double), cudaMemcpyHostToDevice, c->main.stream));
+        CK(cudaMemcpyAsync(din + nc, e_lab_h, n_E * sizeof(double), cudaMemcpyHostToDevice, c->main.stream));
     }
     st = wpcd_solve(c, vset_id, nc ? din : nullptr, S, din + nc, n_E, prec, res, t_h ? dout : nullptr,
                     delta_h ? dout + nt : nullptr, sigma_h ? dout + nt + nd : nullptr);
     if (st) return st;
     {
         std::lock_guard<std::mutex> lk(c->mu);
-        if (out_bytes) CK(cudaMemcpyAsync(hout, dout, out_bytes, cudaMemcpyDeviceToHost, c->main.stream));
+        if (t_h) CK(cudaMemcpyAsync(t_h, dout, nt * sizeof(double), cudaMemcpyDeviceToHost, c->main.stream));
+        if (delta_h)
+            CK(cudaMemcpyAsync(delta_h, dout + nt, nd * sizeof(double), cudaMemcpyDeviceToHost, c->main.stream));
+        if (sigma_h)
+            CK(cudaMemcpyAsync(sigma_h, dout + nt + nd, ns * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->main.stream));
     }
     st = wpcd_sync(c);
-    if (t_h) memcpy(t_h, hout, nt * sizeof(double));
-    if (delta_h) memcpy(delta_h, hout + nt, nd * sizeof(double));
-    if (sigma_h) memcpy(sigma_h, hout + nt + nd, ns * sizeof(double));
     return st;
 }
 
