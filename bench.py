@@ -32,7 +32,7 @@ METRIC = "channel-solves/s and p50/p99 latency at <=1e-3 deg phase error vs plai
 UNIT = "channel-solves/s"
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (no measured FP64 peak in the driver's file)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA lanes x clock
-JACOBI_MIXED_DRAM_BYTES_1024 = 2.0e9  # k_jacobi_mixed, one step of the 1024-sample batched workload
+JACOBI_MIXED_DRAM_BYTES_1024 = 2.06e9  # k_jacobi_mixed, one step of the 1024-sample batched workload
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 
 
@@ -422,7 +422,7 @@ def run_wpcd(args, ws, rank, lrank):
     if prec == api.PREC_MIXED and jac["launches_per_step"] > 0 and wl.name.startswith("batched_"):
         # DRAM bytes of the mixed Jacobi launches of one step of this workload, from an ncu
         # capture at 1024 samples (dram__bytes_read.sum + dram__bytes_write.sum, all six buckets:
-        # 2.0e9 B), scaled by the channel-solves (the FP64 H and eigenvectors handed to the
+        # 2.06e9 B), scaled by the channel-solves (the FP64 H and eigenvectors handed to the
         # refinement, 16 n^2 B per solve, dominate), per launch like "achieved"
         jac["traffic"] = JACOBI_MIXED_DRAM_BYTES_1024 * (S / 1024.0) / jac["launches_per_step"]
         jac["traffic_note"] = "ncu capture at 1024 samples, scaled by channel-solves; bytes per launch"
