@@ -97,10 +97,13 @@ enum {
  * FP64 (FP64 CUDA cores).  WPCD_OPT_AUTOTUNE (1 = on, the default): on the first
  * batched eigensolve of each (matrix size, precision) the context times CTA
  * sizes 64/128/256/512 on about two full waves of that bucket and keeps the
- * fastest (wpcd_tuning reports the choices); 0 = fixed 256 threads. */
+ * fastest (wpcd_tuning reports the choices); 0 = fixed 256 threads.
+ * WPCD_OPT_GRAPH (1 = on, the default): batched wpcd_solve / wpcd_solve_host
+ * calls are replayed from CUDA graphs (see wpcd_solve); 0 = every call
+ * launches its kernels one by one. */
 enum { WPCD_EXEC_BATCHED = 0, WPCD_EXEC_PLAIN = 1 };
 enum { WPCD_REFINE_TENSOR = 0, WPCD_REFINE_FP64 = 1 };
-enum { WPCD_OPT_EXEC = 1, WPCD_OPT_REFINE = 2, WPCD_OPT_AUTOTUNE = 3 };
+enum { WPCD_OPT_EXEC = 1, WPCD_OPT_REFINE = 2, WPCD_OPT_AUTOTUNE = 3, WPCD_OPT_GRAPH = 4 };
 
 /* ---- context --------------------------------------------------------------------------------- */
 
@@ -221,7 +224,16 @@ wpcd_status wpcd_observables_res(wpcd_ctx *ctx, int eig_id, const double *e_lab_
 
 /* ---- the whole hot path in one call --------------------------------------------------------------
  * wpcd_diag + wpcd_tmatrix + wpcd_observables for one batch, with the
- * eigenpairs kept in context scratch instead of a handle.  Outputs may be NULL. */
+ * eigenpairs kept in context scratch instead of a handle.  Outputs may be NULL.
+ * CUDA graphs (WPCD_OPT_GRAPH on, batched execution, profiling off): the first
+ * call with a given (vset, pointers, sizes, precision, resolvent) launches its
+ * kernels one by one (and autotunes and sizes the workspaces); the second
+ * captures the same launch sequence into a graph on a private stream; that and
+ * every later identical call launch the graph on the context stream.  A graph
+ * is dropped when anything it baked in may have changed (a workspace grew or
+ * was reallocated, an option or the tuning table changed); the next identical
+ * call then runs one by one again.  Results are the same either way: the graph
+ * holds the same kernels with the same arguments. */
 wpcd_status wpcd_solve(wpcd_ctx *ctx, int vset_id, const double *coeffs_dev, int n_samples,
                        const double *e_lab_dev, int n_E, wpcd_precision prec, wpcd_resolvent res,
                        double *t_out_dev, double *delta_dev, double *sigma_dev);
@@ -329,8 +341,15 @@ wpcd_status wpcd_batched_dgemm(wpcd_ctx *ctx, int n, int items, int trans_a, con
  * 512 threads; negative = not run).  Returns the number of entries. */
 int wpcd_tuning(wpcd_ctx *ctx, int max_entries, int *n_out, int *prec_out, int *threads_out, float *ms_out);
 
-/* Number of kernels this context has launched since creation (host count). */
+/* Number of kernels this context has launched since creation (host count;
+ * a graph launch counts the kernels it holds). */
 unsigned long long wpcd_kernel_launches(const wpcd_ctx *ctx);
+
+/* CUDA-graph use of wpcd_solve: graphs captured and graph launches since the
+ * context was created, and graphs currently cached.  Either pointer may be NULL.
+ * Errors: WPCD_ERR_ARG (null context). */
+wpcd_status wpcd_graph_stats(wpcd_ctx *ctx, unsigned long long *captures, unsigned long long *replays,
+                             int *cached);
 
 /* Turn per-launch CUDA-event timing on (1) or off (0); either call clears the
  * accumulated totals.  Timing adds two events per launch on the context stream. */

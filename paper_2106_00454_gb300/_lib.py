@@ -20,7 +20,7 @@ EXPORTED = [
     "wpcd_release", "wpcd_kernel_launches", "wpcd_profile", "wpcd_profile_read",
     "wpcd_channel_solve_noalloc", "wpcd_serve_start", "wpcd_serve_stop", "wpcd_submit", "wpcd_poll", "wpcd_wait",
     "wpcd_release_result", "wpcd_serve_stats", "wpcd_batched_dgemm", "wpcd_tuning", "wpcd_mi_prepare",
-    "wpcd_mi_solve", "wpcd_saclay",
+    "wpcd_mi_solve", "wpcd_saclay", "wpcd_graph_stats",
 ]
 
 
@@ -85,6 +85,8 @@ _SIG = {
     "wpcd_tuning": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "wpcd_serve_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong),
                               ctypes.POINTER(ctypes.c_ulonglong)]),
+    "wpcd_graph_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong),
+                              ctypes.POINTER(ctypes.c_int)]),
 }
 
 _lock = threading.Lock()

@@ -19,7 +19,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 AVG_FREE_BIN, AVG_SWP_INDEX, POINT = 0, 1, 2  # resolvent (wpcd_resolvent)
 EXEC_BATCHED, EXEC_PLAIN = 0, 1
 REFINE_TENSOR, REFINE_FP64 = 0, 1
-OPT_EXEC, OPT_REFINE, OPT_AUTOTUNE = 1, 2, 3
+OPT_EXEC, OPT_REFINE, OPT_AUTOTUNE, OPT_GRAPH = 1, 2, 3, 4
 
 
 class WpcdError(RuntimeError):
@@ -87,6 +87,15 @@ class Context:
 
     def set_autotune(self, on: bool):
         _ck(self.lib.wpcd_set_option(self.h, OPT_AUTOTUNE, 1 if on else 0), "wpcd_set_option")
+
+    def set_graphs(self, on: bool):
+        _ck(self.lib.wpcd_set_option(self.h, OPT_GRAPH, 1 if on else 0), "wpcd_set_option")
+
+    def graph_stats(self) -> dict:
+        cap, rep, cached = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0), ctypes.c_int(0)
+        _ck(self.lib.wpcd_graph_stats(self.h, ctypes.byref(cap), ctypes.byref(rep), ctypes.byref(cached)),
+            "wpcd_graph_stats")
+        return {"captures": cap.value, "replays": rep.value, "cached": cached.value}
 
     def tuning(self) -> list:
         m = 64

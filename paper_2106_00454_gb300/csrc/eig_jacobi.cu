@@ -280,11 +280,11 @@ cudaError_t launch_jacobi_f64(const ChanDev *chans_dev, const int *work_ch_dev, 
     dim3 grid((unsigned)(n_samples * n_work_ch));
     if (cs) {
         cudaFuncSetAttribute(k_jacobi_f64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_jacobi_f64<true><<<grid, threads, smem, st>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
+        k_jacobi_f64<true><<<grid, threads, smem, counted(st)>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
                                                             coeffs, eps_all, C_all, status_all, n_ch_total, err);
     } else {
         cudaFuncSetAttribute(k_jacobi_f64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_jacobi_f64<false><<<grid, threads, smem, st>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
+        k_jacobi_f64<false><<<grid, threads, smem, counted(st)>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
                                                              coeffs, eps_all, C_all, status_all, n_ch_total, err);
     }
     return cudaGetLastError();

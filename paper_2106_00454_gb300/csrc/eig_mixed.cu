@@ -272,11 +272,11 @@ cudaError_t launch_jacobi_mixed(const ChanDev *chans_dev, const int *work_ch_dev
     dim3 grid((unsigned)(n_samples * n_work_ch));
     if (cs) {
         cudaFuncSetAttribute(k_jacobi_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_jacobi_mixed<true><<<grid, threads, smem, st>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
+        k_jacobi_mixed<true><<<grid, threads, smem, counted(st)>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
                                                               coeffs, lam_s, X_s, Cf_s, H_s, status_all, n_ch_total, err);
     } else {
         cudaFuncSetAttribute(k_jacobi_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_jacobi_mixed<false><<<grid, threads, smem, st>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
+        k_jacobi_mixed<false><<<grid, threads, smem, counted(st)>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
                                                                coeffs, lam_s, X_s, Cf_s, H_s, status_all, n_ch_total, err);
     }
     return cudaGetLastError();

@@ -51,7 +51,7 @@ __global__ void k_gauss_legendre(int n, double *x, double *w)
 cudaError_t launch_gauss_legendre(int n, double *x, double *w, cudaStream_t st)
 {
     int m = (n + 1) / 2;
-    k_gauss_legendre<<<(m + 63) / 64, 64, 0, st>>>(n, x, w);
+    k_gauss_legendre<<<(m + 63) / 64, 64, 0, counted(st)>>>(n, x, w);
     return cudaGetLastError();
 }
 
@@ -96,7 +96,7 @@ cudaError_t launch_mesh(int N, int kind, double alpha, double t, double kmax, in
                         const double *glx, const double *glw, double *kb, double *kq, double *wq, double *h0,
                         cudaStream_t st)
 {
-    k_mesh<<<1, 256, (N + 1) * sizeof(double), st>>>(N, kind, alpha, t, kmax, Q, wp_kind, glx, glw, kb, kq, wq, h0);
+    k_mesh<<<1, 256, (N + 1) * sizeof(double), counted(st)>>>(N, kind, alpha, t, kmax, Q, wp_kind, glx, glw, kb, kq, wq, h0);
     return cudaGetLastError();
 }
 
@@ -194,7 +194,7 @@ cudaError_t launch_project_yukawa(const ChanDev *chans_dev, const int *group_dev
                                   cudaStream_t st)
 {
     int nblk = N * (N + 1) / 2;
-    k_project<WPCD_GEN_YUKAWA><<<nblk, proj_threads(Q), 0, st>>>(chans_dev, group_dev, n_group, N, Q, Lmax, gp_dev,
+    k_project<WPCD_GEN_YUKAWA><<<nblk, proj_threads(Q), 0, counted(st)>>>(chans_dev, group_dev, n_group, N, Q, Lmax, gp_dev,
                                                                  angx, angw, n_terms);
     return cudaGetLastError();
 }
@@ -204,7 +204,7 @@ cudaError_t launch_project_yamaguchi_gp(const ChanDev *chans_dev, const int *gro
                                         const double *gp_dev, cudaStream_t st)
 {
     int nblk = N * (N + 1) / 2;
-    k_project<WPCD_GEN_YAMAGUCHI><<<nblk, proj_threads(Q), 0, st>>>(chans_dev, group_dev, n_group, N, Q, 0, gp_dev,
+    k_project<WPCD_GEN_YAMAGUCHI><<<nblk, proj_threads(Q), 0, counted(st)>>>(chans_dev, group_dev, n_group, N, Q, 0, gp_dev,
                                                                     nullptr, nullptr, 1);
     return cudaGetLastError();
 }
@@ -245,7 +245,7 @@ cudaError_t launch_project_fine(const ChanDev *chans_dev, int c, const ChanDev &
                                 int n_terms, cudaStream_t st)
 {
     dim3 grid(ch_host.N, ch_host.N);
-    k_project_fine<<<grid, proj_threads(ch_host.Q), 0, st>>>(chans_dev, c, vfine, n_terms);
+    k_project_fine<<<grid, proj_threads(ch_host.Q), 0, counted(st)>>>(chans_dev, c, vfine, n_terms);
     return cudaGetLastError();
 }
 

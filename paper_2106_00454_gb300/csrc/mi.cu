@@ -44,7 +44,7 @@ __global__ void k_mi_grid(int NQ, double cmap, const double *glx, const double *
 cudaError_t launch_mi_grid(int NQ, double cmap, const double *glx, const double *glw, double *k, double *w,
                            cudaStream_t st)
 {
-    k_mi_grid<<<(NQ + 127) / 128, 128, 0, st>>>(NQ, cmap, glx, glw, k, w);
+    k_mi_grid<<<(NQ + 127) / 128, 128, 0, counted(st)>>>(NQ, cmap, glx, glw, k, w);
     return cudaGetLastError();
 }
 
@@ -140,10 +140,10 @@ cudaError_t launch_mi_pot(int gen, const MiChanDev *chans_dev, int n_ch, int NQ,
     const long long pairs = (long long)NQ * (NQ + 1) / 2;
     const unsigned grid = (unsigned)((pairs + 127) / 128);
     if (gen == WPCD_GEN_YUKAWA)
-        k_mi_pot_grid<WPCD_GEN_YUKAWA><<<grid, 128, 0, st>>>(chans_dev, n_ch, NQ, kg, Lmax, gp_dev, angx, angw,
+        k_mi_pot_grid<WPCD_GEN_YUKAWA><<<grid, 128, 0, counted(st)>>>(chans_dev, n_ch, NQ, kg, Lmax, gp_dev, angx, angw,
                                                              n_terms, Vg);
     else
-        k_mi_pot_grid<WPCD_GEN_YAMAGUCHI><<<grid, 128, 0, st>>>(chans_dev, n_ch, NQ, kg, 0, gp_dev, nullptr, nullptr,
+        k_mi_pot_grid<WPCD_GEN_YAMAGUCHI><<<grid, 128, 0, counted(st)>>>(chans_dev, n_ch, NQ, kg, 0, gp_dev, nullptr, nullptr,
                                                                 n_terms, Vg);
     return cudaGetLastError();
 }
@@ -154,10 +154,10 @@ cudaError_t launch_mi_onshell(int gen, const MiChanDev *chans_dev, int n_ch, int
 {
     const unsigned grid = (unsigned)((n_I * (NQ + 1) + 127) / 128);
     if (gen == WPCD_GEN_YUKAWA)
-        k_mi_pot_onshell<WPCD_GEN_YUKAWA><<<grid, 128, 0, st>>>(chans_dev, n_ch, NQ, kg, n_I, e_int, Lmax, gp_dev, angx,
+        k_mi_pot_onshell<WPCD_GEN_YUKAWA><<<grid, 128, 0, counted(st)>>>(chans_dev, n_ch, NQ, kg, n_I, e_int, Lmax, gp_dev, angx,
                                                                 angw, n_terms, Von);
     else
-        k_mi_pot_onshell<WPCD_GEN_YAMAGUCHI><<<grid, 128, 0, st>>>(chans_dev, n_ch, NQ, kg, n_I, e_int, 0, gp_dev,
+        k_mi_pot_onshell<WPCD_GEN_YAMAGUCHI><<<grid, 128, 0, counted(st)>>>(chans_dev, n_ch, NQ, kg, n_I, e_int, 0, gp_dev,
                                                                    nullptr, nullptr, n_terms, Von);
     return cudaGetLastError();
 }
@@ -514,7 +514,7 @@ cudaError_t launch_mi_solve(const MiChanDev *chans_dev, const int *work_dev, int
     const size_t smem = mi_smem(n, NQ + 1);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(k_mi_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_mi_solve<<<slots, kMiThreads, smem, st>>>(chans_dev, work_dev, n_work, n_ch_total, n_samples, NQ, kg, wg, n_terms,
+    k_mi_solve<<<slots, kMiThreads, smem, counted(st)>>>(chans_dev, work_dev, n_work, n_ch_total, n_samples, NQ, kg, wg, n_terms,
                                                 coeffs, Vg, Von, n_I, e_int, Vs, ph, k_out, status, err);
     return cudaGetLastError();
 }
@@ -589,7 +589,7 @@ cudaError_t launch_mi_observables(const MiChanDev *chans_dev, int n_ch, int n_sa
                                   cudaStream_t st)
 {
     const size_t total = (size_t)n_samples * n_E;
-    k_mi_observables<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(chans_dev, n_ch, n_samples, n_I, e_int, ph, n_E,
+    k_mi_observables<<<(unsigned)((total + 127) / 128), 128, 0, counted(st)>>>(chans_dev, n_ch, n_samples, n_I, e_int, ph, n_E,
                                                                        e_lab, delta, sigma);
     return cudaGetLastError();
 }

@@ -143,7 +143,7 @@ extern "C" wpcd_status wpcd_channel_solve_noalloc(int n_wp, int mesh_kind, doubl
     do {                                                           \
         if ((call) != cudaSuccess) return WPCD_ERR_CUDA;           \
     } while (0)
-    k_store_chan<<<1, 1, 0, st>>>(cd, chan, list);
+    k_store_chan<<<1, 1, 0, counted(st)>>>(cd, chan, list);
     CKN(cudaGetLastError());
     CKN(launch_gauss_legendre(Q, glx, glw, st));
     CKN(launch_mesh(N, mesh_kind, alpha_fm, t, kmax_fm, Q, wp_kind, glx, glw, kb, kq, wq, h0, st));

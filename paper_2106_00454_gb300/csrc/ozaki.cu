@@ -186,8 +186,8 @@ __global__ void __launch_bounds__(256) k_oz_split_cols(int n, int Kp, const doub
 cudaError_t launch_oz_split(int n, int items, bool cols, const double *M, __nv_bfloat16 *S, int *e, cudaStream_t st)
 {
     const int Kp = oz_kpad(n);
-    if (cols) k_oz_split_cols<<<dim3((n + 31) / 32, items), dim3(32, 8), 0, st>>>(n, Kp, M, e, S);
-    else k_oz_split_rows<<<dim3((n + 7) / 8, items), 256, 0, st>>>(n, Kp, M, e, S);
+    if (cols) k_oz_split_cols<<<dim3((n + 31) / 32, items), dim3(32, 8), 0, counted(st)>>>(n, Kp, M, e, S);
+    else k_oz_split_rows<<<dim3((n + 7) / 8, items), 256, 0, counted(st)>>>(n, Kp, M, e, S);
     return cudaGetLastError();
 }
 

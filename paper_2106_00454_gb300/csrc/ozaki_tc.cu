@@ -454,7 +454,7 @@ cudaError_t launch_oz_gemm_tc(int n, int items, const __nv_bfloat16 *sa, const i
     cudaError_t e = cudaFuncSetAttribute(k_oz_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (e != cudaSuccess) return e;
     const int grid = (int)(ntiles < sms ? ntiles : sms);
-    k_oz_gemm_tc<<<grid, kTcThreads, kTcSmem, st>>>(ma, mb, n, Kp, digits - 1, sym, per_item, TC, (int)ntiles, ea, eb,
+    k_oz_gemm_tc<<<grid, kTcThreads, kTcSmem, counted(st)>>>(ma, mb, n, Kp, digits - 1, sym, per_item, TC, (int)ntiles, ea, eb,
                                                     C, err);
     return cudaGetLastError();
 }

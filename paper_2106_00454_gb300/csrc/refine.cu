@@ -249,17 +249,17 @@ cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_s
             CKR(launch_oz_gemm_slices(n, items, sXc, eXc, sYc, eYc, W1, st, dg, true, err));  // S = X^T Y
             CKR(launch_oz_gemm_slices(n, items, sXc, eXc, sXc, eXc, W2, st, dg, true, err));  // G = X^T X
         } else {
-            k_bgemm64<false><<<gg, 256, 0, st>>>(n, H, x, xn);
-            k_bgemm64<true><<<gg, 256, 0, st>>>(n, x, xn, W1);
-            k_bgemm64<true><<<gg, 256, 0, st>>>(n, x, x, W2);
+            k_bgemm64<false><<<gg, 256, 0, counted(st)>>>(n, H, x, xn);
+            k_bgemm64<true><<<gg, 256, 0, counted(st)>>>(n, x, xn, W1);
+            k_bgemm64<true><<<gg, 256, 0, counted(st)>>>(n, x, x, W2);
         }
-        k_oa_update<<<items, 256, (size_t)n * 8, st>>>(n, W1, W2, lam);
+        k_oa_update<<<items, 256, (size_t)n * 8, counted(st)>>>(n, W1, W2, lam);
         if (engine == 0) {
             CKR(launch_oz_split(n, items, false, x, sXr, eXr, st));              // rows of X
             CKR(launch_oz_split(n, items, true, W2, sEc, eEc, st));              // columns of I + E
             CKR(launch_oz_gemm_slices(n, items, sXr, eXr, sEc, eEc, xn, st, dg, false, err)); // X (I + E)
         } else {
-            k_bgemm64<false><<<gg, 256, 0, st>>>(n, x, W2, xn);
+            k_bgemm64<false><<<gg, 256, 0, counted(st)>>>(n, x, W2, xn);
         }
         double *t = x;
         x = xn;
@@ -269,7 +269,7 @@ cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_s
     // entering it; its update moves each vector by |E| ~ 1e-8 and a Rayleigh
     // quotient by O(|E|^2 ||H||), below FP64 resolution, so no further H X is formed
 #undef CKR
-    k_sort_eig<<<items, 256, sort_eig_smem(n), st>>>(chans, work, nw, sample0, n, lam, Xs, eps_all, X_all);
+    k_sort_eig<<<items, 256, sort_eig_smem(n), counted(st)>>>(chans, work, nw, sample0, n, lam, Xs, eps_all, X_all);
     return cudaGetLastError();
 }
 
@@ -285,8 +285,8 @@ cudaError_t launch_batched_dgemm(int n, int items, bool ta, const double *A, con
     }
     const int tiles = (n + kBM - 1) / kBM;
     const dim3 gg(tiles, tiles, items);
-    if (ta) k_bgemm64<true><<<gg, 256, 0, st>>>(n, A, B, C);
-    else k_bgemm64<false><<<gg, 256, 0, st>>>(n, A, B, C);
+    if (ta) k_bgemm64<true><<<gg, 256, 0, counted(st)>>>(n, A, B, C);
+    else k_bgemm64<false><<<gg, 256, 0, counted(st)>>>(n, A, B, C);
     return cudaGetLastError();
 }
 

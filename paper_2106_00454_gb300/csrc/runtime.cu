@@ -3,6 +3,7 @@
 // Every numerical step runs in the kernels of the other translation units;
 // this file only allocates, validates, orders launches and copies.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <atomic>
 #include <chrono>
@@ -20,6 +21,7 @@
 
 namespace wpcd {
 size_t tbin_smem_bytes(int nmax);
+thread_local unsigned long long g_thread_kernels = 0;
 }
 
 using namespace wpcd;
@@ -28,6 +30,7 @@ namespace {
 
 constexpr size_t kRefineScratchBytes = (size_t)8 << 30;  // mixed path: refinement scratch per bucket chunk
 constexpr int kRefineIters = 2;                            // FP64 refinement iterations (even)
+constexpr size_t kGraphCache = 64;                         // wpcd_solve keys remembered for CUDA graphs
 
 struct MeshH {
     int N = 0, Q = 0, kind = 0, wp_kind = 0;
@@ -130,6 +133,20 @@ struct wpcd_ctx {
     std::vector<Rec> recs;
     double prof_ms[WPCD_PHASE_COUNT] = {};
     long prof_n[WPCD_PHASE_COUNT] = {};
+    // CUDA graphs of wpcd_solve.  graph_gen counts every event that may change
+    // what a captured graph baked in (a device allocation or free, an option, a
+    // new tuning); a graph captured under another generation is dropped.
+    int use_graphs = 1;
+    std::atomic<unsigned long long> graph_gen{0};
+    struct GraphE {
+        unsigned long long gen = 0;  // generation when first seen / captured
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long kernels = 0;  // kernels the graph holds
+        bool failed = false;             // capture failed: stay one by one
+    };
+    std::map<std::array<unsigned long long, 12>, GraphE> graphs;
+    cudaStream_t cap_stream = nullptr;  // private stream the captures run on
+    unsigned long long graph_captures = 0, graph_replays = 0;
 };
 
 namespace {
@@ -151,6 +168,7 @@ wpcd_status dmalloc(wpcd_ctx *c, void **p, size_t bytes)
     }
     c->in_use += bytes;
     c->sizes[*p] = bytes;
+    ++c->graph_gen;
     return WPCD_OK;
 }
 
@@ -163,6 +181,7 @@ void dfree(wpcd_ctx *c, void *p)
         c->in_use -= it->second;
         c->sizes.erase(it);
     }
+    ++c->graph_gen;
     cudaFree(p);
 }
 
@@ -172,15 +191,16 @@ wpcd_status dalloc(wpcd_ctx *c, T **p, size_t count)
     return dmalloc(c, reinterpret_cast<void **>(p), count * sizeof(T));
 }
 
-// Counts one kernel launch of `phase`; with profiling on, brackets it with events.
+// One launch step of `phase` (one or more kernels): adds the kernels it
+// launched to the context count; with profiling on, brackets it with events.
 struct Launch {
     wpcd_ctx *c;
     cudaStream_t st;
     wpcd_ctx::Rec r{};
     bool on;
-    Launch(wpcd_ctx *cc, const Exec &X, int phase) : c(cc), st(X.stream), on(cc->prof)
+    unsigned long long k0;
+    Launch(wpcd_ctx *cc, const Exec &X, int phase) : c(cc), st(X.stream), on(cc->prof), k0(g_thread_kernels)
     {
-        ++c->launches;
         r.phase = phase;
         if (on) {
             cudaEventCreate(&r.a);
@@ -190,6 +210,7 @@ struct Launch {
     }
     ~Launch()
     {
+        c->launches += g_thread_kernels - k0;
         if (on) {
             cudaEventRecord(r.b, st);
             std::lock_guard<std::mutex> lk(c->pmu);
@@ -214,9 +235,16 @@ void prof_collect(wpcd_ctx *c)
     c->recs.clear();
 }
 
+bool capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
 wpcd_status ws_reserve(wpcd_ctx *c, const Exec &X, Buf &b, size_t bytes)
 {
     if (b.n >= bytes) return WPCD_OK;
+    if (capturing(X.stream)) return WPCD_ERR_CUDA;  // a graph cannot hold a reallocation
     if (b.p) {
         cudaStreamSynchronize(X.stream);
         dfree(c, b.p);
@@ -314,6 +342,7 @@ int pick_threads(wpcd_ctx *c, Exec &X, int n, int prec, int nw, int nsmp, F laun
         auto it = c->tuned.find(key);
         if (it != c->tuned.end()) return it->second.threads;
     }
+    if (capturing(X.stream)) return -1;  // tuning synchronises: never inside a capture
     if (!c->n_sm) cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
     wpcd_ctx::Tuned t{256, {-1.f, -1.f, -1.f, -1.f}};
     float best = 1e30f;
@@ -350,13 +379,14 @@ int pick_threads(wpcd_ctx *c, Exec &X, int n, int prec, int nw, int nsmp, F laun
     cudaEventDestroy(b);
     std::lock_guard<std::mutex> lk(c->tmu);
     c->tuned[key] = t;
+    ++c->graph_gen;
     return t.threads;
 }
 
-// Allocate (or reuse) eigenpair storage for `S` samples of vset v and run the
-// parameter sum + eigensolve.
-wpcd_status run_diag(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, const double *coeffs, int S, int prec, EigH &e,
-                     bool coeffs_on_device = true)
+// Allocate (or reuse) eigenpair storage for `S` samples of vset v and upload
+// the channel table with this batch's offsets (a pageable host copy, so it
+// stays outside CUDA graphs).
+wpcd_status diag_prep(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, int S, int prec, EigH &e)
 {
     size_t eps_len = 0, c_len = 0;
     std::vector<ChanDev> cd = v.cd;
@@ -388,9 +418,17 @@ wpcd_status run_diag(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, const double *
     e.n_samples = S;
     e.prec = prec;
     CK(cudaMemcpyAsync(e.cd_dev, cd.data(), sizeof(ChanDev) * v.n_ch, cudaMemcpyHostToDevice, X.stream));
+    return WPCD_OK;
+}
+
+// The parameter sum + eigensolve of the batch diag_prep set up (device-only
+// work on X.stream: capturable).  coeffs: device, [S][n_terms - 1].
+wpcd_status diag_body(wpcd_ctx *c, Exec &X, VSetH &v, const double *coeffs, int S, int prec, EigH &e)
+{
+    wpcd_status st = WPCD_OK;
     if (v.n_terms > 1) {
-        CK(cudaMemcpyAsync(e.coeffs, coeffs, sizeof(double) * S * (v.n_terms - 1),
-                           coeffs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, X.stream));
+        CK(cudaMemcpyAsync(e.coeffs, coeffs, sizeof(double) * S * (v.n_terms - 1), cudaMemcpyDeviceToDevice,
+                           X.stream));
     }
     const double *cf = v.n_terms > 1 ? e.coeffs : nullptr;
     // FP64: one Jacobi launch per size bucket (largest first), or per solve in plain mode.
@@ -448,12 +486,18 @@ wpcd_status run_diag(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, const double *
         // one solve per launch: the baseline execution on the same GPU
         for (int s = 0; s < S; ++s)
             for (int k = 0; k < v.n_ch; ++k)
-                if ((st = run_bucket(v.ident_dev + k, 1, 1, s, cd[k].n))) return st;
+                if ((st = run_bucket(v.ident_dev + k, 1, 1, s, v.cd[k].n))) return st;
     } else {
         for (auto it = v.buckets.rbegin(); it != v.buckets.rend(); ++it)
             if ((st = run_bucket(v.bucket_dev[it->first], (int)it->second.size(), S, 0, it->first))) return st;
     }
     return WPCD_OK;
+}
+
+wpcd_status run_diag(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, const double *coeffs, int S, int prec, EigH &e)
+{
+    wpcd_status st = diag_prep(c, X, v, vset_id, S, prec, e);
+    return st ? st : diag_body(c, X, v, coeffs, S, prec, e);
 }
 
 // Energy plan + T at the needed bins into the executor's workspaces.  With
@@ -585,6 +629,10 @@ void wpcd_destroy(wpcd_ctx *c)
         if (kv.second.mi) free_mi(c, *kv.second.mi);
     }
     serve_shutdown(c);
+    for (auto &kv : c->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    c->graphs.clear();
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     free_eig(c, c->main.eig);
     for (auto &kv : c->gl) {
         dfree(c, kv.second.first);
@@ -599,6 +647,11 @@ void wpcd_destroy(wpcd_ctx *c)
 wpcd_status wpcd_set_option(wpcd_ctx *c, int key, int value)
 {
     if (!c) return WPCD_ERR_ARG;
+    ++c->graph_gen;  // any option may change what a graph baked in
+    if (key == WPCD_OPT_GRAPH && (value == 0 || value == 1)) {
+        c->use_graphs = value;
+        return WPCD_OK;
+    }
     if (key == WPCD_OPT_EXEC && (value == WPCD_EXEC_BATCHED || value == WPCD_EXEC_PLAIN)) {
         c->exec_mode = value;
         return WPCD_OK;
@@ -957,6 +1010,86 @@ wpcd_status wpcd_observables(wpcd_ctx *c, int eig_id, const double *e_lab, int n
     return wpcd_observables_res(c, eig_id, e_lab, n_E, WPCD_AVG_FREE_BIN, delta, sigma);
 }
 
+// wpcd_solve through the graph cache (the caller holds c->mu).  First sight of
+// a key: launch one by one and remember the key under the current generation.
+// Second sight under the same generation: capture the device work on the
+// private stream, instantiate, launch.  Later: launch the graph.  The channel
+// table upload (diag_prep) runs before every launch, outside the graph.
+static wpcd_status solve_graph(wpcd_ctx *c, VSetH &v, int vset_id, const double *coeffs, int S, const double *e_lab,
+                               int n_E, int prec, int res, double *t_out, double *delta, double *sigma)
+{
+    Exec &X = c->main;
+    EigH &e = X.eig;
+    auto body = [&]() -> wpcd_status {
+        wpcd_status st = diag_body(c, X, v, coeffs, S, prec, e);
+        return st ? st : tmatrix_impl(c, v, e, e_lab, n_E, res, t_out, delta, sigma);
+    };
+    typedef unsigned long long u64;
+    const std::array<u64, 12> key = {(u64)vset_id, (u64)S, (u64)n_E, (u64)prec, (u64)res, (u64)c->refine_engine,
+                                     (u64)(uintptr_t)coeffs, (u64)(uintptr_t)e_lab, (u64)(uintptr_t)t_out,
+                                     (u64)(uintptr_t)delta, (u64)(uintptr_t)sigma, (u64)(uintptr_t)X.stream};
+    auto drop = [&](std::map<std::array<u64, 12>, wpcd_ctx::GraphE>::iterator it) {
+        if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+        c->graphs.erase(it);
+    };
+    auto it = c->graphs.find(key);
+    if (it != c->graphs.end() && it->second.gen != c->graph_gen.load()) {
+        drop(it);
+        it = c->graphs.end();
+    }
+    wpcd_status st = diag_prep(c, X, v, vset_id, S, prec, e);
+    if (st) return st;
+    if (it == c->graphs.end() || it->second.failed) {
+        if ((st = body())) return st;
+        if (it == c->graphs.end()) {
+            if (c->graphs.size() >= kGraphCache) {  // forget keys seen once, then everything
+                for (auto jt = c->graphs.begin(); jt != c->graphs.end();)
+                    jt = jt->second.exec ? std::next(jt) : c->graphs.erase(jt);
+                while (c->graphs.size() >= kGraphCache) drop(c->graphs.begin());
+            }
+            c->graphs[key].gen = c->graph_gen.load();
+        }
+        return WPCD_OK;
+    }
+    wpcd_ctx::GraphE &g = it->second;
+    if (g.gen != c->graph_gen.load()) {  // diag_prep reallocated the eigenpair storage
+        drop(it);
+        return body();
+    }
+    if (!g.exec) {
+        if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        cudaStream_t user = X.stream;
+        const u64 k0 = g_thread_kernels;
+        cudaGraph_t graph = nullptr;
+        wpcd_status cst = WPCD_ERR_CUDA;
+        X.stream = c->cap_stream;
+        if (cudaStreamBeginCapture(X.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            cst = body();
+            if (cudaStreamEndCapture(X.stream, &graph) != cudaSuccess) cst = WPCD_ERR_CUDA;
+        }
+        X.stream = user;
+        const u64 kernels = g_thread_kernels - k0;
+        c->launches -= kernels;  // captured, not launched
+        cudaGraphExec_t exec = nullptr;
+        if (cst == WPCD_OK && graph && g.gen == c->graph_gen.load() &&
+            cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+            exec = nullptr;
+        if (graph) cudaGraphDestroy(graph);
+        if (!exec) {  // not capturable: this key stays one by one
+            cudaGetLastError();
+            g.failed = true;
+            return body();
+        }
+        g.exec = exec;
+        g.kernels = kernels;
+        ++c->graph_captures;
+    }
+    CK(cudaGraphLaunch(g.exec, X.stream));
+    c->launches += g.kernels;
+    ++c->graph_replays;
+    return WPCD_OK;
+}
+
 wpcd_status wpcd_solve(wpcd_ctx *c, int vset_id, const double *coeffs, int S, const double *e_lab, int n_E,
                        wpcd_precision prec, wpcd_resolvent res, double *t_out, double *delta, double *sigma)
 {
@@ -969,6 +1102,8 @@ wpcd_status wpcd_solve(wpcd_ctx *c, int vset_id, const double *coeffs, int S, co
     if (v.n_terms > 1 && !coeffs) return WPCD_ERR_ARG;
     if (!resolvent_ok(v, res)) return WPCD_ERR_ARG;
     CK(cudaSetDevice(c->device));
+    if (c->use_graphs && c->exec_mode == WPCD_EXEC_BATCHED && !c->prof)
+        return solve_graph(c, v, vset_id, coeffs, S, e_lab, n_E, prec, res, t_out, delta, sigma);
     wpcd_status st = run_diag(c, c->main, v, vset_id, coeffs, S, prec, c->main.eig);
     if (st) return st;
     return tmatrix_impl(c, v, c->main.eig, e_lab, n_E, res, t_out, delta, sigma);
@@ -1050,6 +1185,20 @@ int wpcd_tuning(wpcd_ctx *c, int max_entries, int *n_out, int *prec_out, int *th
 }
 
 unsigned long long wpcd_kernel_launches(const wpcd_ctx *c) { return c ? c->launches.load() : 0ULL; }
+
+wpcd_status wpcd_graph_stats(wpcd_ctx *c, unsigned long long *captures, unsigned long long *replays, int *cached)
+{
+    if (!c) return WPCD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (captures) *captures = c->graph_captures;
+    if (replays) *replays = c->graph_replays;
+    if (cached) {
+        int k = 0;
+        for (auto &kv : c->graphs) k += kv.second.exec != nullptr;
+        *cached = k;
+    }
+    return WPCD_OK;
+}
 
 wpcd_status wpcd_profile(wpcd_ctx *c, int enable)
 {

@@ -170,7 +170,7 @@ cudaError_t launch_saclay(const SacChanDev *chans_dev, int n_ch, int n_samples, 
                           cudaStream_t st)
 {
     const size_t total = (size_t)n_samples * n_E * n_th;
-    k_saclay<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(chans_dev, n_ch, n_samples, n_E, e_lab, delta, n_th,
+    k_saclay<<<(unsigned)((total + 127) / 128), 128, 0, counted(st)>>>(chans_dev, n_ch, n_samples, n_E, e_lab, delta, n_th,
                                                                theta, abcde, dsig);
     return cudaGetLastError();
 }

@@ -68,7 +68,7 @@ __global__ void k_plan(const ChanDev *chans, int n_ch, int maxN, const double *e
 cudaError_t launch_plan(const ChanDev *chans_dev, int n_ch, int maxN, const double *e_lab, int n_E, PlanDev plan,
                         int *err, cudaStream_t st, int n_plans)
 {
-    k_plan<<<dim3(n_ch, n_plans), 256, 0, st>>>(chans_dev, n_ch, maxN, e_lab, n_E, plan, err);
+    k_plan<<<dim3(n_ch, n_plans), 256, 0, counted(st)>>>(chans_dev, n_ch, maxN, e_lab, n_E, plan, err);
     return cudaGetLastError();
 }
 
@@ -431,7 +431,7 @@ static void launch_tmat_t(const ChanDev *chans_dev, int n_ch, int n_samples, int
                           size_t smem, double *tout, double *phout, int *err, cudaStream_t st)
 {
     cudaFuncSetAttribute(k_tmat<VCID, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_tmat<VCID, MODE><<<(unsigned)(n_samples * n_ch), kTThreads, smem, st>>>(chans_dev, n_ch, n_terms, coeffs, eps_all,
+    k_tmat<VCID, MODE><<<(unsigned)(n_samples * n_ch), kTThreads, smem, counted(st)>>>(chans_dev, n_ch, n_terms, coeffs, eps_all,
                                                                               C_all, plan, n_E, stride, tout, phout,
                                                                               err);
 }
@@ -488,7 +488,7 @@ cudaError_t launch_gather_t(const ChanDev *chans_dev, int n_ch, int n_samples, i
 {
     (void)chans_dev;
     const size_t total = (size_t)n_samples * n_ch * n_E;
-    k_gather_t<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n_ch, n_samples, n_E, direct ? n_E : maxN, direct,
+    k_gather_t<<<(unsigned)((total + 255) / 256), 256, 0, counted(st)>>>(n_ch, n_samples, n_E, direct ? n_E : maxN, direct,
                                                                 plan, tbin, t_out);
     return cudaGetLastError();
 }
@@ -570,7 +570,7 @@ cudaError_t launch_observables(const ChanDev *chans_dev, int n_ch, int n_samples
                                const double *phbin, double *delta, double *sigma, cudaStream_t st, bool direct)
 {
     const size_t total = (size_t)n_samples * n_E;
-    k_observables<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(chans_dev, n_ch, n_samples, n_E,
+    k_observables<<<(unsigned)((total + 127) / 128), 128, 0, counted(st)>>>(chans_dev, n_ch, n_samples, n_E,
                                                                     direct ? n_E : maxN, direct, plan, phbin, delta,
                                                                     sigma);
     return cudaGetLastError();

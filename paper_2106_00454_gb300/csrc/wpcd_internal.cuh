@@ -36,6 +36,16 @@ enum DevErr : int {
     kDevTimeout = 6  // a bounded wait inside a kernel ran out
 };
 
+// Kernels launched by the calling host thread.  Every launch site passes its
+// stream through counted(), so the runtime counts kernels exactly (including
+// the ones a CUDA-graph capture records).
+extern thread_local unsigned long long g_thread_kernels;
+inline cudaStream_t counted(cudaStream_t st)
+{
+    ++g_thread_kernels;
+    return st;
+}
+
 // One channel of a projected potential set, as the kernels see it.
 // Channel of an MI set: its grid potential terms Vg [n_terms][n][n] start at
 // vg_off, its on-shell columns Von [n_I][n_terms][K][K][N_Q+1] at von_off;
