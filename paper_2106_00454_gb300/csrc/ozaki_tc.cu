@@ -10,8 +10,10 @@
 //     64 columns of B; 72 KB), in the 64-byte-swizzled K-major layout the
 //     tensor core reads;
 //   * warp 9 (one thread) owns the tensor memory and issues, per chunk, the 21
-//     digit pairs p + q <= 5 as M = 128, N = 64, K = 16 MMAs into six FP32
-//     accumulators, one per weight d = p + q (6 x 64 TMEM columns);
+//     digit pairs p + q <= 5 into six FP32 accumulators, one per weight
+//     d = p + q (6 x 64 TMEM columns): on full-width tiles as eight M = 128,
+//     K = 16 MMAs of N = 64 .. 256 that each multiply one A digit by up to four
+//     adjacent B digits, on a narrower last column tile as 21 MMAs of N <= 48;
 //   * warps 0-7 drain the accumulators every 128 k into per-thread int64
 //     sums, shifted by 36 - 8d (warp w reads TMEM lanes 32 (w % 4) .. + 31 =
 //     rows of the tile, columns 32 (w / 4) .. + 31), and write the FP64 tile,
@@ -82,6 +84,24 @@ constexpr long long kTcWaitCycles = 1ll << 31;
 // 17-22, N / 8) is set per tile: 64, or the last column tile's width rounded up
 // to 16, so a ragged edge costs at most 15 padded columns
 constexpr uint32_t kTcIdescBase = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcM >> 4) << 24);
+
+// The 21 digit pairs of one 16-k step as eight wide MMAs.  The B digits of a
+// stage lie back to back in shared memory (64 rows each, the same 512-byte
+// row-group stride), so digits q0 .. q0 + nq - 1 form one K-major operand of
+// N = 64 nq rows; A digit p times it lands, 64 columns per digit, on the
+// accumulators of weights p + q0 .. p + q0 + nq - 1, which are adjacent in
+// TMEM.  Segment g = (p, q0, nq): every pair p + q <= 5 exactly once, and the
+// two p = 0 segments write every weight before any other segment does.
+constexpr int kTcSegs = 8;
+__device__ __forceinline__ void tc_seg(int g, int &p, int &q0, int &nq)
+{
+    constexpr int P[kTcSegs] = {0, 0, 1, 1, 2, 3, 4, 5};
+    constexpr int Q0[kTcSegs] = {0, 4, 0, 4, 0, 0, 0, 0};
+    constexpr int NQ[kTcSegs] = {4, 2, 4, 1, 4, 3, 2, 1};
+    p = P[g];
+    q0 = Q0[g];
+    nq = NQ[g];
+}
 
 __device__ __forceinline__ int tc_tile_n(int n, int col0)
 {
@@ -283,7 +303,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             uint32_t ph = 0;
             for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
                 const TcTile tl = tc_tile(t, per_item, TC, sym);
-                const uint32_t idesc = kTcIdescBase | ((uint32_t)(tc_tile_n(n, tl.col0) >> 3) << 17);
+                const int tn = tc_tile_n(n, tl.col0);
+                const bool full = tn == kTcN;  // full-width tile: the wide segments
+                const uint32_t idesc = kTcIdescBase | ((uint32_t)(tn >> 3) << 17);
                 for (int k0 = 0; k0 < Kp; k0 += kTcKC) {
                     const bool bfirst = (k0 % kTcKBlk) == 0;
                     const bool blast = ((k0 + kTcKC) % kTcKBlk) == 0 || k0 + kTcKC >= Kp;
@@ -298,18 +320,37 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     tc_fence_after();
                     const uint32_t sA = ring_s + (uint32_t)(stage * kTcStageBytes), sB = sA + kTcAStage;
                     const uint64_t a0 = tc_desc_sw64(sA), b0 = tc_desc_sw64(sB);
-                    for (int d = 0; d <= dmax; ++d)
-                        for (int p = 0; p <= d; ++p) {
-                            const int q = d - p;
+                    if (full) {
 #pragma unroll
-                            for (int kk = 0; kk < 2; ++kk) {  // K = 16: 32 bytes further into the swizzle span
-                                if (kk == 1 && k0 + 16 >= n) break;  // that half of the chunk is zero padding
+                        for (int kk = 0; kk < 2; ++kk) {  // K = 16: 32 bytes further into the swizzle span
+                            if (kk == 1 && k0 + 16 >= n) break;  // that half of the chunk is zero padding
+#pragma unroll
+                            for (int g = 0; g < kTcSegs; ++g) {
+                                int p, q0, nq;
+                                tc_seg(g, p, q0, nq);
+                                nq = min(nq, dmax - p - q0 + 1);
+                                if (nq <= 0) continue;
                                 const uint64_t ad = a0 + (uint64_t)((p * kTcADigit + kk * 32) >> 4);
-                                const uint64_t bd = b0 + (uint64_t)((q * kTcBDigit + kk * 32) >> 4);
-                                tc_mma(tmem + (uint32_t)(d * kTcN), ad, bd, idesc,
-                                       (bfirst && p == 0 && kk == 0) ? 0u : 1u);
+                                const uint64_t bd = b0 + (uint64_t)((q0 * kTcBDigit + kk * 32) >> 4);
+                                tc_mma(tmem + (uint32_t)((p + q0) * kTcN), ad, bd,
+                                       kTcIdescBase | ((uint32_t)(nq * kTcN >> 3) << 17),
+                                       (bfirst && kk == 0 && p == 0) ? 0u : 1u);
                             }
                         }
+                    } else {
+                        for (int d = 0; d <= dmax; ++d)
+                            for (int p = 0; p <= d; ++p) {
+                                const int q = d - p;
+#pragma unroll
+                                for (int kk = 0; kk < 2; ++kk) {
+                                    if (kk == 1 && k0 + 16 >= n) break;
+                                    const uint64_t ad = a0 + (uint64_t)((p * kTcADigit + kk * 32) >> 4);
+                                    const uint64_t bd = b0 + (uint64_t)((q * kTcBDigit + kk * 32) >> 4);
+                                    tc_mma(tmem + (uint32_t)(d * kTcN), ad, bd, idesc,
+                                           (bfirst && p == 0 && kk == 0) ? 0u : 1u);
+                                }
+                            }
+                    }
                     tc_commit(empty_s + 8u * stage);
                     ++committed;
                     if (blast) {
