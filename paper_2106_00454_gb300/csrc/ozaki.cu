@@ -123,27 +123,79 @@ __device__ __forceinline__ int oz_exp_of(unsigned long long mag)
     return ex;
 }
 
-// Row slices: S[b][p][v][k] = digit p of M[v][k], one warp per row v: the
-// row's exponent from a warp maximum, then its digits with k fastest
-// (coalesced reads and writes); k in [n, Kp) is zero padding.
+// Row slices: S[b][p][v][k] = digit p of M[v][k], one warp per row v.  The
+// row is read once into registers (lane l holds the pairs k = 2 l + 64 j,
+// k + 1, all loads issued before any is used), its exponent comes from a warp
+// maximum, and the digits are written from the registers with k fastest
+// (coalesced); k in [n, Kp) is zero padding.
+// PAIRS per lane: Kp <= 64 PAIRS (the launch picks the smallest of 4, 8, 16).
+template <int PAIRS>
 __global__ void __launch_bounds__(256) k_oz_split_rows(int n, int Kp, const double *M_all, int *e_all,
                                                        __nv_bfloat16 *S_all)
 {
+    constexpr int kOzRowPairs = PAIRS;
     const int b = blockIdx.y, v = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (v >= n) return;
     const double *row = M_all + (size_t)b * n * n + (size_t)v * n;
+    double x0[kOzRowPairs], x1[kOzRowPairs];
     unsigned long long m = 0;
-    for (int k = lane; k < n; k += 32) m = max(m, oz_mag(row[k]));
+#pragma unroll
+    for (int j = 0; j < kOzRowPairs; ++j) {
+        const int k = 2 * lane + 64 * j;
+        x0[j] = k < n ? row[k] : 0.0;
+        x1[j] = k + 1 < n ? row[k + 1] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kOzRowPairs; ++j) m = max(m, max(oz_mag(x0[j]), oz_mag(x1[j])));
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     const int ex = oz_exp_of(m);
     if (lane == 0) e_all[(size_t)b * n + v] = ex;
     __nv_bfloat16 *S = S_all + (size_t)b * kOzP * n * Kp + (size_t)v * Kp;
-    for (int k = 2 * lane; k < Kp; k += 64)  // Kp is even: pairs (k, k + 1)
-        oz_digits2(k < n ? row[k] : 0.0, k + 1 < n ? row[k + 1] : 0.0, ex, S + k, (size_t)n * Kp);
+#pragma unroll
+    for (int j = 0; j < kOzRowPairs; ++j) {
+        const int k = 2 * lane + 64 * j;  // Kp is even: pairs (k, k + 1)
+        if (k < Kp) oz_digits2(x0[j], x1[j], ex, S + k, (size_t)n * Kp);
+    }
 }
 
-// Column slices: S[b][p][v][k] = digit p of M[k][v], one CTA (32 x 8) per 32
-// columns: the column maxima first (reads along v), then 64 x 32 tiles
+// Column slices for Kp <= kOzColBlockKp: one CTA (32 x 8) per 32 columns reads
+// its Kp x 32 block once into shared memory (pitch 33 doubles; v fastest,
+// coalesced), takes the column maxima while loading, and writes the digits
+// from shared memory along k (two per thread, coalesced).
+constexpr int kOzColBlockKp = 384;  // 101 KB of shared memory at most
+__global__ void __launch_bounds__(256) k_oz_split_cols_block(int n, int Kp, const double *M_all, int *e_all,
+                                                             __nv_bfloat16 *S_all)
+{
+    extern __shared__ double blk[];  // [Kp][33]
+    __shared__ unsigned long long mcol[8][32];
+    __shared__ int ecol[32];
+    const int b = blockIdx.y;
+    const int v0 = blockIdx.x * 32, tx = threadIdx.x, ty = threadIdx.y, v = v0 + tx;
+    const double *M = M_all + (size_t)b * n * n;
+    unsigned long long m = 0;
+#pragma unroll 8
+    for (int k = ty; k < Kp; k += 8) {
+        const double x = (k < n && v < n) ? M[(size_t)k * n + v] : 0.0;
+        blk[k * 33 + tx] = x;
+        m = max(m, oz_mag(x));
+    }
+    mcol[ty][tx] = m;
+    __syncthreads();
+    if (ty == 0) {
+        for (int r = 1; r < 8; ++r) m = max(m, mcol[r][tx]);
+        ecol[tx] = oz_exp_of(m);
+        if (v < n) e_all[(size_t)b * n + v] = ecol[tx];
+    }
+    __syncthreads();
+    __nv_bfloat16 *S = S_all + (size_t)b * kOzP * n * Kp;
+    for (int r = ty; r < 32 && v0 + r < n; r += 8)  // column v0 + r, k pairs 2 tx + 64 j
+        for (int k = 2 * tx; k < Kp; k += 64)
+            oz_digits2(blk[k * 33 + r], blk[(k + 1) * 33 + r], ecol[r], S + (size_t)(v0 + r) * Kp + k,
+                       (size_t)n * Kp);
+}
+
+// Column slices for larger Kp: S[b][p][v][k] = digit p of M[k][v], one CTA
+// (32 x 8) per 32 columns: the column maxima first (reads along v), then 64 x 32 tiles
 // transposed through shared memory so that both the reads (v fastest) and the
 // writes (k fastest, two per thread) are coalesced.
 __global__ void __launch_bounds__(256) k_oz_split_cols(int n, int Kp, const double *M_all, int *e_all,
@@ -186,8 +238,20 @@ __global__ void __launch_bounds__(256) k_oz_split_cols(int n, int Kp, const doub
 cudaError_t launch_oz_split(int n, int items, bool cols, const double *M, __nv_bfloat16 *S, int *e, cudaStream_t st)
 {
     const int Kp = oz_kpad(n);
-    if (cols) k_oz_split_cols<<<dim3((n + 31) / 32, items), dim3(32, 8), 0, counted(st)>>>(n, Kp, M, e, S);
-    else k_oz_split_rows<<<dim3((n + 7) / 8, items), 256, 0, counted(st)>>>(n, Kp, M, e, S);
+    if (!cols) {
+        const dim3 g((n + 7) / 8, items);
+        if (Kp <= 256) k_oz_split_rows<4><<<g, 256, 0, counted(st)>>>(n, Kp, M, e, S);
+        else if (Kp <= 512) k_oz_split_rows<8><<<g, 256, 0, counted(st)>>>(n, Kp, M, e, S);
+        else k_oz_split_rows<16><<<g, 256, 0, counted(st)>>>(n, Kp, M, e, S);
+    } else if (Kp <= kOzColBlockKp) {
+        const size_t smem = (size_t)Kp * 33 * sizeof(double);
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_oz_split_cols_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kOzColBlockKp * 33 * (int)sizeof(double));
+        k_oz_split_cols_block<<<dim3((n + 31) / 32, items), dim3(32, 8), smem, counted(st)>>>(n, Kp, M, e, S);
+    } else {
+        k_oz_split_cols<<<dim3((n + 31) / 32, items), dim3(32, 8), 0, counted(st)>>>(n, Kp, M, e, S);
+    }
     return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ def _mats(n, items, seed):
     return A, B
 
 
-@pytest.mark.parametrize("n", [8, 40, 100, 200, 300])
+@pytest.mark.parametrize("n", [8, 40, 57, 100, 200, 300])
 @pytest.mark.parametrize("trans_a", [False, True])
 def test_batched_dgemm_engines(ctx, n, trans_a):
     import torch
@@ -54,7 +54,7 @@ def test_batched_dgemm_engines(ctx, n, trans_a):
 
 
 def test_batched_dgemm_long_contraction(ctx):
-    # K beyond the tcgen05 step schedule (n > 768) takes the mma.sync kernel
+    # seven 128-k blocks per tile, and the column split for Kp beyond a shared-memory block
     import torch
     from paper_2106_00454_gb300 import api
     n = 800
