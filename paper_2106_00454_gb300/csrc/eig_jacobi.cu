@@ -279,11 +279,11 @@ cudaError_t launch_jacobi_f64(const ChanDev *chans_dev, const int *work_ch_dev, 
     if (!cs && (size_t)(threads / 32) * n > packed_len(n)) return cudaErrorInvalidValue;  // row buffers fit in A
     dim3 grid((unsigned)(n_samples * n_work_ch));
     if (cs) {
-        cudaFuncSetAttribute(k_jacobi_f64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_smem_limit((const void *)k_jacobi_f64<true>, smem);
         k_jacobi_f64<true><<<grid, threads, smem, counted(st)>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
                                                             coeffs, eps_all, C_all, status_all, n_ch_total, err);
     } else {
-        cudaFuncSetAttribute(k_jacobi_f64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_smem_limit((const void *)k_jacobi_f64<false>, smem);
         k_jacobi_f64<false><<<grid, threads, smem, counted(st)>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
                                                              coeffs, eps_all, C_all, status_all, n_ch_total, err);
     }
@@ -296,10 +296,10 @@ int jacobi_f64_occupancy(int n, int threads)
     const size_t smem = jacobi_smem_bytes(n, cs);
     int blocks = 0;
     if (cs) {
-        cudaFuncSetAttribute(k_jacobi_f64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_smem_limit((const void *)k_jacobi_f64<true>, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_jacobi_f64<true>, threads, smem);
     } else {
-        cudaFuncSetAttribute(k_jacobi_f64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_smem_limit((const void *)k_jacobi_f64<false>, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_jacobi_f64<false>, threads, smem);
     }
     return blocks;

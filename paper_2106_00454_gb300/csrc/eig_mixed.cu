@@ -271,11 +271,11 @@ cudaError_t launch_jacobi_mixed(const ChanDev *chans_dev, const int *work_ch_dev
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     dim3 grid((unsigned)(n_samples * n_work_ch));
     if (cs) {
-        cudaFuncSetAttribute(k_jacobi_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_smem_limit((const void *)k_jacobi_mixed<true>, smem);
         k_jacobi_mixed<true><<<grid, threads, smem, counted(st)>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
                                                               coeffs, lam_s, X_s, Cf_s, H_s, status_all, n_ch_total, err);
     } else {
-        cudaFuncSetAttribute(k_jacobi_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_smem_limit((const void *)k_jacobi_mixed<false>, smem);
         k_jacobi_mixed<false><<<grid, threads, smem, counted(st)>>>(chans_dev, work_ch_dev, n_work_ch, sample0, n_terms,
                                                                coeffs, lam_s, X_s, Cf_s, H_s, status_all, n_ch_total, err);
     }
@@ -290,10 +290,10 @@ int jacobi_mixed_occupancy(int n, int threads)
     const size_t smem = mix_smem(n, cs);
     int blocks = 0;
     if (cs) {
-        cudaFuncSetAttribute(k_jacobi_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_smem_limit((const void *)k_jacobi_mixed<true>, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_jacobi_mixed<true>, threads, smem);
     } else {
-        cudaFuncSetAttribute(k_jacobi_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_smem_limit((const void *)k_jacobi_mixed<false>, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_jacobi_mixed<false>, threads, smem);
     }
     return blocks;

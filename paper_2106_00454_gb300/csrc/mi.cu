@@ -513,7 +513,7 @@ cudaError_t launch_mi_solve(const MiChanDev *chans_dev, const int *work_dev, int
 {
     const size_t smem = mi_smem(n, NQ + 1);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaFuncSetAttribute(k_mi_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_limit((const void *)k_mi_solve, smem);
     k_mi_solve<<<slots, kMiThreads, smem, counted(st)>>>(chans_dev, work_dev, n_work, n_ch_total, n_samples, NQ, kg, wg, n_terms,
                                                 coeffs, Vg, Von, n_I, e_int, Vs, ph, k_out, status, err);
     return cudaGetLastError();
@@ -522,7 +522,7 @@ cudaError_t launch_mi_solve(const MiChanDev *chans_dev, const int *work_dev, int
 int mi_slots_per_sm(int n, int NQ)
 {
     const size_t smem = mi_smem(n, NQ + 1);
-    cudaFuncSetAttribute(k_mi_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_limit((const void *)k_mi_solve, smem);
     int blocks = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_mi_solve, kMiThreads, smem);
     return blocks;

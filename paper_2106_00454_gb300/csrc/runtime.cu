@@ -22,6 +22,16 @@
 namespace wpcd {
 size_t tbin_smem_bytes(int nmax);
 thread_local unsigned long long g_thread_kernels = 0;
+
+cudaError_t raise_smem_limit(const void *kernel, size_t bytes)
+{
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess || (size_t)a.maxDynamicSharedSizeBytes >= bytes) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 }
 
 using namespace wpcd;

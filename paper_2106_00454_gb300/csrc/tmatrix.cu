@@ -430,7 +430,7 @@ static void launch_tmat_t(const ChanDev *chans_dev, int n_ch, int n_samples, int
                           const double *eps_all, const double *C_all, PlanDev plan, int n_E, int stride,
                           size_t smem, double *tout, double *phout, int *err, cudaStream_t st)
 {
-    cudaFuncSetAttribute(k_tmat<VCID, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_limit((const void *)k_tmat<VCID, MODE>, smem);
     k_tmat<VCID, MODE><<<(unsigned)(n_samples * n_ch), kTThreads, smem, counted(st)>>>(chans_dev, n_ch, n_terms, coeffs, eps_all,
                                                                               C_all, plan, n_E, stride, tout, phout,
                                                                               err);

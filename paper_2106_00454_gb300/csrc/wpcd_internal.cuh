@@ -46,6 +46,12 @@ inline cudaStream_t counted(cudaStream_t st)
     return st;
 }
 
+// Raise, never lower, a kernel's dynamic shared-memory limit to `bytes`.  The
+// limit is a property of the kernel, and a CUDA graph captured earlier may
+// hold a launch of the same kernel with more shared memory than the current
+// launch needs, so the limit only grows (thread-safe).
+cudaError_t raise_smem_limit(const void *kernel, size_t bytes);
+
 // One channel of a projected potential set, as the kernels see it.
 // Channel of an MI set: its grid potential terms Vg [n_terms][n][n] start at
 // vg_off, its on-shell columns Von [n_I][n_terms][K][K][N_Q+1] at von_off;
