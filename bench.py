@@ -417,6 +417,23 @@ def run_wpcd(args, ws, rank, lrank):
            "peak": FP64_PEAK_TFLOPS if prec == api.PREC_FP64 else FP32_PEAK_TFLOPS,
            "peak_source": ("nominal GB300 FP64 rate (measured 1.19 TFLOP/s with a DFMA probe)" if prec == api.PREC_FP64
                            else "FP32 FMA rate from unit counts: 152 SM x 128 lanes x 2 flop x 2.07 GHz")}
+    if args.exec == "batched":
+        # executed eigensolver work, from the sweep count of every solve (the eigensolver's
+        # status): a round updates the packed matrix in ~n^2/8 quads of 16 flop and rotates
+        # n/2 eigenvector column pairs at 4n flop, n - 1 rounds a sweep, so <= 4 n^3 per
+        # sweep (an upper bound: pairs below the rotation threshold are skipped)
+        eid = ctx.diag(md.vset, cf, S, prec=prec)
+        sweeps = torch.zeros((S, nch), dtype=torch.int32, device=dev)
+        ctx.diag_status(eid, sweeps)
+        ctx.sync()
+        sw = np.clip(sweeps.cpu().numpy(), 0, None).astype(np.float64)
+        ctx.release(eid)
+        nvec = np.array([n * (2 if ch.coupled else 1) for n, ch in zip(wl.nwp, wl.channels)], dtype=np.float64)
+        ex = float((sw * 4.0 * nvec[None, :] ** 3).sum())
+        ach = ex / (jac["ms_per_step"] * 1e-3) / 1e12
+        jac["executed"] = {"flops_per_step": ex, "achieved": ach, "frac": ach / jac["peak"],
+                           "sweeps_mean": float(sw.mean()), "sweeps_max": int(sw.max()),
+                           "note": "upper bound: sweeps x 4 n^3 per solve"}
     ref = None
     if ref_n:
         if ctx.refine_engine == api.REFINE_TENSOR:

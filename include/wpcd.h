@@ -345,6 +345,13 @@ int wpcd_tuning(wpcd_ctx *ctx, int max_entries, int *n_out, int *prec_out, int *
  * a graph launch counts the kernels it holds). */
 unsigned long long wpcd_kernel_launches(const wpcd_ctx *ctx);
 
+/* The natural logarithm the resolvent kernel uses (table-driven after Tang,
+ * ACM TOMS 16, 1990; about 1 ulp for positive normal arguments, the CUDA
+ * library log for zero, subnormal, infinite and NaN ones), applied to n device
+ * doubles x_dev into y_dev on the context stream: a test hook for comparing it
+ * with other implementations.  Errors: WPCD_ERR_ARG, WPCD_ERR_CUDA. */
+wpcd_status wpcd_device_log(wpcd_ctx *ctx, const double *x_dev, double *y_dev, int n);
+
 /* CUDA-graph use of wpcd_solve: graphs captured and graph launches since the
  * context was created, and graphs currently cached.  Either pointer may be NULL.
  * Errors: WPCD_ERR_ARG (null context). */

@@ -20,7 +20,7 @@ EXPORTED = [
     "wpcd_release", "wpcd_kernel_launches", "wpcd_profile", "wpcd_profile_read",
     "wpcd_channel_solve_noalloc", "wpcd_serve_start", "wpcd_serve_stop", "wpcd_submit", "wpcd_poll", "wpcd_wait",
     "wpcd_release_result", "wpcd_serve_stats", "wpcd_batched_dgemm", "wpcd_tuning", "wpcd_mi_prepare",
-    "wpcd_mi_solve", "wpcd_saclay", "wpcd_graph_stats",
+    "wpcd_mi_solve", "wpcd_saclay", "wpcd_graph_stats", "wpcd_device_log",
 ]
 
 
@@ -87,6 +87,7 @@ _SIG = {
                               ctypes.POINTER(ctypes.c_ulonglong)]),
     "wpcd_graph_stats": (_i, [_vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong),
                               ctypes.POINTER(ctypes.c_int)]),
+    "wpcd_device_log": (_i, [_vp, _vp, _vp, _i]),
 }
 
 _lock = threading.Lock()

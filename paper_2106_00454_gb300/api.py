@@ -91,6 +91,10 @@ class Context:
     def set_graphs(self, on: bool):
         _ck(self.lib.wpcd_set_option(self.h, OPT_GRAPH, 1 if on else 0), "wpcd_set_option")
 
+    def device_log(self, x, y):
+        """y = the resolvent kernel's log(x), elementwise (float64 device tensors)."""
+        _ck(self.lib.wpcd_device_log(self.h, _ptr(x), _ptr(y), x.numel()), "wpcd_device_log")
+
     def graph_stats(self) -> dict:
         cap, rep, cached = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0), ctypes.c_int(0)
         _ck(self.lib.wpcd_graph_stats(self.h, ctypes.byref(cap), ctypes.byref(rep), ctypes.byref(cached)),

@@ -1196,6 +1196,16 @@ int wpcd_tuning(wpcd_ctx *c, int max_entries, int *n_out, int *prec_out, int *th
 
 unsigned long long wpcd_kernel_launches(const wpcd_ctx *c) { return c ? c->launches.load() : 0ULL; }
 
+wpcd_status wpcd_device_log(wpcd_ctx *c, const double *x_dev, double *y_dev, int n)
+{
+    if (!c || n < 0 || (n > 0 && (!x_dev || !y_dev))) return WPCD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(cudaSetDevice(c->device));
+    Launch L(c, c->main, WPCD_PHASE_TMATRIX);
+    CK(launch_wlog(x_dev, y_dev, n, c->main.stream));
+    return WPCD_OK;
+}
+
 wpcd_status wpcd_graph_stats(wpcd_ctx *c, unsigned long long *captures, unsigned long long *replays, int *cached)
 {
     if (!c) return WPCD_ERR_ARG;

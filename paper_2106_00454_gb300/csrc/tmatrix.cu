@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include "wpcd_internal.cuh"
+#include "logtab.h"
 
 namespace wpcd {
 
@@ -72,7 +73,42 @@ cudaError_t launch_plan(const ChanDev *chans_dev, int n_ch, int maxN, const doub
     return cudaGetLastError();
 }
 
-__device__ __forceinline__ double xlogabs(double d) { return d == 0.0 ? 0.0 : d * log(fabs(d)); }
+// Natural logarithm of a positive double, table-driven after P. T. P. Tang,
+// "Table-driven implementation of the logarithm function in IEEE
+// floating-point arithmetic", ACM TOMS 16 (1990): x = 2^k m with m in [1, 2),
+// F = 1 + j/256 the nearest table point (j = 256 is folded into k + 1 and
+// F = 1), u = (m - F) / F with |u| <= 2^-9, and
+//     log x = k log 2 + log F + log1p(u),
+// log 2 and log F as double-double table values (logtab.h) and log1p(u) from
+// its series through u^6 (truncation |u|^7 / 7 < 2^-65).  About 1 ulp; the
+// resolvent evaluates (m + 1)(n + 1) of these per solve, so the 13 FP64
+// operations here instead of the library routine's longer sequence matter on
+// GB300's FP64 pipe.  Zero, subnormal, infinite and NaN arguments take the
+// library log.
+__device__ __forceinline__ double wlog(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const int be = (int)(b >> 52);  // biased exponent; negative for a negative x
+    if (be <= 0 || be >= 0x7FF) return log(x);
+    const long long mant = b & 0x000FFFFFFFFFFFFFll;
+    int j = (int)((mant + (1ll << 43)) >> 44);  // nearest of 256 (m - 1), 0 .. 256
+    int k = be - 1023;
+    long long mb = mant | 0x3FF0000000000000ll;  // m
+    if (j == 256) {  // m / 2 in [1 - 2^-10, 1) against F = 1
+        mb -= 1ll << 52;
+        ++k;
+        j = 0;
+    }
+    const LogEntry t = kLogTab[j];
+    const double f = __longlong_as_double(mb) - __longlong_as_double(0x3FF0000000000000ll + ((long long)j << 44));
+    const double u = f * t.inv;  // f is exact: m and F are within a factor of two
+    const double kd = (double)k;
+    const double c = fma(u, fma(u, fma(u, fma(u, -1.0 / 6.0, 0.2), -0.25), 1.0 / 3.0), -0.5);
+    const double lo = fma(kd, kLn2Lo, t.lo);
+    return fma(kd, kLn2Hi, t.hi) + (u + fma(u * u, c, lo));
+}
+
+__device__ __forceinline__ double xlogabs(double d) { return d == 0.0 ? 0.0 : d * wlog(fabs(d)); }
 
 // ---------------------------------------------------------------------------------------------
 // On-shell T.  One CTA per (sample, channel).
@@ -326,13 +362,13 @@ __global__ void __launch_bounds__(kTThreads, 5) k_tmat(const ChanDev *chans, int
         for (int s = tid; s < n; s += nt) {
             double gre, gim = 0.0;
             if (s < nb) {
-                gre = MODE == 2 ? 1.0 / (E - eps[s]) : log((Ebn - eps[s]) / (Ea - eps[s])) * idE;
+                gre = MODE == 2 ? 1.0 / (E - eps[s]) : wlog((Ebn - eps[s]) / (Ea - eps[s])) * idE;
             } else {
                 const int d = s - nb;
                 const int b = (K == 2) ? (((n - 1 - s) & 1) == 0 ? 1 : 0) : 0;
                 const int q = b * dstride + ((K == 2) ? d / 2 : d);
                 if (MODE == 2) {  // the log of the ratio: no cancellation far from the bin
-                    gre = log(fabs((E - lo[s]) / (E - hi[s]))) * idB[s];
+                    gre = wlog(fabs((E - lo[s]) / (E - hi[s]))) * idB[s];
                     if (E >= lo[s] && E <= hi[s]) gim = -kPi * idB[s];
                 } else {
                     const double w = idB[s] * idE;  // 1 / (dE dB)
@@ -481,6 +517,19 @@ __global__ void k_gather_t(int n_ch, int n_samples, int n_E, int stride, bool di
     double2 *d2 = reinterpret_cast<double2 *>(dst);
 #pragma unroll
     for (int k = 0; k < 4; ++k) d2[k] = s2[k];
+}
+
+// The T kernel's logarithm applied elementwise, for tests against other implementations.
+__global__ void k_wlog(const double *x, double *y, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = wlog(x[i]);
+}
+
+cudaError_t launch_wlog(const double *x, double *y, int n, cudaStream_t st)
+{
+    if (n > 0) k_wlog<<<(n + 255) / 256, 256, 0, counted(st)>>>(x, y, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gather_t(const ChanDev *chans_dev, int n_ch, int n_samples, int n_E, int maxN, PlanDev plan,

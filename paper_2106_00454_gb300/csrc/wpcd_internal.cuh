@@ -291,6 +291,7 @@ int mi_slots_per_sm(int n, int NQ);
 cudaError_t launch_mi_observables(const MiChanDev *chans_dev, int n_ch, int n_samples, int n_I, const double *e_int,
                                   const double *ph, int n_E, const double *e_lab, double *delta, double *sigma,
                                   cudaStream_t st);
+cudaError_t launch_wlog(const double *x, double *y, int n, cudaStream_t st);
 cudaError_t launch_gather_t(const ChanDev *chans_dev, int n_ch, int n_samples, int n_E, int maxN, PlanDev plan,
                             const double *tbin, double *t_out, cudaStream_t st, bool direct = false);
 cudaError_t launch_observables(const ChanDev *chans_dev, int n_ch, int n_samples, int n_E, int maxN, PlanDev plan,
