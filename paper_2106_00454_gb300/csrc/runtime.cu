@@ -38,7 +38,7 @@ using namespace wpcd;
 
 namespace {
 
-constexpr size_t kRefineScratchBytes = (size_t)8 << 30;  // mixed path: refinement scratch per bucket chunk
+constexpr size_t kRefineScratchBytes = (size_t)32 << 30;  // mixed path: refinement scratch per bucket chunk (one chunk per bucket up to ~7000 samples of n = 200)
 constexpr int kRefineIters = 2;                            // FP64 refinement iterations (even)
 constexpr size_t kGraphCache = 64;                         // wpcd_solve keys remembered for CUDA graphs
 
@@ -471,6 +471,7 @@ wpcd_status diag_body(wpcd_ctx *c, Exec &X, VSetH &v, const double *coeffs, int 
         const size_t ref_item = refine_scratch_per_item(n, c->refine_engine);
         const size_t per_item = ref_item + (c_smem ? 0 : jacobi_mixed_c_bytes(n)) + 256;
         int chunk = (int)std::max<size_t>(1, kRefineScratchBytes / (per_item * nw));
+        chunk = std::min(chunk, std::max(1, 65535 / nw));  // the refinement grids put items in y / z (<= 65535)
         chunk = std::min(chunk, nsmp);
         wpcd_status st2 = ws_reserve(c, X, X.ws_ref, per_item * nw * chunk);
         if (st2) return st2;
