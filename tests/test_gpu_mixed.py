@@ -28,8 +28,9 @@ def ctx():
 
 
 def _report(name, worst):
-    out = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(out):
+    """Append the worst errors of a case to $WPCD_REPORT_DIR/mixed_errors.jsonl when that is set."""
+    out = os.environ.get("WPCD_REPORT_DIR", "")
+    if out and os.path.isdir(out):
         with open(os.path.join(out, "mixed_errors.jsonl"), "a") as f:
             f.write(json.dumps({"case": name, **worst}) + "\n")
 
@@ -98,7 +99,7 @@ def test_mixed_eigenvalues_refined(ctx, orc):
         b, C = ctx.eig_get(e32, s, 0, 200)
         # The resolvent sees an eigenvalue error through the SWP bin width it
         # shifts, ~ (e_{s+2} - e_{s-2})/4 for the two interleaved branches;
-        # judged where the requested energies reach (0.5..200 MeV c.m.).  The
+        # checked where the requested energies reach (0.5..200 MeV c.m.).  The
         # refinement deliberately leaves clusters of near-zero eigenvalues
         # (far below 1 MeV) unrotated: T is invariant to rotations inside them.
         idx = np.arange(200)
