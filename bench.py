@@ -30,7 +30,7 @@ from paper_2106_00454_gb300 import inputs as W  # noqa: E402
 
 METRIC = "channel-solves/s and p50/p99 latency at <=1e-3 deg phase error vs plain FP64"
 UNIT = "channel-solves/s"
-FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (no measured FP64 peak in the driver's file)
+FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (MEASURED_PEAKS.json holds no FP64 figure)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA lanes x clock
 JACOBI_MIXED_DRAM_BYTES_1024 = 2.06e9  # k_jacobi_mixed, one step of the 1024-sample batched workload
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
@@ -72,6 +72,12 @@ def dist_init(args):
         backend = "nccl" if args.impl == "wpcd" else "gloo"
         dist.init_process_group(backend)
     return ws, rank, lrank
+
+
+def rank_workload(samples, rank):
+    """This rank's shard of a weak-scaling job: the same channels, meshes and
+    energies on every rank, its own block of parameter samples."""
+    return W.workload_batched(n_samples=samples, sample_seed=W.SEED + 7919 * rank)
 
 
 def barrier(ws):
@@ -253,7 +259,7 @@ def run_wpcd(args, ws, rank, lrank):
     if args.exec == "plain":
         ctx.set_exec(api.EXEC_PLAIN)
     # weak scaling: every rank owns its own block of samples (independent seeds)
-    wl = W.workload_batched(n_samples=args.samples, seed=W.SEED + 7919 * rank)
+    wl = rank_workload(args.samples, rank)
     md = api.Model(ctx, wl)
     S, nch, nE = wl.n_samples, len(wl.channels), len(wl.e_lab)
     cf = torch.tensor(wl.coeffs, dtype=torch.float64, device=dev)

@@ -172,13 +172,18 @@ def workload_all_channels(n_wp: int = 100, jmax: int = 6, n_e: int = 0) -> Workl
 
 
 def workload_batched(n_samples: int = 4096, n_e: int = 128, seed: int = SEED,
-                     nwp_choices=(40, 64, 100)) -> Workload:
-    """Workload 3: 15 channels J <= 4, N_WP per channel from {40, 64, 100}."""
+                     nwp_choices=(40, 64, 100), sample_seed: int | None = None) -> Workload:
+    """Workload 3: 15 channels J <= 4, N_WP per channel from {40, 64, 100}.
+
+    `seed` fixes the channel set's N_WP draw (and, by default, the parameter
+    samples); `sample_seed` draws only the parameter samples, so that shards of
+    one job (one per GPU) solve the same channels on different samples."""
     chs = np_channels(4, extra_1s0_tz=True)
     rng = np.random.default_rng(seed + 1)
     nwp = [int(x) for x in rng.choice(np.array(nwp_choices), size=len(chs))]
+    cseed = seed if sample_seed is None else sample_seed
     return Workload(f"batched_{n_samples}x15ch", chs, nwp, GEN_YUKAWA, YUKAWA_PARAMS.copy(),
-                    N_TERMS_YUKAWA, coefficient_samples(n_samples, seed), lab_energies(n_e))
+                    N_TERMS_YUKAWA, coefficient_samples(n_samples, cseed), lab_energies(n_e))
 
 
 def workload_mixed(n_samples: int = 16384, n_wp: int = 150, n_e: int = 128, seed: int = SEED) -> Workload:
