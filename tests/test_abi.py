@@ -55,3 +55,26 @@ def test_create_rejects_bad_arguments_without_device(lib):
     assert f(None, 0, 0, None) == -1   # null out pointer
     h = ctypes.c_void_p()
     assert f(ctypes.byref(h), -1, 0, None) == -1  # bad device
+
+
+def test_null_context_is_rejected_without_device(lib):
+    """Every entry point that takes a context returns WPCD_ERR_ARG (or a zero
+    count) for a null one, before touching the device."""
+    from paper_2106_00454_gb300 import _lib
+    skip = {"wpcd_create", "wpcd_strerror", "wpcd_channel_solve_noalloc", "wpcd_destroy", "wpcd_release_result"}
+    zero_ok = {"wpcd_kernel_launches", "wpcd_bytes_in_use", "wpcd_tuning"}
+    checked = 0
+    for name, (res, argtypes) in _lib._SIG.items():
+        if name in skip or not argtypes or argtypes[0] is not ctypes.c_void_p:
+            continue
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, argtypes
+        args = [t() if t is not ctypes.c_void_p and not isinstance(t, type(ctypes.POINTER(ctypes.c_int)))
+                else None for t in argtypes]
+        got = f(*args)
+        if name in zero_ok:
+            assert got == 0, name
+        else:
+            assert got == -1, (name, got)
+        checked += 1
+    assert checked >= 25
