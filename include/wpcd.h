@@ -240,7 +240,9 @@ wpcd_status wpcd_solve(wpcd_ctx *ctx, int vset_id, const double *coeffs_dev, int
 
 /* Same as wpcd_solve with every buffer on the host: inputs are copied to the
  * device and outputs back inside the call, which synchronises and returns the
- * device status as wpcd_sync would. */
+ * device status as wpcd_sync would.  The copies go straight from and into the
+ * caller's buffers; page-locked (pinned) buffers move at the link's full rate,
+ * pageable ones are accepted too. */
 wpcd_status wpcd_solve_host(wpcd_ctx *ctx, int vset_id, const double *coeffs_host, int n_samples,
                             const double *e_lab_host, int n_E, wpcd_precision prec, wpcd_resolvent res,
                             double *t_out_host, double *delta_host, double *sigma_host);
