@@ -80,11 +80,11 @@ cudaError_t launch_plan(const ChanDev *chans_dev, int n_ch, int maxN, const doub
 // F = 1), u = (m - F) / F with |u| <= 2^-9, and
 //     log x = k log 2 + log F + log1p(u),
 // log 2 and log F as double-double table values (logtab.h) and log1p(u) from
-// its series through u^6 (truncation |u|^7 / 7 < 2^-65).  About 1 ulp; the
-// resolvent evaluates (m + 1)(n + 1) of these per solve, so the 13 FP64
-// operations here instead of the library routine's longer sequence matter on
-// GB300's FP64 pipe.  Zero, subnormal, infinite and NaN arguments take the
-// library log.
+// its series through u^6 (truncation |u|^7 / 7 < 2^-65).  Below 1 ulp in a
+// CPU emulation with exact FMA; 13 FP64 operations.  The resolvent evaluates
+// (m + 1)(n + 1) of these per solve on GB300's narrow FP64 pipe; against the
+// library log this took the T phase of a 4096-sample step from 28.9 to 21.9 ms.
+// Zero, subnormal, infinite and NaN arguments take the library log.
 __device__ __forceinline__ double wlog(double x)
 {
     const long long b = __double_as_longlong(x);
