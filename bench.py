@@ -157,6 +157,25 @@ def measured_peak(key, fallback):
         return fallback, "fallback"
 
 
+def host_cpu():
+    """The host CPU as /proc/cpuinfo names it, with the machine type and logical CPU count."""
+    import platform
+    name = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key, _, val = line.partition(":")
+                key = key.strip().lower()
+                if key in ("model name", "cpu model", "hardware") and val.strip():
+                    name = val.strip()
+                    break
+                if key == "cpu part" and not name:  # Arm: the part number (0xd4f = Neoverse V2)
+                    name = "Arm part " + val.strip()
+    except OSError:
+        pass
+    return f"{name or platform.processor() or 'unknown'} ({platform.machine()}, {os.cpu_count()} logical CPUs)"
+
+
 def cpu_baseline(wl, n_samples, steps=1):
     """Time the FP64 oracle on a bounded sample of the workload (host cores)."""
     import oracle
@@ -173,7 +192,7 @@ def cpu_baseline(wl, n_samples, steps=1):
         assert rc == 0
     sec = statistics.median(times)
     return {"value": n_samples * len(wl.channels) / sec, "unit": UNIT, "cores": oracle.max_threads(),
-            "kind": "oracle",
+            "kind": "oracle", "cpu": host_cpu(),
             "sample": f"first {n_samples} of {wl.n_samples} samples x {len(wl.channels)} channels, "
                       f"{len(wl.e_lab)} energies (projection excluded, as on the GPU)"}, sec
 
