@@ -178,7 +178,10 @@ wpcd_status wpcd_vset_get(wpcd_ctx *ctx, int vset_id, int channel, double *out_h
  * channel), then H = C D C^T with eigenvalues ascending.  coeffs_dev:
  * [n_samples][n_terms-1] FP64 (may be NULL when n_terms == 1).  The eigenpairs
  * stay on the device under the returned eig handle.  prec: WPCD_PREC_FP64 or
- * WPCD_PREC_MIXED (see wpcd_precision).
+ * WPCD_PREC_MIXED (see wpcd_precision).  Every size uses the parallel cyclic
+ * Jacobi method (App. C): matrices that fit one CTA's shared memory (FP64 up to
+ * n ~ 230, FP32 up to n ~ 310) are held there; larger ones, up to n = 1024, are
+ * held in global memory (L2-resident while a CTA works on them).
  * Per-solve convergence status: wpcd_diag_status.
  * Errors: WPCD_ERR_ARG, WPCD_ERR_HANDLE, WPCD_ERR_NOMEM, WPCD_ERR_BUDGET, WPCD_ERR_CUDA. */
 wpcd_status wpcd_diag(wpcd_ctx *ctx, int vset_id, const double *coeffs_dev, int n_samples,
@@ -411,8 +414,13 @@ wpcd_status wpcd_serve_start(wpcd_ctx *ctx, const wpcd_channel *channels, int n_
 /* Drain the queue, stop the worker and free the serving state. */
 wpcd_status wpcd_serve_stop(wpcd_ctx *ctx);
 /* Copy a request (the caller may reuse its buffers afterwards).  Errors:
- * WPCD_ERR_ARG (no server, unserved N_WP, bad energies, a matrix larger than
- * the precision's eigensolver holds), WPCD_ERR_BUDGET (admission refused). */
+ * WPCD_ERR_ARG (no server, unserved N_WP, an energy that is not positive or
+ * whose momentum is not below the mesh's top boundary -- checked here, with the
+ * energy plan's own test, so that it never reaches a batch), WPCD_ERR_BUDGET
+ * (admission refused).  A result's status is its own: WPCD_ERR_NOCONVERGE when
+ * one of its solves hit the sweep cap, whatever the other requests of its
+ * batch did; an error of the batch's launch or layout fails every request of
+ * that batch. */
 wpcd_status wpcd_submit(wpcd_ctx *ctx, const wpcd_request *req, uint64_t *ticket);
 /* WPCD_OK and the result, WPCD_ERR_NOTREADY while in flight, WPCD_ERR_HANDLE for an unknown ticket. */
 wpcd_status wpcd_poll(wpcd_ctx *ctx, uint64_t ticket, wpcd_result *out);
@@ -448,7 +456,10 @@ wpcd_status wpcd_serve_stats(wpcd_ctx *ctx, unsigned long long *completed, unsig
  * problem whose intermediates do not fit (roughly n_samples * (K n_wp)^2 * 8
  * bytes plus small terms) is rejected with WPCD_ERR_ARG.  The first call on
  * each device looks up the array's device address with that device current;
- * make that first call before any stream capture.  All calls share the array:
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process: after cudaDeviceReset (or anything else that
+ * recreates the device's primary context) the array may move, so do not call
+ * this entry point on a device that was reset.  All calls share the array:
  * calls whose work overlaps on the GPU race on it and must be serialised by
  * the caller (one stream, or events).
  * Errors: WPCD_ERR_ARG, WPCD_ERR_CUDA. */

@@ -11,7 +11,11 @@
 // its inputs and outputs.
 //
 // The array is shared by every call: calls whose work overlaps on the GPU
-// (different streams, or different host threads) race on it.  A call leaves
+// (different streams, or different host threads) race on it.  Its device
+// address is looked up once per device and kept: after cudaDeviceReset (or
+// anything else that tears down and recreates the device's primary context)
+// the module is loaded again and the array may move, so a process that resets
+// a device must not call this entry point on it afterwards.  A call leaves
 // its intermediates behind; each call rewrites everything it later reads, so
 // nothing needs clearing between calls.
 #include <mutex>
@@ -75,7 +79,10 @@ extern "C" wpcd_status wpcd_channel_solve_noalloc(int n_wp, int mesh_kind, doubl
     if (ch.coupled && (ch.s != 1 || ch.J < 1 || ch.l != ch.J - 1 || ch.lp != ch.J + 1)) return WPCD_ERR_ARG;
     if (!ch.coupled && ch.l != ch.lp) return WPCD_ERR_ARG;
     const int K = ch.coupled ? 2 : 1, N = n_wp, n = K * N, Q = n_quad;
-    if (jacobi_smem_bytes(n, false) > 227 * 1024) return WPCD_ERR_ARG;
+    // matrices above one CTA's shared memory take the global-memory Jacobi
+    // kernel with one scratch slot (its matrix and eigenvector copies) here
+    const bool big = !jacobi_fits_smem(n, true);
+    if (big && n > jacobi_big_max_n()) return WPCD_ERR_ARG;
 
     // carve the scratch array (every piece 256-byte aligned)
     size_t off = 0;
@@ -96,6 +103,7 @@ extern "C" wpcd_status wpcd_channel_solve_noalloc(int n_wp, int mesh_kind, doubl
     const size_t o_cnt = take(sizeof(int)), o_plist = take(sizeof(int) * N), o_pE = take(sizeof(double) * n_E);
     const size_t o_tbin = take(sizeof(double) * (size_t)n_samples * N * 8);
     const size_t o_phbin = take(sizeof(double) * (size_t)n_samples * N * 3);
+    const size_t o_big = big ? take(jacobi_big_scratch_bytes(n, true)) : 0;
     if (off > kScratchBytes) return WPCD_ERR_ARG;  // problem larger than the fixed scratch array
 
     void *base_v = nullptr;
@@ -147,7 +155,11 @@ extern "C" wpcd_status wpcd_channel_solve_noalloc(int n_wp, int mesh_kind, doubl
     CKN(cudaGetLastError());
     CKN(launch_gauss_legendre(Q, glx, glw, st));
     CKN(launch_mesh(N, mesh_kind, alpha_fm, t, kmax_fm, Q, wp_kind, glx, glw, kb, kq, wq, h0, st));
-    CKN(launch_jacobi_f64(chan, list, 1, n_samples, 0, n_terms, cf, n, eps, C, status, 1, status_dev, st));
+    if (big)
+        CKN(launch_jacobi_big(true, chan, list, 1, n_samples, 0, n_terms, cf, n, base + o_big, 1, eps, C, nullptr,
+                              nullptr, nullptr, status, 1, status_dev, st));
+    else
+        CKN(launch_jacobi_f64(chan, list, 1, n_samples, 0, n_terms, cf, n, eps, C, status, 1, status_dev, st));
     CKN(launch_plan(chan, 1, N, e_lab_dev, n_E, plan, status_dev, st));
     CKN(launch_tbin(chan, 1, n_samples, n_terms, cf, eps, C, plan, N, n_E, tbin, phbin, status_dev, st, false,
                     WPCD_AVG_FREE_BIN));

@@ -431,6 +431,55 @@ wpcd_status diag_prep(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, int S, int pr
     return WPCD_OK;
 }
 
+// A size bucket whose matrices exceed one CTA's shared memory: the Jacobi
+// kernel with the matrix and eigenvectors in global memory (eig_big.cu), one
+// scratch slot per resident CTA; the mixed path then refines as for the other
+// sizes.
+wpcd_status run_bucket_big(wpcd_ctx *c, Exec &X, VSetH &v, EigH &e, const double *cf, const int *work, int nw,
+                           int nsmp, int smp0, int n, int prec)
+{
+    (void)v;
+    const bool f64 = prec == WPCD_PREC_FP64;
+    if (n > jacobi_big_max_n()) return WPCD_ERR_ARG;
+    if (!c->n_sm) cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    const int occ = std::max(1, jacobi_big_occupancy(n, f64));
+    const size_t slot_b = (jacobi_big_scratch_bytes(n, f64) + 255) & ~(size_t)255;
+    if (f64) {
+        const int items = nsmp * nw;
+        const int slots = std::max(1, std::min(items, c->n_sm * occ));
+        wpcd_status st = ws_reserve(c, X, X.ws_ref, slot_b * slots);
+        if (st) return st;
+        Launch L(c, X, WPCD_PHASE_EIGEN);
+        CK(launch_jacobi_big(true, e.cd_dev, work, nw, nsmp, smp0, v.n_terms, cf, n, X.ws_ref.p, slots, e.eps, e.C,
+                             nullptr, nullptr, nullptr, e.status, v.n_ch, X.err, X.stream));
+        return WPCD_OK;
+    }
+    const size_t ref_item = refine_scratch_per_item(n, c->refine_engine);
+    int chunk = (int)std::max<size_t>(1, kRefineScratchBytes / (ref_item * nw));
+    chunk = std::min(chunk, std::max(1, 65535 / nw));  // the refinement grids put items in y / z (<= 65535)
+    chunk = std::min(chunk, nsmp);
+    const int slots = std::max(1, std::min(chunk * nw, c->n_sm * occ));
+    const size_t ref_b = (ref_item * nw * chunk + 255) & ~(size_t)255;
+    wpcd_status st = ws_reserve(c, X, X.ws_ref, ref_b + slot_b * slots);
+    if (st) return st;
+    unsigned char *base = static_cast<unsigned char *>(X.ws_ref.p);
+    double *Xs = reinterpret_cast<double *>(base);
+    for (int s0 = 0; s0 < nsmp; s0 += chunk) {
+        const int ns = std::min(chunk, nsmp - s0);
+        {
+            Launch L(c, X, WPCD_PHASE_EIGEN);
+            // X, H and lambda in the layout of launch_refine (blocks 0, 1 and the lambda block)
+            CK(launch_jacobi_big(false, e.cd_dev, work, nw, ns, smp0 + s0, v.n_terms, cf, n, base + ref_b, slots,
+                                 nullptr, nullptr, Xs + (size_t)5 * ns * nw * n * n, Xs,
+                                 Xs + (size_t)ns * nw * n * n, e.status, v.n_ch, X.err, X.stream));
+        }
+        Launch L(c, X, WPCD_PHASE_REFINE);
+        CK(launch_refine(e.cd_dev, work, nw, ns, smp0 + s0, n, v.n_terms, cf, base, e.eps, e.C, kRefineIters,
+                         c->refine_engine, X.stream, X.err));
+    }
+    return WPCD_OK;
+}
+
 // The parameter sum + eigensolve of the batch diag_prep set up (device-only
 // work on X.stream: capturable).  coeffs: device, [S][n_terms - 1].
 wpcd_status diag_body(wpcd_ctx *c, Exec &X, VSetH &v, const double *coeffs, int S, int prec, EigH &e)
@@ -445,6 +494,7 @@ wpcd_status diag_body(wpcd_ctx *c, Exec &X, VSetH &v, const double *coeffs, int 
     // MIXED: per bucket, in sample chunks sized to the refinement scratch, an FP32
     // Jacobi launch followed by two FP64 refinement iterations.
     auto run_bucket = [&](const int *work, int nw, int nsmp, int smp0, int n) -> wpcd_status {
+        if (!jacobi_fits_smem(n, prec == WPCD_PREC_FP64)) return run_bucket_big(c, X, v, e, cf, work, nw, nsmp, smp0, n, prec);
         const int threads = pick_threads(c, X, n, prec, nw, nsmp, [&](int th, int ns) {
             if (prec == WPCD_PREC_FP64)
                 return launch_jacobi_f64(e.cd_dev, work, nw, ns, smp0, v.n_terms, cf, n, e.eps, e.C, e.status, v.n_ch,
@@ -1518,6 +1568,7 @@ struct ModelS {
     int n_wp = 0, vset_id = -1;
     std::vector<int> mesh_ids;
     VSetH *v = nullptr;
+    double k_top = 0.0;  // kb[N] of its mesh: energies must have p(E) below it
 };
 
 }  // namespace
@@ -1572,7 +1623,8 @@ wpcd_status launch_batch(Server *sv, Slot &sl)
     sl.nt = (size_t)S * v.n_ch * nE * 8;
     sl.nd = (size_t)S * v.n_ch * nE * 3;
     sl.ns = (size_t)S * nE;
-    const size_t out_bytes = (sl.nt + sl.nd + sl.ns) * 8 + 8;
+    // outputs, the slot's device status word, then the per-solve eigensolver status [S][n_ch]
+    const size_t out_bytes = (sl.nt + sl.nd + sl.ns) * 8 + 8 + (size_t)S * v.n_ch * 4;
     wpcd_status st;
     if ((st = ws_reserve(c, X, X.ws_in, in_bytes)) || (st = ws_reserve(c, X, X.ws_out, out_bytes))) return st;
     if (sl.pin_in_n < in_bytes) {
@@ -1604,6 +1656,8 @@ wpcd_status launch_batch(Server *sv, Slot &sl)
     if ((st = run_tbin(c, X, v, X.eig, de, nE, dn, plan))) return st;
     if ((st = run_outputs(c, X, v, X.eig, nE, plan, dout, dout + sl.nt, dout + sl.nt + sl.nd))) return st;
     CK(cudaMemcpyAsync(dout + sl.nt + sl.nd + sl.ns, X.err, sizeof(int), cudaMemcpyDeviceToDevice, X.stream));
+    CK(cudaMemcpyAsync(dout + sl.nt + sl.nd + sl.ns + 1, X.eig.status, sizeof(int) * S * v.n_ch,
+                       cudaMemcpyDeviceToDevice, X.stream));
     CK(cudaMemsetAsync(X.err, 0, sizeof(int), X.stream));
     CK(cudaMemcpyAsync(sl.pin_out, dout, out_bytes, cudaMemcpyDeviceToHost, X.stream));
     sl.done.store(0);
@@ -1617,7 +1671,8 @@ void finish_batch(Server *sv, Slot &sl)
     const ModelS &m = sv->models[sl.reqs[0]->model];
     const int nch = m.v->n_ch;
     const double *T = sl.pin_out, *D = T + sl.nt, *G = D + sl.nd;
-    int derr = *reinterpret_cast<const int *>(G + sl.ns);
+    const int derr = *reinterpret_cast<const int *>(G + sl.ns);
+    const int *eig_st = reinterpret_cast<const int *>(G + sl.ns + 1);  // [S][n_ch], < 0: not converged
     const auto now = Clock::now();
     std::lock_guard<std::mutex> lk(sv->mu);
     for (int k = 0; k < S; ++k) {
@@ -1631,7 +1686,14 @@ void finish_batch(Server *sv, Slot &sl)
                    sizeof(double) * 3 * r.n_E);
         }
         memcpy(r.sigma.data(), G + (size_t)k * nE, sizeof(double) * r.n_E);
-        r.status = derr == 0 ? WPCD_OK : (derr == kDevNoConverge ? WPCD_ERR_NOCONVERGE : WPCD_ERR_ARG);
+        // each request's own status: its solves' convergence; the slot's error word
+        // only for errors that are not a property of one sample (energies outside
+        // the mesh are refused at submission and never reach a batch)
+        bool conv = true;
+        for (int ch = 0; ch < nch; ++ch) conv &= eig_st[(size_t)k * nch + ch] >= 0;
+        if (!conv) r.status = WPCD_ERR_NOCONVERGE;
+        else if (derr == 0 || derr == kDevNoConverge) r.status = WPCD_OK;
+        else r.status = derr == kDevTimeout ? WPCD_ERR_TIMEOUT : (derr == kDevBadSize ? WPCD_ERR_CUDA : WPCD_ERR_ARG);
         r.latency_us = std::chrono::duration<double, std::micro>(now - r.t_submit).count();
         r.state = 2;
         sv->queued_bytes -= r.bytes;
@@ -1767,6 +1829,8 @@ wpcd_status wpcd_serve_start(wpcd_ctx *c, const wpcd_channel *channels, int n_ch
         {
             std::lock_guard<std::mutex> lk(c->mu);
             m.v = find(c, m.vset_id, kVSet)->vset.get();
+            const MeshH &mh = *find(c, mid, kMesh)->mesh;
+            CK(cudaMemcpy(&m.k_top, mh.kb + mh.N, sizeof(double), cudaMemcpyDeviceToHost));
         }
         sv->models.push_back(m);
     }
@@ -1802,13 +1866,13 @@ wpcd_status wpcd_submit(wpcd_ctx *c, const wpcd_request *rq, uint64_t *ticket)
     for (size_t k = 0; k < sv->models.size(); ++k)
         if (sv->models[k].n_wp == rq->n_wp) model = (int)k;
     if (model < 0) return WPCD_ERR_ARG;
-    // the eigensolver of the requested precision must hold the largest matrix of the model
-    const int maxn = sv->models[model].v->maxn;
-    if (rq->prec == WPCD_PREC_FP64 ? jacobi_smem_bytes(maxn, false) > 227 * 1024
-                                   : jacobi_mixed_smem_bytes(maxn, false) > 227 * 1024)
-        return WPCD_ERR_ARG;
-    for (int e = 0; e < rq->n_E; ++e)
-        if (!(rq->e_lab[e] > 0.0)) return WPCD_ERR_ARG;
+    if (sv->models[model].v->maxn > jacobi_big_max_n()) return WPCD_ERR_ARG;
+    // the energy plan's test, on the host: a request with an energy outside the
+    // mesh is refused here instead of failing the batch it would join
+    for (int e = 0; e < rq->n_E; ++e) {
+        const double T = rq->e_lab[e];
+        if (!(T > 0.0) || !(std::sqrt(kMn * T / 2.0) / kHbarc < sv->models[model].k_top)) return WPCD_ERR_ARG;
+    }
     auto r = std::make_shared<Req>();
     r->model = model;
     r->prec = rq->prec;

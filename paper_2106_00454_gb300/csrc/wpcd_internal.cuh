@@ -247,6 +247,15 @@ cudaError_t launch_jacobi_mixed(const ChanDev *chans_dev, const int *work_ch_dev
                                 int sample0, int n_terms, const double *coeffs, int n, double *lam_s, double *X_s,
                                 float *Cf_s, double *H_s, int *status_all, int n_ch_total, int *err, cudaStream_t st,
                                 int threads = 256);
+// Matrices above one CTA's shared memory: Jacobi with A and C in global memory.
+bool jacobi_fits_smem(int n, bool f64);
+int jacobi_big_max_n();
+int jacobi_big_occupancy(int n, bool f64);
+size_t jacobi_big_scratch_bytes(int n, bool f64);
+cudaError_t launch_jacobi_big(bool f64, const ChanDev *chans_dev, const int *work_ch_dev, int n_work_ch,
+                              int n_samples, int sample0, int n_terms, const double *coeffs, int n, void *scratch,
+                              int slots, double *eps_all, double *C_all, double *lam_s, double *X_s, double *H_s,
+                              int *status_all, int n_ch_total, int *err, cudaStream_t st);
 constexpr int kOzDigits = 6;  // balanced 8-bit digits per operand of the Ozaki products
 size_t oz_slice_elems(int n);
 int oz_kpad(int n);

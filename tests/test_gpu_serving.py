@@ -111,3 +111,57 @@ def test_admission_refusal_and_timeout():
     finally:
         c.serve_stop()
         c.close()
+
+
+def test_energy_above_mesh_refused_and_mix_unaffected(server):
+    """A request with an energy above the mesh's top (p(E) >= 8 fm^-1, T_lab > 5.3
+    GeV) is refused at submission, so the good requests around it in the same
+    burst still complete with WPCD_OK and the same results as alone."""
+    c0, e0, nw0 = _req(11, 32)
+    alone = server.wait(server.submit(c0, e0, nw0, 1))
+    assert alone.status == 0
+    bad_e = np.concatenate([e0[:-1], [6000.0]])
+    tickets = [server.submit(*_req(300 + k, 32), 1) for k in range(10)]
+    assert server.submit(c0, bad_e, nw0, 1, raise_on_error=False) == -1
+    tm = server.submit(c0, e0, nw0, 1)
+    tickets += [server.submit(*_req(320 + k, 32), 1) for k in range(10)]
+    mixed = server.wait(tm)
+    assert mixed.status == 0
+    _same(alone, mixed)
+    for tk in tickets:
+        assert server.wait(tk).status == 0
+        server.release_result(tk)
+
+
+def test_served_nwp256_matches_oracle(orc):
+    """N_WP = 256 (coupled blocks 512 x 512, the global-memory Jacobi) served on
+    the mixed path and in FP64, against the oracle at each path's tolerances."""
+    from parity_util import TOL_MIXED_DELTA_DEG, TOL_MIXED_SIGMA_MB
+    chans = [CHANNELS[0], CHANNELS[4]]  # 1S0 (256 x 256) and 3S1-3D1 (512 x 512)
+    c = _ctx()
+    try:
+        c.serve_start(chans, W.GEN_YUKAWA, W.YUKAWA_PARAMS, W.N_TERMS_YUKAWA, [256], max_batch=8, n_slots=2)
+        coeffs, e_lab, _ = _req(21, 256)
+        r64 = c.wait(c.submit(coeffs, e_lab, 256, 0), 600000)
+        rmx = c.wait(c.submit(coeffs, e_lab, 256, 1), 600000)
+        assert r64.status == 0 and rmx.status == 0
+        meshes = [orc.Mesh(256) for _ in chans]
+        Vts = [orc.project_channel(m, ch.astuple(), W.GEN_YUKAWA, W.YUKAWA_PARAMS, W.N_TERMS_YUKAWA)
+               for m, ch in zip(meshes, chans)]
+        ot, od, os_, rc = orc.batch([ch.astuple() for ch in chans], meshes, Vts, coeffs[None], e_lab)
+        assert rc == 0
+        for ci, ch in enumerate(chans):
+            k = 2 if ch.coupled else 1
+            scale = np.max(np.abs(ot[0, ci]))
+            assert np.max(np.abs(r64.T[ci] - ot[0, ci])) <= TOL_T * scale
+            assert np.max(np.abs(dphase(r64.delta[ci, :, :k], od[0, ci, :, :k]))) <= TOL_DELTA_DEG
+            assert np.max(np.abs(dphase(rmx.delta[ci, :, :k], od[0, ci, :, :k]))) <= TOL_MIXED_DELTA_DEG
+            if ch.coupled:
+                assert np.max(np.abs(r64.delta[ci, :, 2] - od[0, ci, :, 2])) <= TOL_DELTA_DEG
+                assert np.max(np.abs(rmx.delta[ci, :, 2] - od[0, ci, :, 2])) <= TOL_MIXED_DELTA_DEG
+        # sigma here sums only the two served channels, on both sides
+        assert np.max(np.abs(r64.sigma - os_[0]) / os_[0]) <= TOL_SIGMA_REL
+        assert np.max(np.abs(rmx.sigma - os_[0])) <= TOL_MIXED_SIGMA_MB
+    finally:
+        c.serve_stop()
+        c.close()
