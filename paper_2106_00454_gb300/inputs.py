@@ -186,11 +186,16 @@ def workload_batched(n_samples: int = 4096, n_e: int = 128, seed: int = SEED,
                     N_TERMS_YUKAWA, coefficient_samples(n_samples, cseed), lab_energies(n_e))
 
 
-def workload_mixed(n_samples: int = 16384, n_wp: int = 150, n_e: int = 128, seed: int = SEED) -> Workload:
-    """Workload 4: 20 channels J <= 6, N_WP = 150, 16384 samples."""
+def workload_mixed(n_samples: int = 16384, n_wp: int = 150, n_e: int = 128, seed: int = SEED,
+                   sample_seed: int | None = None) -> Workload:
+    """Workload 4: 20 channels J <= 6, N_WP = 150, 16384 samples.
+
+    `sample_seed` draws the parameter samples of one shard of a multi-GPU job
+    (default: `seed`, the single-GPU workload)."""
     chs = np_channels(6)
+    cseed = seed if sample_seed is None else sample_seed
     return Workload(f"mixed_{n_samples}x20ch_nwp{n_wp}", chs, [n_wp] * len(chs), GEN_YUKAWA,
-                    YUKAWA_PARAMS.copy(), N_TERMS_YUKAWA, coefficient_samples(n_samples, seed),
+                    YUKAWA_PARAMS.copy(), N_TERMS_YUKAWA, coefficient_samples(n_samples, cseed),
                     lab_energies(n_e))
 
 

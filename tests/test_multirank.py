@@ -28,7 +28,8 @@ def _rank(rank, ws, port, q):
     import bench
     import torch.distributed as dist
     try:
-        args = types.SimpleNamespace(impl="reference", samples=6, gpus=ws, steps=1, warmup=0, cpu_samples=1)
+        args = types.SimpleNamespace(impl="reference", samples=6, gpus=ws, steps=1, warmup=0, cpu_samples=1,
+                                     ref_samples=1, workload="config4")
         got_ws, r, _ = bench.dist_init(args)  # the oracle leg's backend: gloo
         wl = bench.rank_workload(6, r)
         step_max = bench.max_over_ranks(got_ws, 10.0 + 5.0 * r)
@@ -69,6 +70,6 @@ def test_two_cpu_ranks_shard_by_sample():
     assert m0 == m1 == 15.0                    # the maximum over ranks, on every rank
     assert nwp0 == nwp1 and e0 == e1           # the same channel set and energies
     assert not np.allclose(np.array(c0), np.array(c1))  # different parameter samples
-    single = W.workload_batched(n_samples=6)
+    single = W.workload_mixed(n_samples=6)
     assert nwp0 == single.nwp and np.array_equal(np.array(c0), single.coeffs)
     assert skipped is None
