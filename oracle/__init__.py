@@ -65,6 +65,9 @@ def lib():
                 "or_phases_from_S": (None, [i, _dp, _dp]),
                 "or_S_from_T": (None, [i, d, _dp, _dp]),
                 "or_channel_solve": (i, [i, _dp, i, i, i, _dp, _dp, i, _dp, _dp, _dp, _ip]),
+                "or_channel_solve_ip": (i, [i, _dp, i, i, i, _dp, _dp, i, d, _dp, _dp, _dp, _ip]),
+                "or_interp_phase_ip": (None, [i, _dp, _dp, i, d, d, _dp]),
+                "or_batch_ip": (i, [i, _ip, _ip, _lp, _dp, i, i, _lp, _dp, i, _dp, i, _dp, i, d, _dp, _dp, _dp, i]),
                 "or_channel_solve_point": (i, [i, _dp, i, i, i, _dp, _dp, i, _dp, _dp, _dp]),
                 "or_interp_phase": (None, [i, _dp, _dp, i, d, _dp]),
                 "or_sigma_term": (d, [i, i, _dp]),
@@ -238,10 +241,16 @@ def S_from_K(K, p, Km):
     return S.reshape(K, K)
 
 
-def interp_phase(mesh: Mesh, ph, K, p):
+def interp_phase(mesh: Mesh, ph, K, p, frac=0.5):
+    """Phases interpolated linearly in p between the interpolation points of
+    consecutive bins, (1 - frac) k_i + frac k_{i+1} (Sec. 5.1.1; frac = 0.5:
+    the midpoints)."""
     ph = _f64(ph)
     out = np.zeros(3)
-    lib().or_interp_phase(mesh.N, _d(mesh.kb), _d(ph), K, float(p), _d(out))
+    if frac == 0.5:
+        lib().or_interp_phase(mesh.N, _d(mesh.kb), _d(ph), K, float(p), _d(out))
+    else:
+        lib().or_interp_phase_ip(mesh.N, _d(mesh.kb), _d(ph), K, float(p), float(frac), _d(out))
     return out
 
 
@@ -258,7 +267,7 @@ def sigma_prefactor_mb(p):
 AVG_FREE_BIN, AVG_SWP_INDEX, POINT = 0, 1, 2  # resolvent modes
 
 
-def channel_solve(mesh: Mesh, K, Vt, c, wp_kind=0, mode=AVG_FREE_BIN):
+def channel_solve(mesh: Mesh, K, Vt, c, wp_kind=0, mode=AVG_FREE_BIN, frac=0.5):
     """One channel-solve at every free bin.
 
     mode: AVG_FREE_BIN (resolvent averaged over the free bin) or AVG_SWP_INDEX
@@ -275,8 +284,8 @@ def channel_solve(mesh: Mesh, K, Vt, c, wp_kind=0, mode=AVG_FREE_BIN):
     ph = np.zeros((N, 3))
     eps = np.zeros(n)
     sweeps = ctypes.c_int()
-    rc = lib().or_channel_solve(N, _d(mesh.kb), wp_kind, K, n_terms, _d(Vt), _d(c), int(mode),
-                                Tc.ctypes.data_as(_dp), _d(ph), _d(eps), ctypes.byref(sweeps))
+    rc = lib().or_channel_solve_ip(N, _d(mesh.kb), wp_kind, K, n_terms, _d(Vt), _d(c), int(mode), float(frac),
+                                   Tc.ctypes.data_as(_dp), _d(ph), _d(eps), ctypes.byref(sweeps))
     return Tc, ph, eps, rc
 
 
@@ -306,7 +315,7 @@ def mi_kmatrix(gen, gp, ch, n_terms, c, p, NQ=96, cmap=1.0):
     return Km.reshape(K, K)
 
 
-def batch(channels, meshes, Vts, coeffs, e_lab, wp_kind=0, n_threads=0, mode=AVG_FREE_BIN):
+def batch(channels, meshes, Vts, coeffs, e_lab, wp_kind=0, n_threads=0, mode=AVG_FREE_BIN, frac=0.5):
     """Every (sample, channel) solve plus interpolation and sigma_tot.
 
     channels: list of 6-tuples (s, J, l, lp, coupled, tz); meshes: one Mesh per
@@ -328,9 +337,13 @@ def batch(channels, meshes, Vts, coeffs, e_lab, wp_kind=0, n_threads=0, mode=AVG
     t_out = np.zeros((S, n_ch, nE, 2, 2), dtype=np.complex128)
     delta = np.zeros((S, n_ch, nE, 3))
     sigma = np.zeros((S, nE))
-    rc = lib().or_batch(n_ch, _i(chdesc), _i(nwp), kb_off.ctypes.data_as(_lp), _d(kb_all), wp_kind, n_terms,
-                        vt_off.ctypes.data_as(_lp), _d(vt_all), S, _d(coeffs), nE, _d(e_lab), int(mode),
-                        t_out.ctypes.data_as(_dp), _d(delta), _d(sigma), int(n_threads))
+    args = (n_ch, _i(chdesc), _i(nwp), kb_off.ctypes.data_as(_lp), _d(kb_all), wp_kind, n_terms,
+            vt_off.ctypes.data_as(_lp), _d(vt_all), S, _d(coeffs), nE, _d(e_lab), int(mode))
+    outs = (t_out.ctypes.data_as(_dp), _d(delta), _d(sigma), int(n_threads))
+    if frac == 0.5:
+        rc = lib().or_batch(*args, *outs)
+    else:  # interpolation point at fraction frac of each bin (Sec. 5.1.1)
+        rc = lib().or_batch_ip(*args, float(frac), *outs)
     return t_out, delta, sigma, rc
 
 

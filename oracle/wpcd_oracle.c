@@ -585,8 +585,28 @@ void or_S_from_T(int K, double p, const double complex *T, double complex *S)
 /*          or a negative code (-1 no convergence, -2 bad branch sizes,       */
 /*          -4 mode 1 on a coupled channel or with a bound state).            */
 /* ------------------------------------------------------------------------- */
+/* Sec. 5.1.1, Eq. "interpolation point": the point of free bin i (boundaries */
+/* k_i < k_{i+1}) at which its T is converted to the continuum and its phase  */
+/* placed for the interpolation, q = k_i + (n/m)(k_{i+1} - k_i), written as   */
+/* the weighted average (1 - f) k_i + f k_{i+1} with f = n/m; f = 1/2 is the  */
+/* bin midpoint (0.5 k_i + 0.5 k_{i+1} is then exactly 0.5 (k_i + k_{i+1})).  */
+static double ip_point(const double *kb, int i, double f) { return (1.0 - f) * kb[i] + f * kb[i + 1]; }
+
+int or_channel_solve_ip(int N, const double *kb, int wp_kind, int K, int n_terms, const double *Vt,
+                        const double *c, int mode, double frac, double complex *Tc, double *ph, double *eps_out,
+                        int *sweeps_out);
+
 int or_channel_solve(int N, const double *kb, int wp_kind, int K, int n_terms, const double *Vt,
                      const double *c, int mode, double complex *Tc, double *ph, double *eps_out, int *sweeps_out)
+{
+    return or_channel_solve_ip(N, kb, wp_kind, K, n_terms, Vt, c, mode, 0.5, Tc, ph, eps_out, sweeps_out);
+}
+
+/* or_channel_solve with the conversion point of each bin at fraction frac of */
+/* the bin (0 < frac < 1; 0.5 = the midpoint of reading G18).                 */
+int or_channel_solve_ip(int N, const double *kb, int wp_kind, int K, int n_terms, const double *Vt,
+                        const double *c, int mode, double frac, double complex *Tc, double *ph, double *eps_out,
+                        int *sweeps_out)
 {
     int n = K * N;
     double mu = or_mu();
@@ -644,8 +664,8 @@ int or_channel_solve(int N, const double *kb, int wp_kind, int K, int n_terms, c
         for (int a = 0; a < K; ++a)
             for (int b = 0; b < K; ++b) Vd[a * K + b] = V[(a * N + i) * n + (b * N + i)];
         or_contract(n, K, Vd, R, gre, gim, Tr, Ti);
-        /* continuum normalisation at q = kbar_i */
-        double kbar = 0.5 * (kb[i] + kb[i + 1]);
+        /* continuum normalisation at q = kbar_i (the interpolation point of bin i) */
+        double kbar = ip_point(kb, i, frac);
         double Ni = wp_norm(wp_kind, kb[i], kb[i + 1]);
         double fac = wp_f(wp_kind, kbar) * wp_f(wp_kind, kbar) / (Ni * kbar * kbar);
         double complex Tq[4], S[4];
@@ -759,14 +779,25 @@ static double wrap90(double d)
     return d;
 }
 
+void or_interp_phase_ip(int N, const double *kb, const double *ph /*[N][3]*/, int K, double p, double frac,
+                        double *out);
+
 void or_interp_phase(int N, const double *kb, const double *ph /*[N][3]*/, int K, double p, double *out)
+{
+    or_interp_phase_ip(N, kb, ph, K, p, 0.5, out);
+}
+
+/* The same between the interpolation points q_j = (1 - frac) k_j + frac k_{j+1} */
+/* of consecutive bins (Eq. "interpolation point"; frac = 0.5: midpoints).      */
+void or_interp_phase_ip(int N, const double *kb, const double *ph /*[N][3]*/, int K, double p, double frac,
+                        double *out)
 {
     int j = -1;
     for (int i = 0; i < N; ++i)
-        if (0.5 * (kb[i] + kb[i + 1]) <= p) j = i;
+        if (ip_point(kb, i, frac) <= p) j = i;
     if (j < 0) j = 0;
     if (j > N - 2) j = N - 2;
-    double q0 = 0.5 * (kb[j] + kb[j + 1]), q1 = 0.5 * (kb[j + 1] + kb[j + 2]);
+    double q0 = ip_point(kb, j, frac), q1 = ip_point(kb, j + 1, frac);
     double w = (p - q0) / (q1 - q0);
     int ncomp = (K == 2) ? 2 : 1;
     for (int c = 0; c < ncomp; ++c) {
@@ -970,10 +1001,26 @@ static int batch_point(int n_ch, const int *chdesc, const int *nwp, const long *
 /* and phases at each p(E) directly).  OpenMP over (sample, channel).         */
 /* Returns 0 or the first error code.                                         */
 /* ------------------------------------------------------------------------- */
+int or_batch_ip(int n_ch, const int *chdesc, const int *nwp, const long *kb_off, const double *kb_all, int wp_kind,
+                int n_terms, const long *vt_off, const double *Vt_all, int n_samples, const double *coeffs, int n_E,
+                const double *e_lab, int mode, double frac, double complex *t_out, double *delta_out,
+                double *sigma_out, int n_threads);
+
 int or_batch(int n_ch, const int *chdesc /* n_ch x 6 */, const int *nwp, const long *kb_off, const double *kb_all,
              int wp_kind, int n_terms, const long *vt_off, const double *Vt_all, int n_samples,
              const double *coeffs, int n_E, const double *e_lab, int mode, double complex *t_out, double *delta_out,
              double *sigma_out, int n_threads)
+{
+    return or_batch_ip(n_ch, chdesc, nwp, kb_off, kb_all, wp_kind, n_terms, vt_off, Vt_all, n_samples, coeffs, n_E,
+                       e_lab, mode, 0.5, t_out, delta_out, sigma_out, n_threads);
+}
+
+/* or_batch with the interpolation point at fraction frac of each bin (Sec.  */
+/* 5.1.1, Eq. "interpolation point"; 0 < frac < 1, 0.5 = the midpoints).     */
+int or_batch_ip(int n_ch, const int *chdesc, const int *nwp, const long *kb_off, const double *kb_all, int wp_kind,
+                int n_terms, const long *vt_off, const double *Vt_all, int n_samples, const double *coeffs, int n_E,
+                const double *e_lab, int mode, double frac, double complex *t_out, double *delta_out,
+                double *sigma_out, int n_threads)
 {
     if (mode == 2) /* point resolvent: T and phases at each energy, no interpolation */
         return batch_point(n_ch, chdesc, nwp, kb_off, kb_all, wp_kind, n_terms, vt_off, Vt_all, n_samples, coeffs,
@@ -995,8 +1042,8 @@ int or_batch(int n_ch, const int *chdesc /* n_ch x 6 */, const int *nwp, const l
             double *eps = (double *)malloc(sizeof(double) * n);
             double complex *Tc = Tall + ((size_t)smp * n_ch + c) * maxN * 4;
             double *ph = phall + ((size_t)smp * n_ch + c) * maxN * 3;
-            int rc = or_channel_solve(N, kb_all + kb_off[c], wp_kind, K, n_terms, Vt_all + vt_off[c],
-                                      coeffs + (size_t)smp * (n_terms - 1), mode, Tc, ph, eps, NULL);
+            int rc = or_channel_solve_ip(N, kb_all + kb_off[c], wp_kind, K, n_terms, Vt_all + vt_off[c],
+                                         coeffs + (size_t)smp * (n_terms - 1), mode, frac, Tc, ph, eps, NULL);
             if (rc < 0) {
 #ifdef _OPENMP
 #pragma omp critical(or_err)
@@ -1028,7 +1075,7 @@ int or_batch(int n_ch, const int *chdesc /* n_ch x 6 */, const int *nwp, const l
                 }
                 for (int a = 0; a < K; ++a)
                     for (int b = 0; b < K; ++b) tout[a * 2 + b] = Tc[(size_t)bin * K * K + a * K + b];
-                or_interp_phase(N, kb, ph, K, p, dout);
+                or_interp_phase_ip(N, kb, ph, K, p, frac, dout);
                 if (chdesc[c * 6 + 5] == 0) acc += or_sigma_term(chdesc[c * 6 + 1], K, dout);
             }
             sigma_out[(size_t)smp * n_E + e] = or_sigma_prefactor_mb(p) * acc;
