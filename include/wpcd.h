@@ -100,10 +100,14 @@ enum {
  * fastest (wpcd_tuning reports the choices); 0 = fixed 256 threads.
  * WPCD_OPT_GRAPH (1 = on, the default): batched wpcd_solve / wpcd_solve_host
  * calls are replayed from CUDA graphs (see wpcd_solve); 0 = every call
- * launches its kernels one by one. */
+ * launches its kernels one by one.  WPCD_OPT_BIG_SLOTS: CTAs (each with its
+ * own scratch copy of the matrix and eigenvectors) of the global-memory
+ * eigensolver used above the shared-memory size; 0 (the default) = automatic
+ * (FP64: every resident CTA; FP32: as many as keep the copies within about
+ * three quarters of the L2 cache, at least a quarter of the SMs). */
 enum { WPCD_EXEC_BATCHED = 0, WPCD_EXEC_PLAIN = 1 };
 enum { WPCD_REFINE_TENSOR = 0, WPCD_REFINE_FP64 = 1 };
-enum { WPCD_OPT_EXEC = 1, WPCD_OPT_REFINE = 2, WPCD_OPT_AUTOTUNE = 3, WPCD_OPT_GRAPH = 4 };
+enum { WPCD_OPT_EXEC = 1, WPCD_OPT_REFINE = 2, WPCD_OPT_AUTOTUNE = 3, WPCD_OPT_GRAPH = 4, WPCD_OPT_BIG_SLOTS = 5 };
 
 /* ---- context --------------------------------------------------------------------------------- */
 
@@ -118,6 +122,15 @@ void wpcd_destroy(wpcd_ctx *ctx);
 
 /* Static, human-readable text for a status code. */
 const char *wpcd_strerror(wpcd_status st);
+
+/* Interpolation point (Sec. 5.1.1, Eq. "interpolation point"): the point
+ * q_i = k_i + frac (k_{i+1} - k_i) of each free bin at which the averaged
+ * resolvents' T is converted to the continuum (wpcd_tmatrix) and the bin's
+ * phase shift is placed for the linear interpolation (wpcd_observables);
+ * frac = n/m of the paper, 0 < frac < 1, default 0.5 (the bin midpoint).
+ * Applies to calls queued afterwards (served batches included); the point
+ * resolvent ignores it.  Errors: WPCD_ERR_ARG (frac outside (0, 1)). */
+wpcd_status wpcd_set_interp_point(wpcd_ctx *ctx, double frac);
 
 /* Set an execution option (see WPCD_OPT_*).  Errors: WPCD_ERR_ARG. */
 wpcd_status wpcd_set_option(wpcd_ctx *ctx, int key, int value);

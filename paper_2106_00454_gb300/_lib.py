@@ -20,7 +20,7 @@ EXPORTED = [
     "wpcd_release", "wpcd_kernel_launches", "wpcd_profile", "wpcd_profile_read",
     "wpcd_channel_solve_noalloc", "wpcd_serve_start", "wpcd_serve_stop", "wpcd_submit", "wpcd_poll", "wpcd_wait",
     "wpcd_release_result", "wpcd_serve_stats", "wpcd_batched_dgemm", "wpcd_tuning", "wpcd_mi_prepare",
-    "wpcd_mi_solve", "wpcd_saclay", "wpcd_graph_stats", "wpcd_device_log",
+    "wpcd_mi_solve", "wpcd_saclay", "wpcd_graph_stats", "wpcd_device_log", "wpcd_set_interp_point",
 ]
 
 
@@ -51,6 +51,7 @@ _SIG = {
     "wpcd_destroy": (None, [_vp]),
     "wpcd_strerror": (ctypes.c_char_p, [_i]),
     "wpcd_set_option": (_i, [_vp, _i, _i]),
+    "wpcd_set_interp_point": (_i, [_vp, _d]),
     "wpcd_sync": (_i, [_vp]),
     "wpcd_bytes_in_use": (_sz, [_vp]),
     "wpcd_mesh": (_i, [_vp, _i, _i, _d, _d, _d, _i, _i, _ip]),

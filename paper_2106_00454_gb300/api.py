@@ -19,7 +19,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 AVG_FREE_BIN, AVG_SWP_INDEX, POINT = 0, 1, 2  # resolvent (wpcd_resolvent)
 EXEC_BATCHED, EXEC_PLAIN = 0, 1
 REFINE_TENSOR, REFINE_FP64 = 0, 1
-OPT_EXEC, OPT_REFINE, OPT_AUTOTUNE, OPT_GRAPH = 1, 2, 3, 4
+OPT_EXEC, OPT_REFINE, OPT_AUTOTUNE, OPT_GRAPH, OPT_BIG_SLOTS = 1, 2, 3, 4, 5
 
 
 class WpcdError(RuntimeError):
@@ -84,6 +84,14 @@ class Context:
         items, n, _ = A.shape
         _ck(self.lib.wpcd_batched_dgemm(self.h, n, items, 1 if trans_a else 0, _ptr(A), _ptr(B), _ptr(C), engine),
             "wpcd_batched_dgemm")
+
+    def set_interp_point(self, frac: float):
+        """Interpolation point of every bin as a fraction of it (Sec. 5.1.1; 0.5 = midpoint)."""
+        _ck(self.lib.wpcd_set_interp_point(self.h, float(frac)), "wpcd_set_interp_point")
+
+    def set_big_slots(self, slots: int):
+        """CTAs of the global-memory eigensolver (0 = automatic)."""
+        _ck(self.lib.wpcd_set_option(self.h, OPT_BIG_SLOTS, int(slots)), "wpcd_set_option")
 
     def set_autotune(self, on: bool):
         _ck(self.lib.wpcd_set_option(self.h, OPT_AUTOTUNE, 1 if on else 0), "wpcd_set_option")

@@ -46,6 +46,11 @@ constexpr int kBigMaxN = 2 * kMaxNwp;
 constexpr float kBigRelTol = 1.1920929e-7f;  // 2^-23
 constexpr int kBigThreshSweeps = 2;
 constexpr float kBigThreshFrac = 0.1f;
+// column slots (or eigenvector rows) whose loads a lane batches: 8 in FP32, 4 in FP64 (registers)
+template <class T>
+struct BigUnroll {
+    static constexpr int v = sizeof(T) == 8 ? 4 : 8;
+};
 
 __host__ __device__ inline int big_pad(int n) { return (n + 1) & ~1; }
 
@@ -103,6 +108,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_jacobi_big(const ChanDev *ch
                                                           int *err)
 {
     constexpr bool F64 = sizeof(T) == 8;
+    constexpr int kBigUnroll = BigUnroll<T>::v;
     extern __shared__ double smem_big[];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -207,59 +213,93 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_jacobi_big(const ChanDev *ch
                 }
                 __syncthreads();
                 if (flag[1 + g3]) {
-                    // phase 2: rows p, q of every row pair, and columns p, q of Cc
+                    // phase 2: rows p, q of every row pair, and columns p, q of Cc.  Each lane
+                    // issues the loads of kBigUnroll column slots (or rows of Cc) before any
+                    // store: the accesses are L2 round trips, and a store may alias a later
+                    // load for all the compiler knows, so batching them is what keeps
+                    // enough requests in flight
                     for (int P = warp; P < h; P += nwarp) {
                         const int4 u = sl[P];
                         const BigRot<T> r1 = rot[P];
                         T *Rp = A + (size_t)u.x * np, *Rq = A + (size_t)u.y * np;
-                        for (int k = lane; k < h; k += 32) {
-                            const BigRot<T> r2 = rot[k];
-                            if (k == P) {
-                                if (r1.s != T(0)) {
-                                    Rp[u.x] = r1.app;
-                                    Rq[u.y] = r1.aqq;
-                                    Rp[u.y] = T(0);
-                                    Rq[u.x] = T(0);
+                        for (int k0 = lane; k0 < h; k0 += 32 * kBigUnroll) {
+                            T pa[kBigUnroll], pb[kBigUnroll], qa[kBigUnroll], qb[kBigUnroll];
+                            int ca[kBigUnroll], cb[kBigUnroll];
+                            bool act[kBigUnroll];
+#pragma unroll
+                            for (int t = 0; t < kBigUnroll; ++t) {
+                                const int k = k0 + 32 * t;
+                                act[t] = k < h && k != P && !(r1.s == T(0) && rot[k].s == T(0));
+                                if (act[t]) {
+                                    const int4 v = sl[k];
+                                    ca[t] = v.z;
+                                    cb[t] = v.w;
+                                    pa[t] = Rp[v.z];
+                                    pb[t] = Rp[v.w];
+                                    qa[t] = Rq[v.z];
+                                    qb[t] = Rq[v.w];
                                 }
-                                continue;
                             }
-                            if (r1.s == T(0) && r2.s == T(0)) continue;
-                            const int4 v = sl[k];
-                            // columns in slot order (a, b); the rotation acts on (p2, q2) = (min, max)
-                            const bool ab = v.z < v.w;
-                            const int ca = v.z, cb = v.w;
-                            const T pa = Rp[ca], pb = Rp[cb], qa = Rq[ca], qb = Rq[cb];
-                            const T b00 = ab ? pa : pb, b01 = ab ? pb : pa;
-                            const T b10 = ab ? qa : qb, b11 = ab ? qb : qa;
-                            // J_P^T B J_k, the rotation of the lower slot index applied first:
-                            // the mirror block (rows of slot k, columns of slot P) is then the
-                            // exact transpose, and A stays exactly symmetric
-                            T y00, y01, y10, y11;
-                            if (k > P) {
-                                T x00, x01, x10, x11;
-                                big_rot(r2.c, r2.s, b00, b01, x00, x01);  // columns (J_k)
-                                big_rot(r2.c, r2.s, b10, b11, x10, x11);
-                                big_rot(r1.c, r1.s, x00, x10, y00, y10);  // rows (J_P)
-                                big_rot(r1.c, r1.s, x01, x11, y01, y11);
-                            } else {
-                                T z00, z01, z10, z11;
-                                big_rot(r1.c, r1.s, b00, b10, z00, z10);  // rows (J_P)
-                                big_rot(r1.c, r1.s, b01, b11, z01, z11);
-                                big_rot(r2.c, r2.s, z00, z01, y00, y01);  // columns (J_k)
-                                big_rot(r2.c, r2.s, z10, z11, y10, y11);
+#pragma unroll
+                            for (int t = 0; t < kBigUnroll; ++t) {
+                                if (!act[t]) continue;
+                                const int k = k0 + 32 * t;
+                                const BigRot<T> r2 = rot[k];
+                                // columns in slot order (a, b); the rotation acts on (p2, q2) = (min, max)
+                                const bool ab = ca[t] < cb[t];
+                                const T b00 = ab ? pa[t] : pb[t], b01 = ab ? pb[t] : pa[t];
+                                const T b10 = ab ? qa[t] : qb[t], b11 = ab ? qb[t] : qa[t];
+                                // J_P^T B J_k, the rotation of the lower slot index applied first:
+                                // the mirror block (rows of slot k, columns of slot P) is then the
+                                // exact transpose, and A stays exactly symmetric
+                                T y00, y01, y10, y11;
+                                if (k > P) {
+                                    T x00, x01, x10, x11;
+                                    big_rot(r2.c, r2.s, b00, b01, x00, x01);  // columns (J_k)
+                                    big_rot(r2.c, r2.s, b10, b11, x10, x11);
+                                    big_rot(r1.c, r1.s, x00, x10, y00, y10);  // rows (J_P)
+                                    big_rot(r1.c, r1.s, x01, x11, y01, y11);
+                                } else {
+                                    T z00, z01, z10, z11;
+                                    big_rot(r1.c, r1.s, b00, b10, z00, z10);  // rows (J_P)
+                                    big_rot(r1.c, r1.s, b01, b11, z01, z11);
+                                    big_rot(r2.c, r2.s, z00, z01, y00, y01);  // columns (J_k)
+                                    big_rot(r2.c, r2.s, z10, z11, y10, y11);
+                                }
+                                Rp[ca[t]] = ab ? y00 : y01;
+                                Rp[cb[t]] = ab ? y01 : y00;
+                                Rq[ca[t]] = ab ? y10 : y11;
+                                Rq[cb[t]] = ab ? y11 : y10;
                             }
-                            Rp[ca] = ab ? y00 : y01;
-                            Rp[cb] = ab ? y01 : y00;
-                            Rq[ca] = ab ? y10 : y11;
-                            Rq[cb] = ab ? y11 : y10;
                         }
                         if (r1.s != T(0)) {
+                            if (lane == 0) {  // the diagonal block of the pair
+                                Rp[u.x] = r1.app;
+                                Rq[u.y] = r1.aqq;
+                                Rp[u.y] = T(0);
+                                Rq[u.x] = T(0);
+                            }
                             T *Cp = Cc + (size_t)u.x * np, *Cq = Cc + (size_t)u.y * np;
-                            for (int row = lane; row < np; row += 32) {
-                                T a, b;
-                                big_rot(r1.c, r1.s, Cp[row], Cq[row], a, b);
-                                Cp[row] = a;
-                                Cq[row] = b;
+                            for (int r0 = lane; r0 < np; r0 += 32 * kBigUnroll) {
+                                T a[kBigUnroll], b[kBigUnroll];
+#pragma unroll
+                                for (int t = 0; t < kBigUnroll; ++t) {
+                                    const int row = r0 + 32 * t;
+                                    if (row < np) {
+                                        a[t] = Cp[row];
+                                        b[t] = Cq[row];
+                                    }
+                                }
+#pragma unroll
+                                for (int t = 0; t < kBigUnroll; ++t) {
+                                    const int row = r0 + 32 * t;
+                                    if (row < np) {
+                                        T x, y;
+                                        big_rot(r1.c, r1.s, a[t], b[t], x, y);
+                                        Cp[row] = x;
+                                        Cq[row] = y;
+                                    }
+                                }
                             }
                         }
                     }

@@ -230,6 +230,30 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
                     float4 *Cp = reinterpret_cast<float4 *>(C + (size_t)u.x * ldc);
                     float4 *Cq = reinterpret_cast<float4 *>(C + (size_t)u.y * ldc);
                     const float c = r1.x, s = r1.y;
+                    if (!C_SMEM && nv <= 96) {
+                        // columns in global memory (L2): every load of the two columns is
+                        // issued before the first store, one L2 round trip per rotation
+                        float4 a[3], b[3];
+#pragma unroll
+                        for (int t = 0; t < 3; ++t) {
+                            const int v = lane + 32 * t;
+                            if (v < nv) {
+                                a[t] = Cp[v];
+                                b[t] = Cq[v];
+                            }
+                        }
+#pragma unroll
+                        for (int t = 0; t < 3; ++t) {
+                            const int v = lane + 32 * t;
+                            if (v < nv) {
+                                Cp[v] = make_float4(c * a[t].x - s * b[t].x, c * a[t].y - s * b[t].y,
+                                                    c * a[t].z - s * b[t].z, c * a[t].w - s * b[t].w);
+                                Cq[v] = make_float4(s * a[t].x + c * b[t].x, s * a[t].y + c * b[t].y,
+                                                    s * a[t].z + c * b[t].z, s * a[t].w + c * b[t].w);
+                            }
+                        }
+                        continue;
+                    }
                     for (int v = lane; v < nv; v += 32) {
                         const float4 a = Cp[v], b = Cq[v];
                         Cp[v] = make_float4(c * a.x - s * b.x, c * a.y - s * b.y, c * a.z - s * b.z, c * a.w - s * b.w);

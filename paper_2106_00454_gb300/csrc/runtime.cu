@@ -146,6 +146,9 @@ struct wpcd_ctx {
     // CUDA graphs of wpcd_solve.  graph_gen counts every event that may change
     // what a captured graph baked in (a device allocation or free, an option, a
     // new tuning); a graph captured under another generation is dropped.
+    double ip_frac = 0.5;  // interpolation point of the averaged resolvents (Sec. 5.1.1)
+    int big_slots = 0;     // CTAs of the global-memory eigensolver (0: automatic)
+    int l2_bytes = 0;
     int use_graphs = 1;
     std::atomic<unsigned long long> graph_gen{0};
     struct GraphE {
@@ -444,9 +447,15 @@ wpcd_status run_bucket_big(wpcd_ctx *c, Exec &X, VSetH &v, EigH &e, const double
     if (!c->n_sm) cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
     const int occ = std::max(1, jacobi_big_occupancy(n, f64));
     const size_t slot_b = (jacobi_big_scratch_bytes(n, f64) + 255) & ~(size_t)255;
+    // CTAs in flight: FP64 is bound by the FP64 pipe, so every resident CTA; FP32 by the
+    // traffic of its matrix copies, which should stay L2-resident
+    if (!c->l2_bytes) cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, c->device);
+    int cap = c->n_sm * occ;
+    if (!f64) cap = std::min(cap, std::max(c->n_sm / 4, (int)((size_t)c->l2_bytes * 3 / 4 / slot_b)));
+    if (c->big_slots > 0) cap = c->big_slots;
     if (f64) {
         const int items = nsmp * nw;
-        const int slots = std::max(1, std::min(items, c->n_sm * occ));
+        const int slots = std::max(1, std::min(items, cap));
         wpcd_status st = ws_reserve(c, X, X.ws_ref, slot_b * slots);
         if (st) return st;
         Launch L(c, X, WPCD_PHASE_EIGEN);
@@ -458,7 +467,7 @@ wpcd_status run_bucket_big(wpcd_ctx *c, Exec &X, VSetH &v, EigH &e, const double
     int chunk = (int)std::max<size_t>(1, kRefineScratchBytes / (ref_item * nw));
     chunk = std::min(chunk, std::max(1, 65535 / nw));  // the refinement grids put items in y / z (<= 65535)
     chunk = std::min(chunk, nsmp);
-    const int slots = std::max(1, std::min(chunk * nw, c->n_sm * occ));
+    const int slots = std::max(1, std::min(chunk * nw, cap));
     const size_t ref_b = (ref_item * nw * chunk + 255) & ~(size_t)255;
     wpcd_status st = ws_reserve(c, X, X.ws_ref, ref_b + slot_b * slots);
     if (st) return st;
@@ -584,6 +593,7 @@ wpcd_status run_tbin(wpcd_ctx *c, Exec &X, VSetH &v, EigH &e, const double *e_la
     plan.pE = static_cast<double *>(X.ws_plan_d.p);
     plan.per_sample = n_E_s ? 1 : 0;
     plan.n_E_s = n_E_s;
+    plan.ip_frac = c->ip_frac;
     {
         Launch L(c, X, WPCD_PHASE_PLAN);
         CK(launch_plan(e.cd_dev, nch, maxN, e_lab, n_E, plan, X.err, X.stream, P));
@@ -721,6 +731,10 @@ wpcd_status wpcd_set_option(wpcd_ctx *c, int key, int value)
         c->refine_engine = value;
         return WPCD_OK;
     }
+    if (key == WPCD_OPT_BIG_SLOTS && value >= 0) {
+        c->big_slots = value;
+        return WPCD_OK;
+    }
     if (key == WPCD_OPT_AUTOTUNE && (value == 0 || value == 1)) {
         c->autotune = value;
         if (!value) {
@@ -730,6 +744,15 @@ wpcd_status wpcd_set_option(wpcd_ctx *c, int key, int value)
         return WPCD_OK;
     }
     return WPCD_ERR_ARG;
+}
+
+wpcd_status wpcd_set_interp_point(wpcd_ctx *c, double frac)
+{
+    if (!c || !(frac > 0.0 && frac < 1.0)) return WPCD_ERR_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->ip_frac = frac;
+    ++c->graph_gen;  // captured graphs hold the energy plan's value
+    return WPCD_OK;
 }
 
 wpcd_status wpcd_sync(wpcd_ctx *c)

@@ -14,7 +14,7 @@ constexpr int kTThreads = 256;
 
 // ---------------------------------------------------------------------------------------------
 // Energy plan: per channel and energy, the free bin holding p(E) and the
-// midpoint segment used for interpolation; per channel, the distinct bins
+// segment of interpolation points used for interpolation; per channel, the distinct bins
 // whose T is needed (the bin itself and both ends of its segment).
 // ---------------------------------------------------------------------------------------------
 __global__ void k_plan(const ChanDev *chans, int n_ch, int maxN, const double *e_lab, int n_E, PlanDev plan, int *err)
@@ -43,10 +43,10 @@ __global__ void k_plan(const ChanDev *chans, int n_ch, int maxN, const double *e
             }
             bin = lo;
             lo = -1;
-            hi = N - 1;  // largest j with kbar_j <= p (or -1)
+            hi = N - 1;  // largest j whose interpolation point is <= p (or -1)
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
-                if (0.5 * (ch.kb[mid] + ch.kb[mid + 1]) <= p) lo = mid;
+                if (ip_point(ch.kb, mid, plan.ip_frac) <= p) lo = mid;
                 else hi = mid - 1;
             }
             j = lo < 0 ? 0 : (lo > N - 2 ? N - 2 : lo);
@@ -130,7 +130,8 @@ __device__ __forceinline__ double xlogabs(double d) { return d == 0.0 ? 0.0 : d 
 //        g_s = [ln|(E - B_s)/(E - B_s+1)| - i pi 1{E in [B_s, B_s+1]}] / dB,
 //        or 1/(E - e_b);
 //    then T_ab = V_(a,i),(b,i) + sum_s R_as g_s R_bs.
-//  - continuum T: T f(q)^2 / (N_i q^2) at q = the bin midpoint (modes 0, 1)
+//  - continuum T: T f(q)^2 / (N_i q^2) at q = the bin's interpolation point (modes 0, 1;
+//    the midpoint unless the caller set another, Sec. 5.1.1)
 //    or q = p(E) (mode 2); S = 1 - 2 pi i mu q T; phases (Stapp for coupled
 //    channels).
 // Averaged modes visit the needed bins in ascending order, so the X(E_{i+1}, B)
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(kTThreads, 5) k_tmat(const ChanDev *chans, int
                 a = ch.kb[i] * ch.kb[i] / (2.0 * kMu);
                 b = ch.kb[i + 1] * ch.kb[i + 1] / (2.0 * kMu);
             }
-            const double q = 0.5 * (ch.kb[i] + ch.kb[i + 1]);
+            const double q = ip_point(ch.kb, i, plan.ip_frac);
             const double Ni = ch.wp_kind == 0 ? (ch.kb[i + 1] - ch.kb[i])
                                               : (ch.kb[i + 1] * ch.kb[i + 1] - ch.kb[i] * ch.kb[i]) / (2.0 * kMu);
             const double f2 = ch.wp_kind == 0 ? 1.0 : q / kMu;
@@ -454,7 +455,7 @@ __global__ void __launch_bounds__(kTThreads, 5) k_tmat(const ChanDev *chans, int
     for (int ii = tid; ii < cnt; ii += nt) {
         const int slot = MODE == 2 ? ii : plan.list[pc * stride + ii];
         const int i = MODE == 2 ? plan.bin[pc * n_E + ii] : slot;
-        const double q = MODE == 2 ? plan.pE[(size_t)ps * n_E + ii] : 0.5 * (ch.kb[i] + ch.kb[i + 1]);
+        const double q = MODE == 2 ? plan.pE[(size_t)ps * n_E + ii] : ip_point(ch.kb, i, plan.ip_frac);
         phases_of_T(K, q, tout + (obase + slot) * 8, phout + (obase + slot) * 3);
     }
 }
@@ -543,8 +544,9 @@ cudaError_t launch_gather_t(const ChanDev *chans_dev, int n_ch, int n_samples, i
 }
 
 // ---------------------------------------------------------------------------------------------
-// Phases interpolated linearly in p between the midpoints of the segment j,
-// j+1 (extended past the end midpoints), after moving delta_{j+1} by a
+// Phases interpolated linearly in p between the interpolation points (the
+// midpoints unless the caller set another) of the segment j, j+1 (extended
+// past the end points), after moving delta_{j+1} by a
 // multiple of 180 deg to within 90 deg of delta_j; result mapped to
 // (-90, 90]; with the point resolvent (direct) the phases at p(E) itself.
 // Total cross section sigma = pi/(2p^2) sum (2J+1) sum_l Re(1 - S_ll) over the
@@ -579,7 +581,7 @@ __global__ void k_observables(const ChanDev *chans, int n_ch, int n_samples, int
             for (int k = 0; k < 3; ++k) out[k] = ph[3 * e + k];
         } else {
             const int j = plan.brk[((size_t)ps * n_ch + c) * n_E + e];
-            const double q0 = 0.5 * (ch.kb[j] + ch.kb[j + 1]), q1 = 0.5 * (ch.kb[j + 1] + ch.kb[j + 2]);
+            const double q0 = ip_point(ch.kb, j, plan.ip_frac), q1 = ip_point(ch.kb, j + 1, plan.ip_frac);
             const double w = (p - q0) / (q1 - q0);
             const int ncomp = ch.K == 2 ? 2 : 1;
             for (int k = 0; k < ncomp; ++k) {

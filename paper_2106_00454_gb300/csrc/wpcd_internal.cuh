@@ -98,7 +98,18 @@ struct PlanDev {
     double *pE;         // [P][n_E] c.m. momentum of each energy
     int per_sample;     // 0: P = 1, the plan of every sample; 1: P = n_samples
     const int *n_E_s;   // per-sample list lengths (per_sample only; NULL = all n_E)
+    double ip_frac = 0.5;  // interpolation point of a bin, as a fraction of it (0.5: the midpoint)
 };
+
+// Sec. 5.1.1, Eq. "interpolation point": the point k_i + f (k_{i+1} - k_i) of
+// bin i at which its T is converted to the continuum and its phase placed for
+// the interpolation, as (1 - f) k_i + f k_{i+1}; f = 1/2 gives exactly the
+// midpoint 0.5 (k_i + k_{i+1}) (halving is exact, with or without a fused
+// multiply-add).
+__host__ __device__ __forceinline__ double ip_point(const double *kb, int i, double f)
+{
+    return (1.0 - f) * kb[i] + f * kb[i + 1];
+}
 
 __device__ __forceinline__ int plan_of(const PlanDev &pl, int smp) { return pl.per_sample ? smp : 0; }
 __device__ __forceinline__ int plan_nE(const PlanDev &pl, int ps, int n_E) { return pl.n_E_s ? pl.n_E_s[ps] : n_E; }

@@ -7,7 +7,10 @@ solution of the same LS equation, both through the public API.
 * ``rmse_study``: the root-mean-square deviation of sigma_tot from the exact
   result over lab-energy ranges, RMSE = sqrt(sum_i (sigma_exact,i -
   sigma_method,i)^2 / n_E) (Sec. 5.2), for WPCD at several N_WP and for MI with
-  linear interpolation between n_I Chebyshev energies.
+  linear interpolation between n_I Chebyshev energies;
+* ``interpolation_bands``: the spread of the interpolated phase shifts and
+  sigma_tot over the interpolation point q_i = k_i + (n/m)(k_{i+1} - k_i)
+  (Sec. 5.1.1; the paper's m = 10, n in {0.1, 1, 2, ..., 9, 9.9}).
 
 Only orchestration lives here: every number comes from wpcd_solve and
 wpcd_mi_solve.
@@ -84,3 +87,35 @@ def rmse_study(ctx, wl: W.Workload, nwp_list, mi_interp_list=(), ranges=((0.0, 3
     for n_i in mi_interp_list:
         res["mi"][int(n_i)] = rmse(_mi_sigma(ctx, wl, W.chebyshev_energies(int(n_i)), n_quad))
     return res
+
+
+BAND_FRACS = (0.01, 0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9, 0.99)
+
+
+def interpolation_bands(ctx, wl: W.Workload, fracs=BAND_FRACS, prec=api.PREC_FP64):
+    """Phase shifts and sigma_tot for each interpolation point of fracs:
+    {"delta": [len(fracs), S, ch, n_E, 3], "sigma": [len(fracs), S, n_E],
+    "delta_lo"/"delta_hi", "sigma_lo"/"sigma_hi": the band over fracs}.
+    The context's interpolation point is restored to the midpoint afterwards."""
+    import torch
+    dev = f"cuda:{ctx.device}"
+    md = api.Model(ctx, wl)
+    S, nch, nE = wl.n_samples, len(wl.channels), len(wl.e_lab)
+    cf = None if wl.n_terms == 1 else torch.tensor(wl.coeffs, dtype=torch.float64, device=dev)
+    e = torch.tensor(wl.e_lab, dtype=torch.float64, device=dev)
+    ds, ss = [], []
+    try:
+        for f in fracs:
+            ctx.set_interp_point(f)
+            d = torch.empty((S, nch, nE, 3), dtype=torch.float64, device=dev)
+            s = torch.empty((S, nE), dtype=torch.float64, device=dev)
+            ctx.solve(md.vset, cf, S, e, None, d, s, prec=prec)
+            ctx.sync()
+            ds.append(d.cpu().numpy())
+            ss.append(s.cpu().numpy())
+    finally:
+        ctx.set_interp_point(0.5)
+        md.release()
+    d, s = np.array(ds), np.array(ss)
+    return {"fracs": list(fracs), "delta": d, "sigma": s, "delta_lo": d.min(axis=0), "delta_hi": d.max(axis=0),
+            "sigma_lo": s.min(axis=0), "sigma_hi": s.max(axis=0)}
