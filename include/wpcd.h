@@ -102,12 +102,18 @@ enum {
  * calls are replayed from CUDA graphs (see wpcd_solve); 0 = every call
  * launches its kernels one by one.  WPCD_OPT_BIG_SLOTS: CTAs (each with its
  * own scratch copy of the matrix and eigenvectors) of the global-memory
- * eigensolver used above the shared-memory size; 0 (the default) = automatic
- * (FP64: every resident CTA; FP32: as many as keep the copies within about
- * three quarters of the L2 cache, at least a quarter of the SMs). */
+ * eigensolver used above the shared-memory size; 0 (the default) = every
+ * CTA that can be resident at once.  WPCD_OPT_ROTATE (1 = on, the default;
+ * mixed path with the tensor refinement engine): the FP32 eigensolve starts
+ * from C0^T H C0, C0 the FP64 eigenvectors of the projected set's diag(H0) + V0
+ * (built once per set, on its first mixed solve), which is nearly diagonal for
+ * samples near the mean and takes fewer Jacobi sweeps; the refined
+ * eigenvectors are rotated back with FP64-accurate products.  0 = the FP32
+ * eigensolve starts from H itself. */
 enum { WPCD_EXEC_BATCHED = 0, WPCD_EXEC_PLAIN = 1 };
 enum { WPCD_REFINE_TENSOR = 0, WPCD_REFINE_FP64 = 1 };
-enum { WPCD_OPT_EXEC = 1, WPCD_OPT_REFINE = 2, WPCD_OPT_AUTOTUNE = 3, WPCD_OPT_GRAPH = 4, WPCD_OPT_BIG_SLOTS = 5 };
+enum { WPCD_OPT_EXEC = 1, WPCD_OPT_REFINE = 2, WPCD_OPT_AUTOTUNE = 3, WPCD_OPT_GRAPH = 4, WPCD_OPT_BIG_SLOTS = 5,
+       WPCD_OPT_ROTATE = 6 };
 
 /* ---- context --------------------------------------------------------------------------------- */
 

@@ -121,9 +121,12 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_jacobi_big(const ChanDev *ch
         int4 *sl = reinterpret_cast<int4 *>(smem_big);
         BigRot<T> *rot = reinterpret_cast<BigRot<T> *>(sl + h);
         double *red = reinterpret_cast<double *>(rot + h);  // 32 doubles
-        int *flag = reinterpret_cast<int *>(red + 32);      // [0] rotation this sweep, [1..3] this round
-        int *rank = flag + 4;                               // [np]
-        const size_t need = (size_t)h * (sizeof(int4) + sizeof(BigRot<T>)) + 32 * 8 + 4 * 4 + (size_t)np * 4;
+        // flag: [0] rotation this sweep; [1..3] rotating slots this round, cycled over three rounds
+        int *flag = reinterpret_cast<int *>(red + 32);
+        int *act = flag + 4;   // [h] the round's rotating slots
+        int *rank = act + h;   // [np] eigenvalue ranks for the final sort
+        const size_t need = (size_t)h * (sizeof(int4) + sizeof(BigRot<T>)) + 32 * 8 + 4 * 4 + (size_t)h * 4 +
+                            (size_t)np * 4;
         if (n > kBigMaxN || (size_t)dyn_smem_bytes() < need) {
             if (tid == 0) {
                 status_all[(size_t)smp * n_ch_total + cidx] = -1;
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_jacobi_big(const ChanDev *ch
                 const size_t ij = i <= j ? (size_t)i * n + j : (size_t)j * n + i;
                 v = ch.V[ij];
                 for (int a = 1; a < n_terms; ++a) v = fma(cf[a - 1], ch.V[(size_t)a * n * n + ij], v);
-                if (i == j) v += ch.h0[i % N];
+                if (i == j) v += ch.d0 ? ch.d0[i] : ch.h0[i % N];  // d0: the diagonal of a rotated basis
                 if (Hg) Hg[(size_t)i * n + j] = v;
                 fro2 = fma(v, v, fro2);
             }
@@ -206,13 +209,14 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_jacobi_big(const ChanDev *ch
                         app -= t * apq;
                         aqq += t * apq;
                         flag[0] = 1;
-                        flag[1 + g3] = 1;
+                        act[atomicAdd(&flag[1 + g3], 1)] = k;
                     }
                     sl[k] = make_int4(p, q, a, b);
                     rot[k] = BigRot<T>{c, s, app, aqq};
                 }
                 __syncthreads();
-                if (flag[1 + g3]) {
+                const int na = flag[1 + g3];  // rotating slots this round
+                if (na > 0) {
                     // phase 2: rows p, q of every row pair, and columns p, q of Cc.  Each lane
                     // issues the loads of kBigUnroll column slots (or rows of Cc) before any
                     // store: the accesses are L2 round trips, and a store may alias a later
@@ -222,15 +226,21 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_jacobi_big(const ChanDev *ch
                         const int4 u = sl[P];
                         const BigRot<T> r1 = rot[P];
                         T *Rp = A + (size_t)u.x * np, *Rq = A + (size_t)u.y * np;
-                        for (int k0 = lane; k0 < h; k0 += 32 * kBigUnroll) {
+                        // a rotating row pair meets every column slot; a fixed one only the
+                        // rotating slots (the other blocks stay as they are)
+                        const bool pa_rot = r1.s != T(0);
+                        const int kend = pa_rot ? h : na;
+                        for (int k0 = lane; k0 < kend; k0 += 32 * kBigUnroll) {
                             T pa[kBigUnroll], pb[kBigUnroll], qa[kBigUnroll], qb[kBigUnroll];
-                            int ca[kBigUnroll], cb[kBigUnroll];
-                            bool act[kBigUnroll];
+                            int ca[kBigUnroll], cb[kBigUnroll], kk[kBigUnroll];
+                            bool on[kBigUnroll];
 #pragma unroll
                             for (int t = 0; t < kBigUnroll; ++t) {
-                                const int k = k0 + 32 * t;
-                                act[t] = k < h && k != P && !(r1.s == T(0) && rot[k].s == T(0));
-                                if (act[t]) {
+                                const int j = k0 + 32 * t;
+                                const int k = j < kend ? (pa_rot ? j : act[j]) : 0;
+                                kk[t] = k;
+                                on[t] = j < kend && k != P && !(r1.s == T(0) && rot[k].s == T(0));
+                                if (on[t]) {
                                     const int4 v = sl[k];
                                     ca[t] = v.z;
                                     cb[t] = v.w;
@@ -242,8 +252,8 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_jacobi_big(const ChanDev *ch
                             }
 #pragma unroll
                             for (int t = 0; t < kBigUnroll; ++t) {
-                                if (!act[t]) continue;
-                                const int k = k0 + 32 * t;
+                                if (!on[t]) continue;
+                                const int k = kk[t];
                                 const BigRot<T> r2 = rot[k];
                                 // columns in slot order (a, b); the rotation acts on (p2, q2) = (min, max)
                                 const bool ab = ca[t] < cb[t];
@@ -353,7 +363,7 @@ template <class T>
 static size_t big_smem(int n)
 {
     const int np = big_pad(n), h = np / 2;
-    return (size_t)h * (sizeof(int4) + sizeof(BigRot<T>)) + 32 * 8 + 4 * 4 + (size_t)np * 4;
+    return (size_t)h * (sizeof(int4) + sizeof(BigRot<T>)) + 32 * 8 + 4 * 4 + (size_t)h * 4 + (size_t)np * 4;
 }
 
 // Whether the shared-memory kernel of that precision holds an n x n matrix

@@ -49,12 +49,13 @@ __host__ __device__ inline size_t mix_a_floats(int n)
 }
 
 // A float packed [npad] | slot table int4 [h] {p, q, base(p), base(q)} | rotations float2 [h] {c, s} |
-// a_pp', a_qq' float [h] each | flags int [4] | slot pairs ushort [quads, even] | (16-byte aligned)
+// a_pp', a_qq' float [h] each | flags int [8] | rank of each slot among the round's rotating
+// slots int [h] | rotating slots ushort [h, even] | slot pairs ushort [quads, even] | (16-byte aligned)
 // C float [n][ldc] (column-major) when it is kept in shared memory
 __host__ __device__ inline size_t mix_smem(int n, bool c_in_smem)
 {
     const int h = mpad(n) / 2;
-    size_t b = mix_a_floats(n) * 4 + (size_t)h * (16 + 8 + 8) + 4 * 4;
+    size_t b = mix_a_floats(n) * 4 + (size_t)h * (16 + 8 + 8) + 8 * 4 + (size_t)h * 4 + (size_t)((h + 1) & ~1) * 2;
     b += (size_t)((mquads(n) + 1) & ~1) * 2;
     b = (b + 15) & ~(size_t)15;
     if (c_in_smem) b += (size_t)n * mldc(n) * 4;
@@ -107,8 +108,12 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
     int4 *sl = reinterpret_cast<int4 *>(A + mix_a_floats(n));
     float2 *cs = reinterpret_cast<float2 *>(sl + h);
     float *dpp = reinterpret_cast<float *>(cs + h), *dqq = dpp + h;
-    int *flags = reinterpret_cast<int *>(dqq + h);  // [0] rotation in this sweep, [1..3] in this round
-    unsigned short *quad = reinterpret_cast<unsigned short *>(flags + 4);
+    // flags: [0] rotation in this sweep; [1..3] rotation in this round and [4..6] the
+    // round's count of rotating slots, both cycled over three rounds
+    int *flags = reinterpret_cast<int *>(dqq + h);
+    int *rank = flags + 8;                                            // [h]: index in act, or -1
+    unsigned short *act = reinterpret_cast<unsigned short *>(rank + h);  // [h]: the rotating slots
+    unsigned short *quad = act + ((h + 1) & ~1);
     const int nq = mquads(n);
     const size_t c_off = ((size_t)(reinterpret_cast<unsigned char *>(quad + ((nq + 1) & ~1)) - sb) + 15) & ~(size_t)15;
     float *C = C_SMEM ? reinterpret_cast<float *>(sb + c_off) : Cf_s + (size_t)blockIdx.x * n * ldc;
@@ -121,7 +126,7 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
         if (i > j) continue;
         double v = ch.V[e];
         for (int a = 1; a < n_terms; ++a) v = fma(cf[a - 1], ch.V[(size_t)a * n * n + e], v);
-        if (i == j) v += ch.h0[i % N];
+        if (i == j) v += ch.d0 ? ch.d0[i] : ch.h0[i % N];  // d0: the diagonal of a rotated basis
         A[pk(i, j)] = (float)v;
         if (Hg) {
             Hg[e] = v;
@@ -138,8 +143,28 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
         const int P = e / h, P2 = e - P * h;
         if (P < P2) quad[P * h - P * (P + 1) / 2 + (P2 - P - 1)] = (unsigned short)((P << 8) | P2);
     }
-    if (tid < 4) flags[tid] = 0;
+    if (tid < 8) flags[tid] = 0;
     __syncthreads();
+    const int nwarps = nt >> 5, warp = tid >> 5;
+
+    // 2 x 2 block of A in rows of slot P and columns of slot P2 (P < P2): J_P^T B J_P2
+    auto quad_update = [&](int P, int P2) {
+        const float2 r1 = cs[P], r2 = cs[P2];
+        const int4 u = sl[P], v = sl[P2];
+        // packed index of (x, y): base(max) + min
+        const int i00 = u.x <= v.x ? v.z + u.x : u.z + v.x;
+        const int i01 = u.x <= v.y ? v.w + u.x : u.z + v.y;
+        const int i10 = u.y <= v.x ? v.z + u.y : u.w + v.x;
+        const int i11 = u.y <= v.y ? v.w + u.y : u.w + v.y;
+        const float b00 = A[i00], b01 = A[i01], b10 = A[i10], b11 = A[i11];
+        const float c = r1.x, s = r1.y, c2 = r2.x, s2 = r2.y;
+        const float x00 = c2 * b00 - s2 * b01, x01 = s2 * b00 + c2 * b01;
+        const float x10 = c2 * b10 - s2 * b11, x11 = s2 * b10 + c2 * b11;
+        A[i00] = c * x00 - s * x10;
+        A[i01] = c * x01 - s * x11;
+        A[i10] = s * x00 + c * x10;
+        A[i11] = s * x01 + c * x11;
+    };
 
     int sweeps = 0, g3 = 0;  // g3: the round's flag, cycling over three so a reset never races a read
     bool converged = false;
@@ -166,7 +191,10 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
         ++sweeps;
         for (int r = 0; r < M; ++r) {
             const int nx3 = g3 == 2 ? 0 : g3 + 1;
-            if (tid == 0) flags[1 + nx3] = 0;  // last read two rounds ago, before this round's barrier
+            if (tid == 0) {  // last read two rounds ago, before this round's barrier
+                flags[1 + nx3] = 0;
+                flags[4 + nx3] = 0;
+            }
             for (int k = tid; k < h; k += nt) {
                 int p, q;
                 mix_pair(r, k, M, p, q);
@@ -184,6 +212,11 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
                     aqq += t * apq;
                     flags[0] = 1;
                     flags[1 + g3] = 1;
+                    const int idx = atomicAdd(&flags[4 + g3], 1);
+                    act[idx] = (unsigned short)k;
+                    rank[k] = idx;
+                } else {
+                    rank[k] = -1;
                 }
                 sl[k] = make_int4(p, q, pb, qb);
                 cs[k] = make_float2(c, s);
@@ -191,41 +224,44 @@ __global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *
                 dqq[k] = aqq;
             }
             __syncthreads();
-            if (flags[1 + g3]) {  // some slot rotates (the same value for every thread)
-                for (int e = tid; e < nq; e += nt) {
-                    const unsigned pr = quad[e];
-                    const int P = pr >> 8, P2 = pr & 0xFF;
-                    const float2 r1 = cs[P], r2 = cs[P2];
-                    if (r1.y == 0.0f && r2.y == 0.0f) continue;  // both rotations are the identity
-                    const int4 u = sl[P], v = sl[P2];
-                    // packed index of (x, y): base(max) + min
-                    const int i00 = u.x <= v.x ? v.z + u.x : u.z + v.x;
-                    const int i01 = u.x <= v.y ? v.w + u.x : u.z + v.y;
-                    const int i10 = u.y <= v.x ? v.z + u.y : u.w + v.x;
-                    const int i11 = u.y <= v.y ? v.w + u.y : u.w + v.y;
-                    const float b00 = A[i00], b01 = A[i01], b10 = A[i10], b11 = A[i11];
-                    const float c = r1.x, s = r1.y, c2 = r2.x, s2 = r2.y;
-                    const float x00 = c2 * b00 - s2 * b01, x01 = s2 * b00 + c2 * b01;
-                    const float x10 = c2 * b10 - s2 * b11, x11 = s2 * b10 + c2 * b11;
-                    A[i00] = c * x00 - s * x10;
-                    A[i01] = c * x01 - s * x11;
-                    A[i10] = s * x00 + c * x10;
-                    A[i11] = s * x01 + c * x11;
-                }
-                for (int k = tid; k < h; k += nt) {
-                    if (cs[k].y != 0.0f) {
-                        const int4 u = sl[k];
-                        A[u.z + u.x] = dpp[k];
-                        A[u.w + u.y] = dqq[k];
-                        A[u.w + u.x] = 0.0f;
+            const int na = flags[4 + g3];  // rotating slots this round (the same value for every thread)
+            if (na > 0) {
+                if (2 * na >= h) {
+                    // most slots rotate: every slot pair from the table
+                    for (int e = tid; e < nq; e += nt) {
+                        const unsigned pr = quad[e];
+                        const int P = pr >> 8, P2 = pr & 0xFF;
+                        if (cs[P].y == 0.0f && cs[P2].y == 0.0f) continue;  // both rotations are the identity
+                        quad_update(P, P2);
                     }
+                } else {
+                    // few slots rotate (late sweeps, threshold sweeps): only the pairs that
+                    // hold a rotating slot, one warp per rotating slot, lanes over the
+                    // others; a pair of two rotating slots is done once, by the lower
+                    // one's warp.  Each pair keeps its orientation (lower slot's rows),
+                    // so the result does not depend on the order of the rotating list.
+                    for (int i = warp; i < na; i += nwarps) {
+                        const int P = act[i];
+                        for (int P2 = lane; P2 < h; P2 += 32) {
+                            if (P2 == P || (P2 < P && rank[P2] >= 0)) continue;
+                            if (P < P2) quad_update(P, P2);
+                            else quad_update(P2, P);
+                        }
+                    }
+                }
+                for (int i = tid; i < na; i += nt) {
+                    const int k = act[i];
+                    const int4 u = sl[k];
+                    A[u.z + u.x] = dpp[k];
+                    A[u.w + u.y] = dqq[k];
+                    A[u.w + u.x] = 0.0f;
                 }
                 // C is column-major (column s contiguous, stride ldc): one warp per
                 // rotation, each lane four consecutive rows of the two columns
                 const int nv = ldc >> 2;
-                for (int k = tid >> 5; k < h; k += nt >> 5) {
+                for (int i = warp; i < na; i += nwarps) {
+                    const int k = act[i];
                     const float2 r1 = cs[k];
-                    if (r1.y == 0.0f) continue;
                     const int4 u = sl[k];
                     float4 *Cp = reinterpret_cast<float4 *>(C + (size_t)u.x * ldc);
                     float4 *Cq = reinterpret_cast<float4 *>(C + (size_t)u.y * ldc);

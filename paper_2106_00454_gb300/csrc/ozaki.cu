@@ -257,9 +257,10 @@ cudaError_t launch_oz_split(int n, int items, bool cols, const double *M, __nv_b
 
 // C = A B from the row slices of A and the column slices of B.
 cudaError_t launch_oz_gemm_slices(int n, int items, const __nv_bfloat16 *sa, const int *ea, const __nv_bfloat16 *sb,
-                                  const int *eb, double *C, cudaStream_t st, int digits, bool sym, int *err)
+                                  const int *eb, double *C, cudaStream_t st, int digits, bool sym, int *err,
+                                  int a_items)
 {
-    return launch_oz_gemm_tc(n, items, sa, ea, sb, eb, C, digits, sym, err, st);
+    return launch_oz_gemm_tc(n, items, sa, ea, sb, eb, C, digits, sym, err, st, a_items);
 }
 
 // C = op(A) B for `items` n x n FP64 matrices (op(A) = A^T when ta), through

@@ -234,7 +234,7 @@ __device__ __forceinline__ TcTile tc_tile(int t, int per_item, int TC, bool sym)
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_oz_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int n, int Kp,
                  int dmax, bool sym, int per_item, int TC, int ntiles, const int *ea_all, const int *eb_all,
-                 double *C_all, int *err)
+                 double *C_all, int *err, int a_mod)
 {
     extern __shared__ unsigned char tc_raw[];
     const uint32_t raw_s = smem_u32(tc_raw);
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     const uint32_t sA = ring_s + (uint32_t)(stage * kTcStageBytes);
                     mbar_expect_tx(full_s + 8u * stage, (uint32_t)kTcStageBytes);
-                    tma_load_3d(sA, &mapA, k0, tl.row0, tl.b * kOzDigits, full_s + 8u * stage);
+                    tma_load_3d(sA, &mapA, k0, tl.row0, (tl.b % a_mod) * kOzDigits, full_s + 8u * stage);
                     tma_load_3d(sA + kTcAStage, &mapB, k0, tl.col0, tl.b * kOzDigits, full_s + 8u * stage);
                     ++issued;
                     if (++stage == kTcStages) {
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (failed) break;
             const int r = tl.row0 + row_in;
             if (r < n) {
-                const int *ea = ea_all + (size_t)tl.b * n, *eb = eb_all + (size_t)tl.b * n;
+                const int *ea = ea_all + (size_t)(tl.b % a_mod) * n, *eb = eb_all + (size_t)tl.b * n;
                 double *C = C_all + (size_t)tl.b * n * n;
                 const int er = ea[r];
 #pragma unroll
@@ -469,14 +469,18 @@ static bool tc_map(CUtensorMap *m, const __nv_bfloat16 *S, int n, int Kp, int it
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// a_items: the number of A slice sets; item b multiplies A set b % a_items (a_items =
+// items: one A per item; a_items < items: A sets shared cyclically, e.g. one per
+// channel of a bucket whose items run channel-fastest).
 cudaError_t launch_oz_gemm_tc(int n, int items, const __nv_bfloat16 *sa, const int *ea, const __nv_bfloat16 *sb,
-                              const int *eb, double *C, int digits, bool sym, int *err, cudaStream_t st)
+                              const int *eb, double *C, int digits, bool sym, int *err, cudaStream_t st, int a_items)
 {
-    if (n < 1 || items < 1 || digits < 1 || digits > kOzDigits) return cudaErrorInvalidValue;
+    if (a_items <= 0) a_items = items;
+    if (n < 1 || items < 1 || digits < 1 || digits > kOzDigits || a_items > items) return cudaErrorInvalidValue;
     const int Kp = oz_kpad(n);
     if (Kp % kTcKC != 0) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!tc_map(&ma, sa, n, Kp, items, kTcM) || !tc_map(&mb, sb, n, Kp, items, kTcN)) return cudaErrorInvalidValue;
+    if (!tc_map(&ma, sa, n, Kp, a_items, kTcM) || !tc_map(&mb, sb, n, Kp, items, kTcN)) return cudaErrorInvalidValue;
     const int TR = (n + kTcM - 1) / kTcM, TC = (n + kTcN - 1) / kTcN;
     int per_item = TR * TC;
     if (sym) {
@@ -496,7 +500,7 @@ cudaError_t launch_oz_gemm_tc(int n, int items, const __nv_bfloat16 *sa, const i
     if (e != cudaSuccess) return e;
     const int grid = (int)(ntiles < sms ? ntiles : sms);
     k_oz_gemm_tc<<<grid, kTcThreads, kTcSmem, counted(st)>>>(ma, mb, n, Kp, digits - 1, sym, per_item, TC, (int)ntiles, ea, eb,
-                                                    C, err);
+                                                    C, err, a_items);
     return cudaGetLastError();
 }
 

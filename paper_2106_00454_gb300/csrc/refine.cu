@@ -207,10 +207,16 @@ size_t refine_scratch_per_item(int n, int engine)
 // On entry Xs (the first n^2-double block of each item) holds the FP32-solve
 // eigenvectors as FP64 and H (the second block) the FP64 Hamiltonian, both
 // written by the FP32 solve.  iters must be even.
+// rot_s, rot_e (tensor engine only): the digit slices of the rows of the nw
+// channels' basis matrices C0 when H and X are given in that basis (C0^T H C0
+// and its eigenvectors X'); the refined vectors are then rotated back, X = C0 X',
+// before the sort.
 cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_samples, int sample0, int n,
                           int n_terms, const double *coeffs, void *scratch, double *eps_all, double *X_all,
-                          int iters, int engine, cudaStream_t st, int *err)
+                          int iters, int engine, cudaStream_t st, int *err, const __nv_bfloat16 *rot_s,
+                          const int *rot_e)
 {
+    if (rot_s && engine != 0) return cudaErrorInvalidValue;
     (void)n_terms;
     (void)coeffs;
     if (iters < 0 || (iters & 1)) return cudaErrorInvalidValue;
@@ -268,8 +274,15 @@ cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_s
     // lam holds the last iteration's Rayleigh quotients S_ii / G_ii of the vectors
     // entering it; its update moves each vector by |E| ~ 1e-8 and a Rayleigh
     // quotient by O(|E|^2 ||H||), below FP64 resolution, so no further H X is formed
+    const double *xout = x;  // == Xs after an even number of iterations
+    if (rot_s) {
+        // X = C0 X' (the same C0 for every sample of a channel: items run channel-fastest)
+        CKR(launch_oz_split(n, items, true, x, sXc, eXc, st));
+        CKR(launch_oz_gemm_slices(n, items, rot_s, rot_e, sXc, eXc, xn, st, 6, false, err, nw));
+        xout = xn;
+    }
 #undef CKR
-    k_sort_eig<<<items, 256, sort_eig_smem(n), counted(st)>>>(chans, work, nw, sample0, n, lam, Xs, eps_all, X_all);
+    k_sort_eig<<<items, 256, sort_eig_smem(n), counted(st)>>>(chans, work, nw, sample0, n, lam, xout, eps_all, X_all);
     return cudaGetLastError();
 }
 

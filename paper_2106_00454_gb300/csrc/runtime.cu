@@ -58,6 +58,20 @@ struct VSetH {
     std::map<int, std::vector<int>> buckets;  // n -> channel indices
     std::map<int, int *> bucket_dev;          // n -> device list of channel indices
     int *ident_dev = nullptr;                 // [n_ch] = 0..n_ch-1 (plain mode)
+    // Mean-potential eigenbasis of the mixed path (built on first use): per channel
+    // C0, eps0 = eig(diag(H0) + V0) in FP64 and the rotated terms W_a = C0^T V_a C0
+    // (W_0 = 0), so that C0^T H(c) C0 = diag(eps0) + sum_a c_a W_a; per size bucket
+    // the digit slices of the rows of its channels' C0 for the back-rotation X = C0 X'.
+    struct RotB {
+        double *C0 = nullptr;  // [nw][n][n], the bucket's channels in bucket order
+        __nv_bfloat16 *sC = nullptr;
+        int *eC = nullptr;
+    };
+    std::unique_ptr<std::mutex> rot_mu{new std::mutex};
+    int rot_state = 0;  // 0 not built, 1 ready, -1 failed (the mixed path then runs in the original basis)
+    double *Vr = nullptr, *eps0 = nullptr, *C0 = nullptr;
+    std::vector<ChanDev> cd_rot;  // host copy: V -> W_a, d0 -> eps0 (offsets zero)
+    std::map<int, RotB> rotb;
 };
 
 struct EigH {
@@ -65,7 +79,9 @@ struct EigH {
     double *eps = nullptr, *C = nullptr, *coeffs = nullptr;
     // (the mixed path leaves refined FP64 eigenpairs in eps / C as well)
     int *status = nullptr;
-    ChanDev *cd_dev = nullptr;  // vset channels with this eig's offsets
+    ChanDev *cd_dev = nullptr;      // vset channels with this eig's offsets
+    ChanDev *cd_rot_dev = nullptr;  // the same in the mean-potential eigenbasis (mixed path)
+    bool rot = false;               // this batch's eigensolve runs in that basis
     size_t eps_len = 0, c_len = 0, coeff_len = 0, status_len = 0, cd_len = 0;
 };
 
@@ -118,6 +134,7 @@ struct wpcd_ctx {
     std::mutex mu;
     int exec_mode = WPCD_EXEC_BATCHED;
     int refine_engine = WPCD_REFINE_TENSOR;
+    int rotate = 1;  // mixed path in the mean-potential eigenbasis (WPCD_OPT_ROTATE)
     int autotune = 1;
     int n_sm = 0;
     struct Tuned {
@@ -148,7 +165,6 @@ struct wpcd_ctx {
     // new tuning); a graph captured under another generation is dropped.
     double ip_frac = 0.5;  // interpolation point of the averaged resolvents (Sec. 5.1.1)
     int big_slots = 0;     // CTAs of the global-memory eigensolver (0: automatic)
-    int l2_bytes = 0;
     int use_graphs = 1;
     std::atomic<unsigned long long> graph_gen{0};
     struct GraphE {
@@ -309,6 +325,7 @@ void free_eig(wpcd_ctx *c, EigH &e)
     dfree(c, e.coeffs);
     dfree(c, e.status);
     dfree(c, e.cd_dev);
+    dfree(c, e.cd_rot_dev);
     e = EigH();
 }
 
@@ -318,6 +335,13 @@ void free_vset(wpcd_ctx *c, VSetH &v)
     dfree(c, v.cd_dev);
     dfree(c, v.ident_dev);
     for (auto &kv : v.bucket_dev) dfree(c, kv.second);
+    dfree(c, v.Vr);
+    dfree(c, v.eps0);
+    dfree(c, v.C0);
+    for (auto &kv : v.rotb) {
+        dfree(c, kv.second.sC);
+        dfree(c, kv.second.eC);
+    }
 }
 
 void free_mi(wpcd_ctx *c, MiH &m)
@@ -396,6 +420,118 @@ int pick_threads(wpcd_ctx *c, Exec &X, int n, int prec, int nw, int nsmp, F laun
     return t.threads;
 }
 
+// Build the mean-potential eigenbasis of a vset (once, on the executor's
+// stream, synchronising; concurrent callers wait on the vset's lock):
+//   C0, eps0 = eig(diag(H0) + V0) with the FP64 Jacobi kernels;
+//   W_a = C0^T V_a C0 (a >= 1) with FP64 products, W_0 = 0;
+//   per size bucket, the digit slices of the rows of its channels' C0.
+// The FP32 eigensolve of the mixed path then starts from C0^T H C0 =
+// diag(eps0) + sum_a c_a W_a, an orthogonal similarity of H that is nearly
+// diagonal for parameter samples near the mean (fewer Jacobi sweeps), and the
+// refined eigenvectors are rotated back, X = C0 X'.
+wpcd_status ensure_rotation(wpcd_ctx *c, Exec &X, VSetH &v)
+{
+    std::lock_guard<std::mutex> lk(*v.rot_mu);
+    if (v.rot_state != 0) return WPCD_OK;
+    v.rot_state = -1;
+    size_t ne = 0, nc = 0, vlen = 0;
+    int nmax = 0;
+    std::vector<ChanDev> cd = v.cd;  // offsets of a one-sample eigen buffer, bucket by bucket
+    std::map<int, size_t> bstart;
+    for (auto &kv : v.buckets) {
+        bstart[kv.first] = nc;
+        for (int k : kv.second) {
+            cd[k].eps_off = (long long)ne;
+            cd[k].c_off = (long long)nc;
+            ne += cd[k].n;
+            nc += (size_t)cd[k].n * cd[k].n;
+        }
+    }
+    for (auto &d : v.cd) {
+        vlen += (size_t)v.n_terms * d.n * d.n;
+        nmax = std::max(nmax, d.n);
+    }
+    wpcd_status st;
+    if ((st = dalloc(c, &v.eps0, ne)) || (st = dalloc(c, &v.C0, nc)) || (st = dalloc(c, &v.Vr, vlen))) return st;
+    ChanDev *cd_tmp = nullptr;
+    int *status = nullptr;
+    void *big = nullptr;
+    double *Crep = nullptr, *T = nullptr;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(X.stream);
+        dfree(c, cd_tmp);
+        dfree(c, status);
+        dfree(c, big);
+        dfree(c, Crep);
+        dfree(c, T);
+    };
+    if ((st = dalloc(c, &cd_tmp, (size_t)v.n_ch)) || (st = dalloc(c, &status, (size_t)v.n_ch))) {
+        cleanup();
+        return st;
+    }
+    CK(cudaMemcpyAsync(cd_tmp, cd.data(), sizeof(ChanDev) * v.n_ch, cudaMemcpyHostToDevice, X.stream));
+    for (auto &kv : v.buckets) {
+        const int n = kv.first, nw = (int)kv.second.size();
+        if (jacobi_fits_smem(n, true)) {
+            CK(launch_jacobi_f64(cd_tmp, v.bucket_dev[n], nw, 1, 0, 1, nullptr, n, v.eps0, v.C0, status, v.n_ch,
+                                 X.err, X.stream, 256));
+        } else {
+            const size_t slot_b = (jacobi_big_scratch_bytes(n, true) + 255) & ~(size_t)255;
+            cudaStreamSynchronize(X.stream);
+            dfree(c, big);
+            big = nullptr;
+            if ((st = dmalloc(c, &big, slot_b * nw))) {
+                cleanup();
+                return st;
+            }
+            CK(launch_jacobi_big(true, cd_tmp, v.bucket_dev[n], nw, 1, 0, 1, nullptr, n, big, nw, v.eps0, v.C0,
+                                 nullptr, nullptr, nullptr, status, v.n_ch, X.err, X.stream));
+        }
+    }
+    const int na = v.n_terms - 1;
+    if (na > 0 && ((st = dalloc(c, &Crep, (size_t)na * nmax * nmax)) || (st = dalloc(c, &T, (size_t)na * nmax * nmax)))) {
+        cleanup();
+        return st;
+    }
+    for (int k = 0; k < v.n_ch; ++k) {
+        const int n = cd[k].n;
+        const size_t nn = (size_t)n * n;
+        double *Vr_k = v.Vr + (v.cd[k].V - v.V);
+        CK(cudaMemsetAsync(Vr_k, 0, nn * sizeof(double), X.stream));  // W_0 = 0
+        if (na == 0) continue;
+        for (int a = 0; a < na; ++a)
+            CK(cudaMemcpyAsync(Crep + (size_t)a * nn, v.C0 + cd[k].c_off, nn * sizeof(double),
+                               cudaMemcpyDeviceToDevice, X.stream));
+        CK(launch_batched_dgemm(n, na, false, v.cd[k].V + nn, Crep, T, nullptr, WPCD_REFINE_FP64, X.stream));
+        CK(launch_batched_dgemm(n, na, true, Crep, T, Vr_k + nn, nullptr, WPCD_REFINE_FP64, X.stream));
+    }
+    for (auto &kv : v.buckets) {
+        const int n = kv.first, nw = (int)kv.second.size();
+        VSetH::RotB &rb = v.rotb[n];
+        rb.C0 = v.C0 + bstart[n];
+        if ((st = dalloc(c, &rb.sC, (size_t)nw * oz_slice_elems(n))) || (st = dalloc(c, &rb.eC, (size_t)nw * n))) {
+            cleanup();
+            return st;
+        }
+        CK(launch_oz_split(n, nw, false, rb.C0, rb.sC, rb.eC, X.stream));
+    }
+    std::vector<int> hs(v.n_ch);
+    int herr = 0;
+    CK(cudaMemcpyAsync(hs.data(), status, sizeof(int) * v.n_ch, cudaMemcpyDeviceToHost, X.stream));
+    CK(cudaMemcpyAsync(&herr, X.err, sizeof(int), cudaMemcpyDeviceToHost, X.stream));
+    cleanup();
+    bool ok = herr == 0;
+    for (int k = 0; k < v.n_ch; ++k) ok &= hs[k] >= 0;
+    if (!ok) return WPCD_OK;  // stays -1: the mixed path keeps the original basis
+    v.cd_rot = v.cd;
+    for (int k = 0; k < v.n_ch; ++k) {
+        v.cd_rot[k].V = v.Vr + (v.cd[k].V - v.V);
+        v.cd_rot[k].d0 = v.eps0 + cd[k].eps_off;
+    }
+    v.rot_state = 1;
+    return WPCD_OK;
+}
+
 // Allocate (or reuse) eigenpair storage for `S` samples of vset v and upload
 // the channel table with this batch's offsets (a pageable host copy, so it
 // stays outside CUDA graphs).
@@ -421,6 +557,7 @@ wpcd_status diag_prep(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, int S, int pr
         if ((st = dalloc(c, &e.coeffs, coeff_len))) return st;
         if ((st = dalloc(c, &e.status, (size_t)S * v.n_ch))) return st;
         if ((st = dalloc(c, &e.cd_dev, (size_t)v.n_ch))) return st;
+        if ((st = dalloc(c, &e.cd_rot_dev, (size_t)v.n_ch))) return st;
         e.eps_len = eps_len;
         e.c_len = c_len;
         e.coeff_len = coeff_len;
@@ -431,6 +568,20 @@ wpcd_status diag_prep(wpcd_ctx *c, Exec &X, VSetH &v, int vset_id, int S, int pr
     e.n_samples = S;
     e.prec = prec;
     CK(cudaMemcpyAsync(e.cd_dev, cd.data(), sizeof(ChanDev) * v.n_ch, cudaMemcpyHostToDevice, X.stream));
+    e.rot = false;
+    if (prec == WPCD_PREC_MIXED && c->rotate && c->refine_engine == WPCD_REFINE_TENSOR) {
+        if ((st = ensure_rotation(c, X, v))) return st;
+        if (v.rot_state == 1) {
+            std::vector<ChanDev> cr = v.cd_rot;
+            for (int k = 0; k < v.n_ch; ++k) {
+                cr[k].eps_off = cd[k].eps_off;
+                cr[k].c_off = cd[k].c_off;
+            }
+            CK(cudaMemcpyAsync(e.cd_rot_dev, cr.data(), sizeof(ChanDev) * v.n_ch, cudaMemcpyHostToDevice,
+                               X.stream));
+            e.rot = true;
+        }
+    }
     return WPCD_OK;
 }
 
@@ -447,11 +598,10 @@ wpcd_status run_bucket_big(wpcd_ctx *c, Exec &X, VSetH &v, EigH &e, const double
     if (!c->n_sm) cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
     const int occ = std::max(1, jacobi_big_occupancy(n, f64));
     const size_t slot_b = (jacobi_big_scratch_bytes(n, f64) + 255) & ~(size_t)255;
-    // CTAs in flight: FP64 is bound by the FP64 pipe, so every resident CTA; FP32 by the
-    // traffic of its matrix copies, which should stay L2-resident
-    if (!c->l2_bytes) cudaDeviceGetAttribute(&c->l2_bytes, cudaDevAttrL2CacheSize, c->device);
+    // CTAs in flight: every resident one.  Each CTA's round is bound by the latency of
+    // its L2 round trips, so the rate grows with the CTAs in flight (measured at
+    // n = 512, FP32: 24 / 48 / 76 / 152 CTAs give 167 / 332 / 953 / 1518 solves/s)
     int cap = c->n_sm * occ;
-    if (!f64) cap = std::min(cap, std::max(c->n_sm / 4, (int)((size_t)c->l2_bytes * 3 / 4 / slot_b)));
     if (c->big_slots > 0) cap = c->big_slots;
     if (f64) {
         const int items = nsmp * nw;
@@ -478,13 +628,14 @@ wpcd_status run_bucket_big(wpcd_ctx *c, Exec &X, VSetH &v, EigH &e, const double
         {
             Launch L(c, X, WPCD_PHASE_EIGEN);
             // X, H and lambda in the layout of launch_refine (blocks 0, 1 and the lambda block)
-            CK(launch_jacobi_big(false, e.cd_dev, work, nw, ns, smp0 + s0, v.n_terms, cf, n, base + ref_b, slots,
-                                 nullptr, nullptr, Xs + (size_t)5 * ns * nw * n * n, Xs,
+            CK(launch_jacobi_big(false, e.rot ? e.cd_rot_dev : e.cd_dev, work, nw, ns, smp0 + s0, v.n_terms, cf, n,
+                                 base + ref_b, slots, nullptr, nullptr, Xs + (size_t)5 * ns * nw * n * n, Xs,
                                  Xs + (size_t)ns * nw * n * n, e.status, v.n_ch, X.err, X.stream));
         }
         Launch L(c, X, WPCD_PHASE_REFINE);
+        const VSetH::RotB *rb = e.rot ? &v.rotb.at(n) : nullptr;
         CK(launch_refine(e.cd_dev, work, nw, ns, smp0 + s0, n, v.n_terms, cf, base, e.eps, e.C, kRefineIters,
-                         c->refine_engine, X.stream, X.err));
+                         c->refine_engine, X.stream, X.err, rb ? rb->sC : nullptr, rb ? rb->eC : nullptr));
     }
     return WPCD_OK;
 }
@@ -515,9 +666,9 @@ wpcd_status diag_body(wpcd_ctx *c, Exec &X, VSetH &v, const double *coeffs, int 
             unsigned char *base = static_cast<unsigned char *>(X.ws_ref.p);
             double *Xs = reinterpret_cast<double *>(base);
             const size_t c_off = (refine_scratch_per_item(n, c->refine_engine) * nw * ns + 255) & ~(size_t)255;
-            return launch_jacobi_mixed(e.cd_dev, work, nw, ns, smp0, v.n_terms, cf, n, Xs + (size_t)5 * ns * nw * n * n,
-                                       Xs, reinterpret_cast<float *>(base + c_off), Xs + (size_t)ns * nw * n * n,
-                                       e.status, v.n_ch, X.err, X.stream, th);
+            return launch_jacobi_mixed(e.rot ? e.cd_rot_dev : e.cd_dev, work, nw, ns, smp0, v.n_terms, cf, n,
+                                       Xs + (size_t)5 * ns * nw * n * n, Xs, reinterpret_cast<float *>(base + c_off),
+                                       Xs + (size_t)ns * nw * n * n, e.status, v.n_ch, X.err, X.stream, th);
         });
         if (threads < 0) return WPCD_ERR_CUDA;
         if (prec == WPCD_PREC_FP64) {
@@ -542,13 +693,14 @@ wpcd_status diag_body(wpcd_ctx *c, Exec &X, VSetH &v, const double *coeffs, int 
             {
                 Launch L(c, X, WPCD_PHASE_EIGEN);
                 // the FP64 H goes to the second n^2 block of the refinement scratch (layout of launch_refine)
-                CK(launch_jacobi_mixed(e.cd_dev, work, nw, ns, smp0 + s0, v.n_terms, cf, n,
+                CK(launch_jacobi_mixed(e.rot ? e.cd_rot_dev : e.cd_dev, work, nw, ns, smp0 + s0, v.n_terms, cf, n,
                                        Xs + (size_t)5 * ns * nw * n * n, Xs, Cf, Xs + (size_t)ns * nw * n * n,
                                        e.status, v.n_ch, X.err, X.stream, threads));
             }
             Launch L(c, X, WPCD_PHASE_REFINE);
+            const VSetH::RotB *rb = e.rot ? &v.rotb.at(n) : nullptr;
             CK(launch_refine(e.cd_dev, work, nw, ns, smp0 + s0, n, v.n_terms, cf, base, e.eps, e.C, kRefineIters,
-                             c->refine_engine, X.stream, X.err));
+                             c->refine_engine, X.stream, X.err, rb ? rb->sC : nullptr, rb ? rb->eC : nullptr));
         }
         return WPCD_OK;
     };
@@ -729,6 +881,10 @@ wpcd_status wpcd_set_option(wpcd_ctx *c, int key, int value)
     }
     if (key == WPCD_OPT_REFINE && (value == WPCD_REFINE_TENSOR || value == WPCD_REFINE_FP64)) {
         c->refine_engine = value;
+        return WPCD_OK;
+    }
+    if (key == WPCD_OPT_ROTATE && (value == 0 || value == 1)) {
+        c->rotate = value;
         return WPCD_OK;
     }
     if (key == WPCD_OPT_BIG_SLOTS && value >= 0) {

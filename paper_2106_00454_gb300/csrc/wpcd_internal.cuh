@@ -83,6 +83,7 @@ struct ChanDev {
     const double *wq;   // fine weights [N*Q]
     const double *h0;   // <x_i|h0|x_i> [N]
     const double *V;    // projected terms [n_terms][n][n]
+    const double *d0;   // NULL, or the diagonal term [n] that replaces H0 (the eigensolvers only)
     long long eps_off;  // offset of this channel's eigenvalue block [S][n] in an eig buffer
     long long c_off;    // offset of this channel's eigenvector block [S][n][n]
 };
@@ -275,13 +276,15 @@ cudaError_t launch_oz_gemm(int n, int items, bool ta, const double *A, const dou
 cudaError_t launch_oz_split(int n, int items, bool cols, const double *M, __nv_bfloat16 *S, int *e, cudaStream_t st);
 cudaError_t launch_oz_gemm_slices(int n, int items, const __nv_bfloat16 *sa, const int *ea, const __nv_bfloat16 *sb,
                                   const int *eb, double *C, cudaStream_t st, int digits = 6, bool sym = false,
-                                  int *err = nullptr);
+                                  int *err = nullptr, int a_items = 0);
 cudaError_t launch_oz_gemm_tc(int n, int items, const __nv_bfloat16 *sa, const int *ea, const __nv_bfloat16 *sb,
-                              const int *eb, double *C, int digits, bool sym, int *err, cudaStream_t st);
+                              const int *eb, double *C, int digits, bool sym, int *err, cudaStream_t st,
+                              int a_items = 0);
 size_t refine_scratch_per_item(int n, int engine);
 cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_samples, int sample0, int n,
                           int n_terms, const double *coeffs, void *scratch, double *eps_all, double *X_all,
-                          int iters, int engine, cudaStream_t st, int *err = nullptr);
+                          int iters, int engine, cudaStream_t st, int *err = nullptr,
+                          const __nv_bfloat16 *rot_s = nullptr, const int *rot_e = nullptr);
 cudaError_t launch_batched_dgemm(int n, int items, bool ta, const double *A, const double *B, double *C,
                                  void *scratch, int engine, cudaStream_t st, int *err = nullptr);
 size_t batched_dgemm_scratch(int n, int items);

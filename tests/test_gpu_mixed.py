@@ -128,3 +128,31 @@ def test_mixed_odd_nwp(ctx, orc, n_wp):
     wl = dataclasses.replace(wl, coeffs=W.coefficient_samples(3))
     md = api.Model(ctx, wl)
     _report(f"odd_nwp{n_wp}", compare_mixed(wl, gpu_run(ctx, md, wl, prec=MIXED), oracle_run(orc, wl)))
+
+
+def test_mean_potential_basis_same_results_fewer_sweeps(ctx, orc):
+    """The FP32 eigensolve in the eigenbasis of diag(H0) + V0 (the default) and in
+    the original basis both match the oracle at the mixed tolerances on the
+    N_WP = 150 workload; the rotated start takes fewer Jacobi sweeps."""
+    import torch
+
+    from paper_2106_00454_gb300 import api
+    wl = W.workload_mixed(n_samples=4)
+    md = api.Model(ctx, wl)
+    ora = oracle_run(orc, wl)
+    cf = torch.tensor(wl.coeffs, dtype=torch.float64, device="cuda:0")
+    sweeps = {}
+    for on in (True, False):
+        ctx.set_rotate(on)
+        try:
+            _report(f"nwp150_rotate_{int(on)}", compare_mixed(wl, gpu_run(ctx, md, wl, prec=MIXED), ora))
+            eid = ctx.diag(md.vset, cf, 4, prec=MIXED)
+            st = torch.zeros((4, len(wl.channels)), dtype=torch.int32, device="cuda:0")
+            ctx.diag_status(eid, st)
+            ctx.sync()
+            ctx.release(eid)
+        finally:
+            ctx.set_rotate(True)
+        sweeps[on] = st.cpu().numpy()
+    assert (sweeps[True] > 0).all() and (sweeps[False] > 0).all()
+    assert sweeps[True].sum() < sweeps[False].sum(), (sweeps[True].sum(), sweeps[False].sum())
