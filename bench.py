@@ -79,6 +79,7 @@ def parse():
     ap.add_argument("--cpu-samples", type=int, default=4, help="oracle sample size for the CPU baseline")
     ap.add_argument("--ref-samples", type=int, default=2, help="oracle samples per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--one-iter-leg", type=int, default=1, help="time the opt-in single refinement iteration")
     ap.add_argument("--secondary", default="on", choices=["on", "off"],
                     help="the 4096 x 15-channel batched workload, MI comparison and spin observables")
     ap.add_argument("--serve-seconds", type=float, default=30.0,
@@ -572,6 +573,8 @@ def run_wpcd(args, ws, rank, lrank):
 
         # the mixed path against the FP64 path on the same GPU (a slice) and both against the oracle
         accuracy, acc_oracle = None, None
+        d6 = s6 = od = os_ = None
+        ko = 0
         k = min(args.check_samples, S)
         if k > 0:
             t64 = torch.empty((k, nch, nE, 2, 2, 2), dtype=torch.float64, device=dev)
@@ -597,6 +600,29 @@ def run_wpcd(args, ws, rank, lrank):
                                             "max_sigma_rel_err": float(np.max(np.abs(s6[:ko] - os_) / os_))},
                               "tolerances": {"mixed": "1e-3 deg, 0.01 mb", "fp64": "1e-10 rel T, 1e-8 deg"}}
             del t64, d64, s64
+
+        # opt-in single FP64 refinement iteration on the headline workload: its time and its errors
+        one_iter = None
+        if prec == api.PREC_MIXED and args.one_iter_leg:
+            ctx.set_refine_iters(1)
+            t1 = torch.empty((S, nch, nE, 2, 2, 2), dtype=torch.float64, device=dev)
+            d1 = torch.empty((S, nch, nE, 3), dtype=torch.float64, device=dev)
+            s1 = torch.empty((S, nE), dtype=torch.float64, device=dev)
+
+            def step1():
+                ctx.solve(md.vset, cf, S, e, t1, d1, s1, prec=prec)
+            for _ in range(2):
+                step1()
+            ms1, _ = device_steps(ctx, step1, 1, flush, stream)
+            ctx.set_refine_iters(2)
+            d1n, s1n = d1.cpu().numpy(), s1.cpu().numpy()
+            one_iter = {"refine_iterations": 1, "value": S * nch / (ms1[0] * 1e-3), "unit": UNIT,
+                        "ms_per_step": ms1[0], "note": "opt-in (WPCD_OPT_REFINE_ITERS = 1); the headline uses 2"}
+            if accuracy is not None:
+                one_iter["vs_fp64_gpu"] = phase_err(wl, d1n[:k], s1n[:k], d6, s6)
+            if acc_oracle is not None:
+                one_iter["vs_oracle"] = phase_err(wl, d1n[:ko], s1n[:ko], od, os_)
+            del t1, d1, s1
 
         # same-GPU FP64 baselines: batched (one launch per size bucket) and plain (one solve per launch)
         base = {}
@@ -708,6 +734,7 @@ def run_wpcd(args, ws, rank, lrank):
             "autotune": ctx.tuning(),
             "accuracy_vs_fp64": accuracy,
             "accuracy_vs_oracle": acc_oracle,
+            "mixed_one_refinement_iteration": one_iter,
             **base,
             "clocks": clocks,
         }

@@ -19,7 +19,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 AVG_FREE_BIN, AVG_SWP_INDEX, POINT = 0, 1, 2  # resolvent (wpcd_resolvent)
 EXEC_BATCHED, EXEC_PLAIN = 0, 1
 REFINE_TENSOR, REFINE_FP64 = 0, 1
-OPT_EXEC, OPT_REFINE, OPT_AUTOTUNE, OPT_GRAPH, OPT_BIG_SLOTS, OPT_ROTATE = 1, 2, 3, 4, 5, 6
+OPT_EXEC, OPT_REFINE, OPT_AUTOTUNE, OPT_GRAPH, OPT_BIG_SLOTS, OPT_ROTATE, OPT_REFINE_ITERS = 1, 2, 3, 4, 5, 6, 7
 
 
 class WpcdError(RuntimeError):
@@ -88,6 +88,10 @@ class Context:
     def set_interp_point(self, frac: float):
         """Interpolation point of every bin as a fraction of it (Sec. 5.1.1; 0.5 = midpoint)."""
         _ck(self.lib.wpcd_set_interp_point(self.h, float(frac)), "wpcd_set_interp_point")
+
+    def set_refine_iters(self, iters: int):
+        """FP64 refinement iterations of the mixed path (1..4, default 2)."""
+        _ck(self.lib.wpcd_set_option(self.h, OPT_REFINE_ITERS, int(iters)), "wpcd_set_option")
 
     def set_rotate(self, on: bool):
         """Mixed path: FP32 eigensolve in the mean-potential eigenbasis (default on)."""

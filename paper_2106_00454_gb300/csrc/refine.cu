@@ -206,7 +206,7 @@ size_t refine_scratch_per_item(int n, int engine)
 // scratch: refine_scratch_per_item(n, engine) bytes per item, carved here.
 // On entry Xs (the first n^2-double block of each item) holds the FP32-solve
 // eigenvectors as FP64 and H (the second block) the FP64 Hamiltonian, both
-// written by the FP32 solve.  iters must be even.
+// written by the FP32 solve.
 // rot_s, rot_e (tensor engine only): the digit slices of the rows of the nw
 // channels' basis matrices C0 when H and X are given in that basis (C0^T H C0
 // and its eigenvectors X'); the refined vectors are then rotated back, X = C0 X',
@@ -219,7 +219,7 @@ cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_s
     if (rot_s && engine != 0) return cudaErrorInvalidValue;
     (void)n_terms;
     (void)coeffs;
-    if (iters < 0 || (iters & 1)) return cudaErrorInvalidValue;
+    if (iters < 0) return cudaErrorInvalidValue;
     const int items = n_samples * nw;
     const size_t nn = (size_t)items * n * n;
     double *Xs = static_cast<double *>(scratch);
@@ -274,7 +274,7 @@ cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_s
     // lam holds the last iteration's Rayleigh quotients S_ii / G_ii of the vectors
     // entering it; its update moves each vector by |E| ~ 1e-8 and a Rayleigh
     // quotient by O(|E|^2 ||H||), below FP64 resolution, so no further H X is formed
-    const double *xout = x;  // == Xs after an even number of iterations
+    const double *xout = x;  // the refined vectors (Xs after an even number of iterations, else Y)
     if (rot_s) {
         // X = C0 X' (the same C0 for every sample of a channel: items run channel-fastest)
         CKR(launch_oz_split(n, items, true, x, sXc, eXc, st));

@@ -39,7 +39,7 @@ using namespace wpcd;
 namespace {
 
 constexpr size_t kRefineScratchBytes = (size_t)32 << 30;  // mixed path: refinement scratch per bucket chunk (one chunk per bucket up to ~7000 samples of n = 200)
-constexpr int kRefineIters = 2;                            // FP64 refinement iterations (even)
+constexpr int kRefineIters = 2;                            // FP64 refinement iterations (default)
 constexpr size_t kGraphCache = 64;                         // wpcd_solve keys remembered for CUDA graphs
 
 struct MeshH {
@@ -135,6 +135,7 @@ struct wpcd_ctx {
     int exec_mode = WPCD_EXEC_BATCHED;
     int refine_engine = WPCD_REFINE_TENSOR;
     int rotate = 1;  // mixed path in the mean-potential eigenbasis (WPCD_OPT_ROTATE)
+    int refine_iters = kRefineIters;  // WPCD_OPT_REFINE_ITERS
     int autotune = 1;
     int n_sm = 0;
     struct Tuned {
@@ -634,7 +635,7 @@ wpcd_status run_bucket_big(wpcd_ctx *c, Exec &X, VSetH &v, EigH &e, const double
         }
         Launch L(c, X, WPCD_PHASE_REFINE);
         const VSetH::RotB *rb = e.rot ? &v.rotb.at(n) : nullptr;
-        CK(launch_refine(e.cd_dev, work, nw, ns, smp0 + s0, n, v.n_terms, cf, base, e.eps, e.C, kRefineIters,
+        CK(launch_refine(e.cd_dev, work, nw, ns, smp0 + s0, n, v.n_terms, cf, base, e.eps, e.C, c->refine_iters,
                          c->refine_engine, X.stream, X.err, rb ? rb->sC : nullptr, rb ? rb->eC : nullptr));
     }
     return WPCD_OK;
@@ -699,7 +700,7 @@ wpcd_status diag_body(wpcd_ctx *c, Exec &X, VSetH &v, const double *coeffs, int 
             }
             Launch L(c, X, WPCD_PHASE_REFINE);
             const VSetH::RotB *rb = e.rot ? &v.rotb.at(n) : nullptr;
-            CK(launch_refine(e.cd_dev, work, nw, ns, smp0 + s0, n, v.n_terms, cf, base, e.eps, e.C, kRefineIters,
+            CK(launch_refine(e.cd_dev, work, nw, ns, smp0 + s0, n, v.n_terms, cf, base, e.eps, e.C, c->refine_iters,
                              c->refine_engine, X.stream, X.err, rb ? rb->sC : nullptr, rb ? rb->eC : nullptr));
         }
         return WPCD_OK;
@@ -881,6 +882,10 @@ wpcd_status wpcd_set_option(wpcd_ctx *c, int key, int value)
     }
     if (key == WPCD_OPT_REFINE && (value == WPCD_REFINE_TENSOR || value == WPCD_REFINE_FP64)) {
         c->refine_engine = value;
+        return WPCD_OK;
+    }
+    if (key == WPCD_OPT_REFINE_ITERS && value >= 1 && value <= 4) {
+        c->refine_iters = value;
         return WPCD_OK;
     }
     if (key == WPCD_OPT_ROTATE && (value == 0 || value == 1)) {

@@ -156,3 +156,17 @@ def test_mean_potential_basis_same_results_fewer_sweeps(ctx, orc):
         sweeps[on] = st.cpu().numpy()
     assert (sweeps[True] > 0).all() and (sweeps[False] > 0).all()
     assert sweeps[True].sum() < sweeps[False].sum(), (sweeps[True].sum(), sweeps[False].sum())
+
+
+def test_single_refinement_iteration_within_tolerance(ctx, orc):
+    """The opt-in single refinement iteration stays inside 1e-3 deg / 0.01 mb of
+    the oracle on the N_WP = 150 workload (two iterations are the default)."""
+    from paper_2106_00454_gb300 import api
+    wl = W.workload_mixed(n_samples=3)
+    md = api.Model(ctx, wl)
+    ctx.set_refine_iters(1)
+    try:
+        gpu = gpu_run(ctx, md, wl, prec=MIXED)
+    finally:
+        ctx.set_refine_iters(2)
+    _report("nwp150_one_iteration", compare_mixed(wl, gpu, oracle_run(orc, wl)))
