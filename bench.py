@@ -617,7 +617,9 @@ def run_wpcd(args, ws, rank, lrank):
             ctx.set_refine_iters(2)
             d1n, s1n = d1.cpu().numpy(), s1.cpu().numpy()
             one_iter = {"refine_iterations": 1, "value": S * nch / (ms1[0] * 1e-3), "unit": UNIT,
-                        "ms_per_step": ms1[0], "note": "opt-in (WPCD_OPT_REFINE_ITERS = 1); the headline uses 2"}
+                        "ms_per_step": ms1[0],
+                        "note": "opt-in (WPCD_OPT_REFINE_ITERS = 1), not within the 0.01 mb cross-section bar "
+                                "on every sample; the headline uses 2"}
             if accuracy is not None:
                 one_iter["vs_fp64_gpu"] = phase_err(wl, d1n[:k], s1n[:k], d6, s6)
             if acc_oracle is not None:
