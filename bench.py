@@ -508,7 +508,27 @@ def run_wpcd(args, ws, rank, lrank):
         ctx.set_exec(api.EXEC_PLAIN)
     # weak scaling: every rank owns its own block of samples (independent seeds)
     wl = rank_workload(args.samples, rank, args.workload)
-    md = api.Model(ctx, wl)
+    prec = api.PREC_MIXED if args.prec == "mixed" else api.PREC_FP64
+    # the projection: FP64 for the FP64 legs; the N_WP = 150 workload's mixed path also
+    # projects in reduced precision (angle integrals on the tensor cores)
+    t0 = time.perf_counter()
+    md64 = api.Model(ctx, wl)
+    proj = {"fp64_ms": (time.perf_counter() - t0) * 1e3}
+    md = md64
+    if prec == api.PREC_MIXED and args.workload == "config4":
+        t0 = time.perf_counter()
+        md = api.Model(ctx, wl, proj_prec=api.PREC_MIXED)
+        proj["mixed_ms"] = (time.perf_counter() - t0) * 1e3
+        worst = 0.0
+        for c in range(len(wl.channels)):
+            a, b = ctx.vset_get(md64.vset, c), ctx.vset_get(md.vset, c)
+            for tt in range(a.shape[0]):
+                sc = np.max(np.abs(a[tt]))
+                if sc > 0:
+                    worst = max(worst, float(np.max(np.abs(a[tt] - b[tt])) / sc))
+        proj["max_rel_diff_mixed_vs_fp64"] = worst
+        proj["note"] = ("wall time of mesh + projection of the 20-channel set (once per set, outside the step); "
+                        "mixed: Yukawa angle integrals as a BF16 three-term tensor-core contraction")
     S, nch, nE = wl.n_samples, len(wl.channels), len(wl.e_lab)
     cf = torch.tensor(wl.coeffs, dtype=torch.float64, device=dev)
     e = torch.tensor(wl.e_lab, dtype=torch.float64, device=dev)
@@ -517,7 +537,6 @@ def run_wpcd(args, ws, rank, lrank):
     s = torch.empty((S, nE), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(lrank)
-    prec = api.PREC_MIXED if args.prec == "mixed" else api.PREC_FP64
 
     def step():
         ctx.solve(md.vset, cf, S, e, t, d, s, prec=prec)
@@ -580,7 +599,7 @@ def run_wpcd(args, ws, rank, lrank):
             t64 = torch.empty((k, nch, nE, 2, 2, 2), dtype=torch.float64, device=dev)
             d64 = torch.empty((k, nch, nE, 3), dtype=torch.float64, device=dev)
             s64 = torch.empty((k, nE), dtype=torch.float64, device=dev)
-            ctx.solve(md.vset, cf[:k].contiguous(), k, e, t64, d64, s64, prec=api.PREC_FP64)
+            ctx.solve(md64.vset, cf[:k].contiguous(), k, e, t64, d64, s64, prec=api.PREC_FP64)
             ctx.sync()
             d6, s6 = d64.cpu().numpy(), s64.cpu().numpy()
             t6 = t64.cpu().numpy().view(np.complex128).reshape(k, nch, nE, 2, 2)
@@ -639,7 +658,7 @@ def run_wpcd(args, ws, rank, lrank):
             ctx.set_exec(mode)
 
             def fstep():
-                ctx.solve(md.vset, cfs, ns, e, None, dd, ss, prec=api.PREC_FP64)
+                ctx.solve(md64.vset, cfs, ns, e, None, dd, ss, prec=api.PREC_FP64)
             reps = 2 if mode == api.EXEC_BATCHED else 1
             for _ in range(reps):  # warm-up (allocations; the batched path's graph capture)
                 fstep()
@@ -720,12 +739,14 @@ def run_wpcd(args, ws, rank, lrank):
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == api.PREC_FP64 else "f32+f64", "data": "synthetic",
             "config": {"workload": workload_label(wl), "samples": S, "channels": nch, "n_E": nE,
+                       "projection": "tensor-core angle integrals" if md is not md64 else "fp64",
                        "n_wp": sorted(set(wl.nwp)), "exec": args.exec, "precision": args.prec,
                        "cuda_graphs": args.graphs, "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": f"replicas{ws}"},
             "roofline": jac,
             "roofline_secondary": ref,
             "phases_ms_per_step": {kk: v[0] / kp for kk, v in prof.items()},
+            "projection": proj,
             "ms_per_step_kernel_by_kernel": statistics.mean(prof_step_ms),
             "cuda_graphs": {"captures": graphs1["captures"],
                             "replays_in_timed_steps": graphs1["replays"] - graphs0["replays"]},
@@ -740,7 +761,9 @@ def run_wpcd(args, ws, rank, lrank):
             **base,
             "clocks": clocks,
         }
-    md.release()
+    if md is not md64:
+        md.release()
+    md64.release()
     del t, d, s
     if rank == 0:
         if args.secondary == "on":

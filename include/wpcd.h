@@ -192,6 +192,19 @@ wpcd_status wpcd_project(wpcd_ctx *ctx, const int *mesh_ids, const wpcd_channel 
                          int generator_id, const double *gen_params_host, int n_gen_params,
                          const double *v_fine_dev, int n_terms, int *vset_id);
 
+/* wpcd_project with a precision for the built-in Yukawa + contact generator
+ * (the other generators ignore it): WPCD_PREC_FP64 is wpcd_project;
+ * WPCD_PREC_MIXED forms the 96-point angle integrals I_L[m](k_a, k_b) of every
+ * fine pair as a contraction on the tensor cores -- the angle integrand
+ * evaluated in FP32 and cut into three BF16 terms, the w_x P_L(x) table
+ * likewise, the six term products of order <= 2 accumulated in FP32 (about
+ * FP32 accuracy, ~1e-7 relative) -- then the potential terms and the bin
+ * reduction in FP64 as for wpcd_project.  Errors as wpcd_project; a device
+ * timeout of the tensor-core contraction is reported by wpcd_sync. */
+wpcd_status wpcd_project_prec(wpcd_ctx *ctx, const int *mesh_ids, const wpcd_channel *channels, int n_ch,
+                              int generator_id, const double *gen_params_host, int n_gen_params,
+                              const double *v_fine_dev, int n_terms, wpcd_precision prec, int *vset_id);
+
 /* Copy the projected matrices of one channel to the host (synchronises):
  * out_host[n_terms][n][n].  Errors: WPCD_ERR_HANDLE, WPCD_ERR_ARG. */
 wpcd_status wpcd_vset_get(wpcd_ctx *ctx, int vset_id, int channel, double *out_host);

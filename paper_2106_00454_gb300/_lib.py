@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libwpcd.so"
 # Every entry point declared in include/wpcd.h.
 EXPORTED = [
     "wpcd_create", "wpcd_destroy", "wpcd_strerror", "wpcd_set_option", "wpcd_sync", "wpcd_bytes_in_use",
-    "wpcd_mesh", "wpcd_mesh_get", "wpcd_project", "wpcd_vset_get", "wpcd_vset_info", "wpcd_diag",
+    "wpcd_mesh", "wpcd_mesh_get", "wpcd_project", "wpcd_project_prec", "wpcd_vset_get", "wpcd_vset_info", "wpcd_diag",
     "wpcd_diag_status", "wpcd_eig_get", "wpcd_tmatrix", "wpcd_observables", "wpcd_observables_res", "wpcd_solve", "wpcd_solve_host",
     "wpcd_release", "wpcd_kernel_launches", "wpcd_profile", "wpcd_profile_read",
     "wpcd_channel_solve_noalloc", "wpcd_serve_start", "wpcd_serve_stop", "wpcd_submit", "wpcd_poll", "wpcd_wait",
@@ -57,6 +57,7 @@ _SIG = {
     "wpcd_mesh": (_i, [_vp, _i, _i, _d, _d, _d, _i, _i, _ip]),
     "wpcd_mesh_get": (_i, [_vp, _i, _vp, _vp, _vp]),
     "wpcd_project": (_i, [_vp, _ip, ctypes.POINTER(wpcd_channel), _i, _i, _vp, _i, _vp, _i, _ip]),
+    "wpcd_project_prec": (_i, [_vp, _ip, ctypes.POINTER(wpcd_channel), _i, _i, _vp, _i, _vp, _i, _i, _ip]),
     "wpcd_vset_get": (_i, [_vp, _i, _i, _vp]),
     "wpcd_vset_info": (_i, [_vp, _i, _ip, _ip, _i, _ip]),
     "wpcd_diag": (_i, [_vp, _i, _vp, _i, _i, _ip]),

@@ -170,15 +170,16 @@ class Context:
         _ck(self.lib.wpcd_mesh_get(self.h, mesh_id, _ptr(kb), _ptr(kq), _ptr(wq)), "wpcd_mesh_get")
         return kb, kq, wq
 
-    def project(self, mesh_ids, channels, gen, gen_params, n_terms, v_fine=None) -> int:
+    def project(self, mesh_ids, channels, gen, gen_params, n_terms, v_fine=None, prec=PREC_FP64) -> int:
+        """Projected potential set; prec = PREC_MIXED: angle integrals on the tensor cores (Yukawa)."""
         n = len(channels)
         arr = (_lib.wpcd_channel * n)(*[_lib.wpcd_channel(*c.astuple()) if hasattr(c, "astuple")
                                         else _lib.wpcd_channel(*c) for c in channels])
         mids = (ctypes.c_int * n)(*mesh_ids)
         gp = None if gen_params is None else np.ascontiguousarray(gen_params, dtype=np.float64)
         vid = ctypes.c_int()
-        _ck(self.lib.wpcd_project(self.h, mids, arr, n, gen, _ptr(gp), 0 if gp is None else gp.size,
-                                  _ptr(v_fine), n_terms, ctypes.byref(vid)), "wpcd_project")
+        _ck(self.lib.wpcd_project_prec(self.h, mids, arr, n, gen, _ptr(gp), 0 if gp is None else gp.size,
+                                       _ptr(v_fine), n_terms, prec, ctypes.byref(vid)), "wpcd_project_prec")
         return vid.value
 
     def vset_info(self, vset_id, channel=0):
@@ -334,7 +335,7 @@ _serve_methods()
 class Model:
     """Meshes + projected potential for one workload's channel set."""
 
-    def __init__(self, ctx: Context, wl: W.Workload, v_fine=None):
+    def __init__(self, ctx: Context, wl: W.Workload, v_fine=None, proj_prec=PREC_FP64):
         self.ctx = ctx
         self.wl = wl
         self.mesh_of_n = {}
@@ -342,7 +343,7 @@ class Model:
             self.mesh_of_n[n] = ctx.mesh(n, wl.mesh_kind, wl.alpha, wl.t, wl.kmax, wl.Q, wl.wp_kind)
         mids = [self.mesh_of_n[n] for n in wl.nwp]
         self.vset = ctx.project(mids, wl.channels, wl.gen if v_fine is None else -1, wl.gen_params, wl.n_terms,
-                                v_fine)
+                                v_fine, prec=proj_prec)
 
     @property
     def n_ch(self):

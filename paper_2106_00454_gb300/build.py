@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libwpcd.so")
-SOURCES = ["mesh_project.cu", "eig_jacobi.cu", "eig_mixed.cu", "eig_big.cu", "refine.cu", "ozaki.cu", "ozaki_tc.cu", "tmatrix.cu", "runtime.cu", "noalloc.cu", "mi.cu", "saclay.cu"]
+SOURCES = ["mesh_project.cu", "project_tc.cu", "eig_jacobi.cu", "eig_mixed.cu", "eig_big.cu", "refine.cu", "ozaki.cu", "ozaki_tc.cu", "tmatrix.cu", "runtime.cu", "noalloc.cu", "mi.cu", "saclay.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -128,10 +128,13 @@ __device__ __forceinline__ double cta_sum(double v, double *red)
     return tot;
 }
 
+// Ibuf (Yukawa only, may be NULL): the angle integrals of every fine pair,
+// [pair][mass][16] FP32 from the tensor-core contraction (project_tc.cu), used
+// instead of the FP64 angle sums.
 template <int GEN>
 __global__ void __launch_bounds__(256) k_project(const ChanDev *chans, const int *group, int n_group, int N, int Q,
                                                  int Lmax, const double *gp, const double *angx, const double *angw,
-                                                 int n_terms)
+                                                 int n_terms, const float *Ibuf)
 {
     // decode the bin pair (i <= j) from the linear block index over the upper triangle
     int b = blockIdx.x;
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(256) k_project(const ChanDev *chans, const int
     __shared__ double ax[kAngleQ];
     __shared__ double red[8];
     const int Lm = (Lmax < kLmaxReg) ? Lmax : kLmaxReg;
-    if (GEN == WPCD_GEN_YUKAWA) {
+    if (GEN == WPCD_GEN_YUKAWA && !Ibuf) {
         angle_tables(angx, angw, Lm, wpl, ax);
         __syncthreads();
     }
@@ -163,7 +166,21 @@ __global__ void __launch_bounds__(256) k_project(const ChanDev *chans, const int
 
     double I1[kLmaxReg + 1], I2[kLmaxReg + 1], I3[kLmaxReg + 1];
     double R = 0.0;
-    if (GEN == WPCD_GEN_YUKAWA) yukawa_angle_integrals(gp, wpl, ax, Lm, pp, p, I1, I2, I3, R);
+    if (GEN == WPCD_GEN_YUKAWA) {
+        if (Ibuf) {
+            const float *Ip = Ibuf + ((size_t)b * Q * Q + (live ? threadIdx.x : 0)) * 48;
+#pragma unroll
+            for (int L = 0; L <= kLmaxReg; ++L) {
+                const bool on = L <= Lm;
+                I1[L] = on ? (double)Ip[L] : 0.0;
+                I2[L] = on ? (double)Ip[16 + L] : 0.0;
+                I3[L] = on ? (double)Ip[32 + L] : 0.0;
+            }
+            R = exp(-(pp * pp + p * p) / (gp[3] * gp[3]));
+        } else {
+            yukawa_angle_integrals(gp, wpl, ax, Lm, pp, p, I1, I2, I3, R);
+        }
+    }
 
     for (int g = 0; g < n_group; ++g) {
         const int cidx = group[g];
@@ -191,11 +208,11 @@ static int proj_threads(int Q) { return ((Q * Q + 31) / 32) * 32; }
 
 cudaError_t launch_project_yukawa(const ChanDev *chans_dev, const int *group_dev, int n_group, int N, int Q, int Lmax,
                                   const double *gp_dev, const double *angx, const double *angw, int n_terms,
-                                  cudaStream_t st)
+                                  cudaStream_t st, const float *Ibuf)
 {
     int nblk = N * (N + 1) / 2;
     k_project<WPCD_GEN_YUKAWA><<<nblk, proj_threads(Q), 0, counted(st)>>>(chans_dev, group_dev, n_group, N, Q, Lmax, gp_dev,
-                                                                 angx, angw, n_terms);
+                                                                 angx, angw, n_terms, Ibuf);
     return cudaGetLastError();
 }
 
@@ -205,7 +222,7 @@ cudaError_t launch_project_yamaguchi_gp(const ChanDev *chans_dev, const int *gro
 {
     int nblk = N * (N + 1) / 2;
     k_project<WPCD_GEN_YAMAGUCHI><<<nblk, proj_threads(Q), 0, counted(st)>>>(chans_dev, group_dev, n_group, N, Q, 0, gp_dev,
-                                                                    nullptr, nullptr, 1);
+                                                                    nullptr, nullptr, 1, nullptr);
     return cudaGetLastError();
 }
 

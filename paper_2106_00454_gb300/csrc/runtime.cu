@@ -991,7 +991,15 @@ wpcd_status wpcd_mesh_get(wpcd_ctx *c, int mesh_id, double *kb, double *kq, doub
 wpcd_status wpcd_project(wpcd_ctx *c, const int *mesh_ids, const wpcd_channel *chs, int n_ch, int gen,
                          const double *gp_host, int n_gp, const double *v_fine_dev, int n_terms, int *vset_id)
 {
+    return wpcd_project_prec(c, mesh_ids, chs, n_ch, gen, gp_host, n_gp, v_fine_dev, n_terms, WPCD_PREC_FP64, vset_id);
+}
+
+wpcd_status wpcd_project_prec(wpcd_ctx *c, const int *mesh_ids, const wpcd_channel *chs, int n_ch, int gen,
+                              const double *gp_host, int n_gp, const double *v_fine_dev, int n_terms,
+                              wpcd_precision prec, int *vset_id)
+{
     if (!c || !mesh_ids || !chs || n_ch < 1 || !vset_id || n_terms < 1 || n_terms > kMaxTerms) return WPCD_ERR_ARG;
+    if (prec != WPCD_PREC_FP64 && prec != WPCD_PREC_MIXED) return WPCD_ERR_ARG;
     if (gen == WPCD_GEN_YAMAGUCHI && (n_terms != 1 || !gp_host || n_gp < 2)) return WPCD_ERR_ARG;
     if (gen == WPCD_GEN_YUKAWA && (n_terms > kYukTerms + 1 || !gp_host || n_gp < kYukParams)) return WPCD_ERR_ARG;
     if (gen == WPCD_GEN_FINE && !v_fine_dev) return WPCD_ERR_ARG;
@@ -1089,6 +1097,7 @@ wpcd_status wpcd_project(wpcd_ctx *c, const int *mesh_ids, const wpcd_channel *c
         std::map<int, std::vector<int>> groups;
         for (int k = 0; k < n_ch; ++k) groups[mesh_ids[k]].push_back(k);
         std::vector<int *> gdevs;
+        std::vector<float *> gdevs_f;  // angle-integral buffers of the reduced-precision projection
         for (auto &kv : groups) {
             int *gd;
             if ((st = dalloc(c, &gd, kv.second.size()))) return st;
@@ -1097,14 +1106,23 @@ wpcd_status wpcd_project(wpcd_ctx *c, const int *mesh_ids, const wpcd_channel *c
                                c->main.stream));
             const ChanDev &d0 = v->cd[kv.second[0]];
             Launch L(c, c->main, WPCD_PHASE_PROJECT);
-            if (gen == WPCD_GEN_YUKAWA)
+            if (gen == WPCD_GEN_YUKAWA) {
+                // reduced precision: the angle integrals from the tensor-core contraction
+                float *Ibuf = nullptr;
+                if (prec == WPCD_PREC_MIXED) {
+                    if ((st = dmalloc(c, reinterpret_cast<void **>(&Ibuf), angle_tc_buffer_bytes(d0.N, d0.Q)))) return st;
+                    gdevs_f.push_back(Ibuf);
+                    CK(launch_angle_tc(v->cd_dev, gd, d0.N, d0.Q, maxJ + 2, gp_dev, angx, angw, Ibuf, c->main.err,
+                                       c->main.stream));
+                }
                 CK(launch_project_yukawa(v->cd_dev, gd, (int)kv.second.size(), d0.N, d0.Q, maxJ + 2, gp_dev, angx, angw,
-                                         n_terms, c->main.stream));
-            else
+                                         n_terms, c->main.stream, Ibuf));
+            } else
                 CK(launch_project_yamaguchi_gp(v->cd_dev, gd, (int)kv.second.size(), d0.N, d0.Q, gp_dev, c->main.stream));
         }
         CK(cudaStreamSynchronize(c->main.stream));
         for (int *gd : gdevs) dfree(c, gd);
+        for (float *fb : gdevs_f) dfree(c, fb);
         dfree(c, gp_dev);
     }
     int id = c->next_id++;

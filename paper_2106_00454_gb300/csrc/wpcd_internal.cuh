@@ -239,7 +239,10 @@ cudaError_t launch_mesh(int N, int kind, double alpha, double t, double kmax, in
                         cudaStream_t st);
 cudaError_t launch_project_yukawa(const ChanDev *chans_dev, const int *group_dev, int n_group, int N, int Q,
                                   int Lmax, const double *gp_dev, const double *angx, const double *angw,
-                                  int n_terms, cudaStream_t st);
+                                  int n_terms, cudaStream_t st, const float *Ibuf = nullptr);
+size_t angle_tc_buffer_bytes(int N, int Q);
+cudaError_t launch_angle_tc(const ChanDev *chans_dev, const int *group_dev, int N, int Q, int Lm, const double *gp_dev,
+                            const double *angx, const double *angw, float *Iout, int *err, cudaStream_t st);
 cudaError_t launch_project_yamaguchi_gp(const ChanDev *chans_dev, const int *group_dev, int n_group, int N, int Q,
                                         const double *gp_dev, cudaStream_t st);
 cudaError_t launch_project_fine(const ChanDev *chans_dev, int c, const ChanDev &ch_host, const double *vfine,
