@@ -195,12 +195,16 @@ wpcd_status wpcd_project(wpcd_ctx *ctx, const int *mesh_ids, const wpcd_channel 
 /* wpcd_project with a precision for the built-in Yukawa + contact generator
  * (the other generators ignore it): WPCD_PREC_FP64 is wpcd_project;
  * WPCD_PREC_MIXED forms the 96-point angle integrals I_L[m](k_a, k_b) of every
- * fine pair as a contraction on the tensor cores -- the angle integrand
- * evaluated in FP32 and cut into three BF16 terms, the w_x P_L(x) table
- * likewise, the six term products of order <= 2 accumulated in FP32 (about
- * FP32 accuracy, ~1e-7 relative) -- then the potential terms and the bin
- * reduction in FP64 as for wpcd_project.  Errors as wpcd_project; a device
- * timeout of the tensor-core contraction is reported by wpcd_sync. */
+ * fine pair as a contraction on the tensor cores: the angle integrand is
+ * evaluated in FP32, every row of it and every column of the w_x P_L(x) table
+ * scaled by a power of two and cut into four balanced 8-bit digits (exact in
+ * BF16), and the ten digit pairs of weight <= 3 accumulated in FP32 as exact
+ * integers; the potential terms and the bin reduction follow in FP64 as for
+ * wpcd_project.  The projected terms then differ from the FP64 ones by a few
+ * 1e-6 of each term's largest element (the FP32 integrand), which keeps the
+ * mixed path within 1e-3 deg and 0.01 mb of the FP64 oracle.  Errors as
+ * wpcd_project; a device timeout of the tensor-core contraction is reported
+ * by wpcd_sync. */
 wpcd_status wpcd_project_prec(wpcd_ctx *ctx, const int *mesh_ids, const wpcd_channel *channels, int n_ch,
                               int generator_id, const double *gen_params_host, int n_gen_params,
                               const double *v_fine_dev, int n_terms, wpcd_precision prec, int *vset_id);

@@ -10,15 +10,24 @@
 // w_x P_L(x) [96 x (L_max + 1)].  Here:
 //   * F is evaluated in FP32 (the squared momentum transfer written as a sum
 //     of non-negative terms, so there is no cancellation, with 1 - x taken
-//     from the FP64 nodes) and cut into three BF16 terms F = F_h + F_m + F_l
-//     (24 significant bits); the table likewise;
-//   * the six term products of order <= 2 (hh, hm, mh, hl, lh, mm; the
-//     dropped ones weigh <= 2^-24) run as tcgen05.mma kind::f16 (BF16
-//     operands, FP32 accumulation in tensor memory): M = 128 fine pairs,
-//     N = 16 (L <= 15), K = 96 in three 32-k spans of the 64-byte-swizzled
-//     K-major layout, one accumulator per mass;
-//   * the integrals leave as FP32 [pair][mass][16]; the potential terms and
-//     the bin reduction that use them stay FP64 (k_project in mesh_project.cu).
+//     from the FP64 nodes);
+//   * split-precision correction in the Ozaki manner: every row of F is scaled
+//     by a power of two from its largest value (at the largest node x, where
+//     the transfer is smallest), rounded to a 31-bit integer and cut into
+//     four balanced 8-bit digits; every column of the table likewise, from
+//     its own largest |value|.  Digits are exact in BF16 and a product of two
+//     is at most 2^14, so the FP32 accumulator of one weight (at most four
+//     digit pairs) over the 96 angles holds an exact integer (< 2^24): the
+//     tensor core's accumulation adds no error;
+//   * the ten digit pairs of weight p + q <= 3 (the dropped ones weigh
+//     <= 2^-32) run as tcgen05.mma kind::f16 (BF16 operands, FP32
+//     accumulation in tensor memory), M = 128 fine pairs, N = 16 (L <= 15),
+//     K = 96 in three 32-k spans of the 64-byte-swizzled K-major layout, one
+//     accumulator per (mass, weight); the epilogue assembles each integral in
+//     FP64 from the exact integer sums and the two scales;
+//   * the integrals leave as FP32 [pair][mass][16] (their FP32 rounding,
+//     2^-24, is below the evaluation error of F); the potential terms and the
+//     bin reduction that use them stay FP64 (k_project in mesh_project.cu).
 // One CTA per tile of 128 consecutive fine pairs (pair = bin pair * Q^2 +
 // qa Q + qb, bin pairs (i <= j) of the upper triangle).  Every wait on the
 // tensor core is bounded; on a timeout the kernel records kDevTimeout and
@@ -33,12 +42,14 @@ namespace wpcd {
 
 constexpr int kPtM = 128;                  // fine pairs per tile (TMEM lanes)
 constexpr int kPtN = 16;                   // L = 0 .. 15 (columns per accumulator)
+constexpr int kPtDigits = 4;               // balanced 8-bit digits per operand
 constexpr int kPtSpans = kAngleQ / 32;     // 32-k spans of 64 bytes
 constexpr int kPtASplit = kPtM * kAngleQ * 2;   // one BF16 term of A: 24 KB
 constexpr int kPtBSplit = kPtN * kAngleQ * 2;   // one BF16 term of B: 3 KB
-constexpr int kPtSmem = 1024 + 3 * kPtASplit + 3 * kPtBSplit + 64;  // alignment slack | A | B | barrier, TMEM slot
+// alignment slack | A digits | B digits | barrier, TMEM slot | B in FP64 [16][96] | column exponents
+constexpr int kPtSmem = 1024 + kPtDigits * (kPtASplit + kPtBSplit) + 64 + kPtN * kAngleQ * 8 + kPtN * 4 + 64;
 constexpr int kPtThreads = 256;
-constexpr int kPtTmemCols = 64;            // 3 masses x 16 columns, allocated as a power of two
+constexpr int kPtTmemCols = 256;           // 3 masses x 4 weights x 16 columns, allocated as a power of two
 constexpr long long kPtWaitCycles = 1ll << 31;
 // D F32, A and B BF16, both K-major, N = 16, M = 128 (the encoding of the digit products)
 constexpr uint32_t kPtIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kPtN >> 3) << 17) |
@@ -84,13 +95,19 @@ __device__ __forceinline__ bool pt_wait(uint32_t a, uint32_t parity)
     return true;
 }
 
-// x = h + m + l: three BF16 terms, 24 significant bits together.
-__device__ __forceinline__ void split3(float x, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l)
+// v = 2^(e - 30) (d0 2^24 + d1 2^16 + d2 2^8 + d3) to the nearest integer
+// multiple of 2^(e - 30), |v| < 2^(e + 1): balanced digits d1..d3 in
+// [-128, 127], |d0| <= 128, all exact in BF16; d[p] is digit p.
+__device__ __forceinline__ void digits4(double v, int e, __nv_bfloat16 *d)
 {
-    h = __float2bfloat16_rn(x);
-    const float r1 = x - __bfloat162float(h);
-    m = __float2bfloat16_rn(r1);
-    l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+    long long N = llrint(ldexp(v, 30 - e));
+#pragma unroll
+    for (int p = kPtDigits - 1; p > 0; --p) {
+        const long long r = ((N + 128) & 255) - 128;
+        d[p] = __float2bfloat16_rn((float)r);
+        N = (N - r) >> 8;
+    }
+    d[0] = __float2bfloat16_rn((float)N);
 }
 
 __global__ void __launch_bounds__(kPtThreads) k_angle_tc(const ChanDev *chans, const int *group, int N, int Q, int Lm,
@@ -101,12 +118,14 @@ __global__ void __launch_bounds__(kPtThreads) k_angle_tc(const ChanDev *chans, c
     const uint32_t raw_s = pt_smem_u32(pt_raw);
     const uint32_t base_s = (raw_s + 1023u) & ~1023u;  // the swizzle follows address bits
     unsigned char *base = pt_raw + (base_s - raw_s);
-    unsigned char *As = base;                      // 3 terms x [3 spans][128 rows][64 B]
-    unsigned char *Bs = base + 3 * kPtASplit;      // 3 terms x [3 spans][16 rows][64 B]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(Bs + 3 * kPtBSplit);
+    unsigned char *As = base;                          // 4 digits x [3 spans][128 rows][64 B]
+    unsigned char *Bs = base + kPtDigits * kPtASplit;  // 4 digits x [3 spans][16 rows][64 B]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Bs + kPtDigits * kPtBSplit);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 1);
+    double *Bd = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(bar) + 64);  // [16][96]
+    int *eCol = reinterpret_cast<int *>(Bd + kPtN * kAngleQ);                              // [16]
     __shared__ float omx[kAngleQ];                 // 1 - x
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t bar_s = pt_smem_u32(bar);
     const long long pair0 = (long long)blockIdx.x * kPtM;
 
@@ -124,14 +143,23 @@ __global__ void __launch_bounds__(kPtThreads) k_angle_tc(const ChanDev *chans, c
                 p0 = p1;
                 p1 = pl;
             }
-            const float v = L <= Lm ? (float)(2.0 * kPi * angw[x] * pl) : 0.0f;
-            __nv_bfloat16 h, m, l;
-            split3(v, h, m, l);
-            const uint32_t o = pt_sw64(L, x, kPtN);
-            *reinterpret_cast<__nv_bfloat16 *>(Bs + o) = h;
-            *reinterpret_cast<__nv_bfloat16 *>(Bs + kPtBSplit + o) = m;
-            *reinterpret_cast<__nv_bfloat16 *>(Bs + 2 * kPtBSplit + o) = l;
+            Bd[L * kAngleQ + x] = L <= Lm ? 2.0 * kPi * angw[x] * pl : 0.0;
         }
+    }
+    __syncthreads();
+    if (tid < kPtN) {  // column exponents: 2^e <= max_x |B[L][x]| < 2^(e + 1)
+        double mx = 0.0;
+        for (int x = 0; x < kAngleQ; ++x) mx = fmax(mx, fabs(Bd[tid * kAngleQ + x]));
+        eCol[tid] = mx > 0.0 ? ilogb(mx) : 0;
+    }
+    __syncthreads();
+    for (int e = tid; e < kPtN * kAngleQ; e += kPtThreads) {
+        const int L = e / kAngleQ, x = e - L * kAngleQ;
+        __nv_bfloat16 d[kPtDigits];
+        digits4(Bd[e], eCol[L], d);
+        const uint32_t o = pt_sw64(L, x, kPtN);
+#pragma unroll
+        for (int p = 0; p < kPtDigits; ++p) *reinterpret_cast<__nv_bfloat16 *>(Bs + p * kPtBSplit + o) = d[p];
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s) : "memory");
@@ -165,39 +193,47 @@ __global__ void __launch_bounds__(kPtThreads) k_angle_tc(const ChanDev *chans, c
         dd = (float)(pp - p);
         s2 = (float)(2.0 * pp * p);
     }
+    // the smallest 1 - x (the largest node) gives the largest F of a row
+    float omin = omx[0];
+    for (int x = 1; x < kAngleQ; ++x) omin = fminf(omin, omx[x]);
     bool ok = true;
+    int erow[3];  // this row's exponent per mass (the epilogue threads hold their own rows)
     for (int m = 0; m < 3; ++m) {
         const float mm = (float)(gp[m] * gp[m]);
         if (m > 0) {  // the MMAs of the previous mass must be done with A
             ok = ok && pt_wait(bar_s, (uint32_t)((m - 1) & 1));
         }
+        const int er = pr < n_pairs ? ilogb(__frcp_rn(fmaf(dd, dd, fmaf(s2, omin, mm)))) : 0;
+        erow[m] = er;
         for (int x = xh; x < kAngleQ; x += 2) {
             float F = 0.0f;
             if (pr < n_pairs) F = __frcp_rn(fmaf(dd, dd, fmaf(s2, omx[x], mm)));
-            __nv_bfloat16 h, md, l;
-            split3(F, h, md, l);
+            __nv_bfloat16 d[kPtDigits];
+            digits4((double)F, er, d);
             const uint32_t o = pt_sw64(r, x, kPtM);
-            *reinterpret_cast<__nv_bfloat16 *>(As + o) = h;
-            *reinterpret_cast<__nv_bfloat16 *>(As + kPtASplit + o) = md;
-            *reinterpret_cast<__nv_bfloat16 *>(As + 2 * kPtASplit + o) = l;
+#pragma unroll
+            for (int p = 0; p < kPtDigits; ++p) *reinterpret_cast<__nv_bfloat16 *>(As + p * kPtASplit + o) = d[p];
         }
         // the generic-proxy stores become visible to the tensor core
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // term pairs (a, b) of order a + b <= 2 over the splits h = 0, m = 1, l = 2:
-            // (0,0) (0,1) (1,0) (0,2) (2,0) (1,1), one nibble per pair
-            uint32_t acc = 0;
-            for (int t = 0; t < 6; ++t) {
-                const int ta = (0x120100 >> (4 * t)) & 0xF, tb = (0x102010 >> (4 * t)) & 0xF;
+            // digit pairs (p, q) of weight p + q <= 3, by weight: (0,0) | (0,1) (1,0) |
+            // (0,2) (2,0) (1,1) | (0,3) (3,0) (1,2) (2,1), one nibble per pair; the pairs
+            // of one weight share the accumulator (mass, weight)
+            for (int t = 0; t < 10; ++t) {
+                const int ta = (int)((0x2130120100ull >> (4 * t)) & 0xF), tb = (int)((0x1203102010ull >> (4 * t)) & 0xF);
+                const bool first = t == 0 || t == 1 || t == 3 || t == 6;  // the first pair of each weight
+                uint32_t acc = first ? 0u : 1u;
+                const uint32_t dcol = tmem + (uint32_t)((m * kPtDigits + ta + tb) * kPtN);
                 for (int s = 0; s < kPtSpans; ++s)
                     for (int kk = 0; kk < 2; ++kk) {  // K = 16 steps, 32 bytes apart inside a span
                         const uint32_t a_s = pt_smem_u32(As) + ta * kPtASplit + s * kPtM * 64 + kk * 32;
                         const uint32_t b_s = pt_smem_u32(Bs) + tb * kPtBSplit + s * kPtN * 64 + kk * 32;
                         asm volatile(
                             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem + m * kPtN),
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dcol),
                             "l"(pt_desc(a_s)), "l"(pt_desc(b_s)), "r"(kPtIdesc), "r"(acc)
                             : "memory");
                         acc = 1;
@@ -212,35 +248,38 @@ __global__ void __launch_bounds__(kPtThreads) k_angle_tc(const ChanDev *chans, c
     if (!__syncthreads_and(ok ? 1 : 0)) {
         if (tid == 0) record_error(err, kDevTimeout);
     } else if (warp < 4) {
-        // warp w reads TMEM lanes 32 w .. 32 w + 31 = rows of the tile, 48 columns
-        uint32_t v[48];
+        // warp w reads TMEM lanes 32 w .. 32 w + 31 = rows of the tile (its own rows:
+        // tid = row), per mass the four weight accumulators of 16 columns each
+        const long long row = pair0 + tid;
         const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-            "%15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(ta));
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-            "%15}, [%16];"
-            : "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(ta + 16u));
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-            "%15}, [%16];"
-            : "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]),
-              "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47])
-            : "r"(ta + 32u));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const long long row = pair0 + warp * 32 + lane;
-        if (row < n_pairs) {
-            float4 *o = reinterpret_cast<float4 *>(Iout + (size_t)row * 48);
+        for (int m = 0; m < 3; ++m) {
+            uint32_t v[16 * kPtDigits];
 #pragma unroll
-            for (int q = 0; q < 12; ++q)
-                o[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                                   __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+            for (int d = 0; d < kPtDigits; ++d) {
+                uint32_t *u = v + 16 * d;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15}, [%16];"
+                    : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+                      "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
+                      "=r"(u[15])
+                    : "r"(ta + (uint32_t)((m * kPtDigits + d) * kPtN)));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < n_pairs) {
+                float out[kPtN];
+#pragma unroll
+                for (int L = 0; L < kPtN; ++L) {
+                    // exact integer sums of weights d = 0..3 times 2^(48 - 8 d), scaled back
+                    double sum = 0.0;
+#pragma unroll
+                    for (int d = 0; d < kPtDigits; ++d) sum += ldexp((double)__uint_as_float(v[16 * d + L]), 48 - 8 * d);
+                    out[L] = (float)ldexp(sum, erow[m] + eCol[L] - 60);
+                }
+                float4 *o = reinterpret_cast<float4 *>(Iout + (size_t)row * 48 + m * kPtN);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) o[q] = make_float4(out[4 * q], out[4 * q + 1], out[4 * q + 2], out[4 * q + 3]);
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
