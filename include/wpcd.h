@@ -96,7 +96,8 @@ enum {
  * products -- TENSOR (BF16 tensor cores with Ozaki splitting, FP64-accurate) or
  * FP64 (FP64 CUDA cores).  WPCD_OPT_AUTOTUNE (1 = on, the default): on the first
  * batched eigensolve of each (matrix size, precision) the context times CTA
- * sizes 64/128/256/512 on about two full waves of that bucket and keeps the
+ * sizes 64/128/256/512 (and 1024 for the FP32 kernel) on about two full waves
+ * of that bucket and keeps the
  * fastest (wpcd_tuning reports the choices); 0 = fixed 256 threads.
  * WPCD_OPT_GRAPH (1 = on, the default): batched wpcd_solve / wpcd_solve_host
  * calls are replayed from CUDA graphs (see wpcd_solve); 0 = every call
@@ -384,8 +385,9 @@ wpcd_status wpcd_batched_dgemm(wpcd_ctx *ctx, int n, int items, int trans_a, con
                                const double *B_dev, double *C_dev, int engine);
 
 /* The autotuner's table: up to max_entries (n, precision, chosen CTA size) and,
- * in ms_out[4 k + j], the measured time per solve of candidate j (64, 128, 256,
- * 512 threads; negative = not run).  Returns the number of entries. */
+ * in ms_out[5 k + j], the measured time per solve of candidate j (64, 128, 256,
+ * 512, 1024 threads; 1024 only for the FP32 kernel; negative = not run).
+ * Returns the number of entries. */
 int wpcd_tuning(wpcd_ctx *ctx, int max_entries, int *n_out, int *prec_out, int *threads_out, float *ms_out);
 
 /* Number of kernels this context has launched since creation (host count;

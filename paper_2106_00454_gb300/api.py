@@ -122,10 +122,10 @@ class Context:
         n = np.zeros(m, dtype=np.int32)
         p = np.zeros(m, dtype=np.int32)
         t = np.zeros(m, dtype=np.int32)
-        ms = np.zeros(4 * m, dtype=np.float32)
+        ms = np.zeros(5 * m, dtype=np.float32)
         k = self.lib.wpcd_tuning(self.h, m, _ptr(n), _ptr(p), _ptr(t), _ptr(ms))
         return [{"n": int(n[i]), "precision": ("fp64", "mixed")[int(p[i])], "threads": int(t[i]),
-                 "ms_per_solve": {c: float(ms[4 * i + j]) for j, c in enumerate((64, 128, 256, 512))}}
+                 "ms_per_solve": {c: float(ms[5 * i + j]) for j, c in enumerate((64, 128, 256, 512, 1024))}}
                 for i in range(k)]
 
     def sync(self):

@@ -83,8 +83,12 @@ __device__ __forceinline__ void mix_pair(int r, int k, int M, int &p, int &q)
     q = a < b ? b : a;
 }
 
+// Launch bound 1024 threads, one CTA per SM (the shared memory holds one
+// matrix per SM at the sizes that need many threads): the rounds are bound by
+// latency, and more warps keep more block updates and eigenvector rotations in
+// flight.  The autotuner picks the CTA size per matrix size.
 template <bool C_SMEM>
-__global__ void __launch_bounds__(kMixMaxThreads) k_jacobi_mixed(const ChanDev *chans, const int *work_ch, int n_work_ch,
+__global__ void __launch_bounds__(2 * kMixMaxThreads, 1) k_jacobi_mixed(const ChanDev *chans, const int *work_ch, int n_work_ch,
                                                                int sample0, int n_terms, const double *coeffs,
                                                                double *lam_s, double *X_s, float *Cf_s,
                                                                double *H_s, int *status_all, int n_ch_total, int *err)
@@ -325,8 +329,8 @@ cudaError_t launch_jacobi_mixed(const ChanDev *chans_dev, const int *work_ch_dev
                                 float *Cf_s, double *H_s, int *status_all, int n_ch_total, int *err, cudaStream_t st,
                                 int threads)
 {
-    if (threads < 32 || threads > kMixMaxThreads || (threads & 31)) return cudaErrorInvalidValue;
     const bool cs = mix_smem(n, true) <= kMixSmemCap;
+    if (threads < 32 || threads > 2 * kMixMaxThreads || (threads & 31)) return cudaErrorInvalidValue;
     const size_t smem = mix_smem(n, cs);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     dim3 grid((unsigned)(n_samples * n_work_ch));

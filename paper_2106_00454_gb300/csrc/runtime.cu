@@ -140,7 +140,7 @@ struct wpcd_ctx {
     int n_sm = 0;
     struct Tuned {
         int threads;
-        float ms[4];
+        float ms[5];
     };
     std::map<std::pair<int, int>, Tuned> tuned;  // (n, precision) -> eigensolver CTA size
     std::mutex tmu;
@@ -372,7 +372,7 @@ void free_mesh(wpcd_ctx *c, MeshH &m)
 template <class F>
 int pick_threads(wpcd_ctx *c, Exec &X, int n, int prec, int nw, int nsmp, F launch)
 {
-    static const int cand[4] = {64, 128, 256, 512};
+    static const int cand[5] = {64, 128, 256, 512, 1024};  // 1024: the FP32 kernel only
     if (!c->autotune || c->exec_mode != WPCD_EXEC_BATCHED) return 256;
     const auto key = std::make_pair(n, prec);
     {
@@ -382,13 +382,14 @@ int pick_threads(wpcd_ctx *c, Exec &X, int n, int prec, int nw, int nsmp, F laun
     }
     if (capturing(X.stream)) return -1;  // tuning synchronises: never inside a capture
     if (!c->n_sm) cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
-    wpcd_ctx::Tuned t{256, {-1.f, -1.f, -1.f, -1.f}};
+    wpcd_ctx::Tuned t{256, {-1.f, -1.f, -1.f, -1.f, -1.f}};
     float best = 1e30f;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         const int th = cand[k];
+        if (th > 512 && prec == WPCD_PREC_FP64) continue;
         if (prec == WPCD_PREC_FP64 && !jacobi_c_in_smem(n) && (th / 32) * n > n * (n + 1) / 2) continue;
         const int occ = prec == WPCD_PREC_FP64 ? jacobi_f64_occupancy(n, th) : jacobi_mixed_occupancy(n, th);
         if (occ < 1) continue;
@@ -1441,7 +1442,7 @@ int wpcd_tuning(wpcd_ctx *c, int max_entries, int *n_out, int *prec_out, int *th
         if (prec_out) prec_out[k] = kv.first.second;
         if (threads_out) threads_out[k] = kv.second.threads;
         if (ms_out)
-            for (int j = 0; j < 4; ++j) ms_out[4 * k + j] = kv.second.ms[j];
+            for (int j = 0; j < 5; ++j) ms_out[5 * k + j] = kv.second.ms[j];
         ++k;
     }
     return k;
