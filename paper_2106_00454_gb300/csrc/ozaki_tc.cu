@@ -4,24 +4,34 @@
 //
 // A persistent kernel, one CTA per SM, walks the 128 x 64 output tiles of
 // C[b] = A[b] B[b] (A: row slices, B: column slices, both k-contiguous).  Its
-// ten warps split the work:
-//   * warp 8 (one thread) streams k-chunks of 32 through a 3-stage ring: one
+// eighteen warps split the work:
+//   * warp 16 (one thread) streams k-chunks of 32 through a 3-stage ring: one
 //     TMA box per operand brings all six digits of the chunk (128 rows of A,
 //     64 columns of B; 72 KB), in the 64-byte-swizzled K-major layout the
 //     tensor core reads;
-//   * warp 9 (one thread) owns the tensor memory and issues, per chunk, the 21
-//     digit pairs p + q <= 5 into six FP32 accumulators, one per weight
-//     d = p + q (6 x 64 TMEM columns): on full-width tiles as eight M = 128,
-//     K = 16 MMAs of N = 64 .. 256 that each multiply one A digit by up to four
-//     adjacent B digits, on a narrower last column tile as 21 MMAs of N <= 48;
-//   * warps 0-7 drain the accumulators every 128 k into per-thread int64
+//   * warp 17 (one thread) owns the tensor memory and issues, per 16-k step,
+//     the 21 digit pairs p + q <= 5 into six FP32 accumulators, one per weight
+//     d = p + q (6 x 64 TMEM columns), as eight M = 128, K = 16 MMAs of
+//     N = 64 .. 256 that each multiply one A digit by up to four adjacent B
+//     digits.  A narrow last column tile takes the same eight MMAs over B rows
+//     that the TMA zero-filled past n: a chain of small-N MMAs into one
+//     accumulator is bound by the MMA latency and costs several times more
+//     than the padded columns;
+//   * warps 0-15 drain the accumulators every 160 k into per-thread int64
 //     sums, shifted by 36 - 8d (warp w reads TMEM lanes 32 (w % 4) .. + 31 =
-//     rows of the tile, columns 32 (w / 4) .. + 31), and write the FP64 tile,
-//     assembled with integer operations, while the MMAs of the next k-block or
-//     tile proceed.
-// Exactness: a weight-d accumulator sums d + 1 digit pairs over <= 128 k of
-// products below 129 * 128 in magnitude, < 6 * 2^21 < 2^24, so every FP32
-// accumulator is an exact integer.
+//     rows of the tile, columns 16 (w / 4) .. + 15), and write the FP64 tile
+//     while the MMAs of the next k-block or tile proceed: each integer becomes
+//     an IEEE-754 pattern with integer operations (exponent added afterwards,
+//     so the 16 conversions of a thread are independent), and a butterfly of
+//     warp shuffles turns the warp's rows into 128-byte row segments for
+//     coalesced stores.  The drain is bound by the FP32 -> int conversions
+//     (6 x 64 x 128 per 160 k and tile) and is the part the MMAs wait for: the
+//     six accumulators take 384 of the 512 TMEM columns, too many to double.
+// Exactness: digit 0 lies in [-129, 129] and digits 1-5 in [-128, 127], so a
+// weight-d accumulator (at most six digit pairs, two of them with digit 0)
+// gains at most 2 * 129 * 128 + 4 * 128^2 = 99,560 per k; over 160 k that is
+// 15,929,600 < 2^24, so every FP32 accumulator is an exact integer.  The int64
+// sums stay below 2^61 for n <= 1024.
 //
 // Every mbarrier wait is bounded (about a second at the SM clock); on a timeout
 // the kernel records kDevTimeout, the other roles stop at their next wait, the
@@ -36,27 +46,25 @@
 
 namespace wpcd {
 
-// v 2^e as a double (round half away from zero), from the IEEE-754 layout with
-// integer operations only; FP64 arithmetic only where the result leaves the
-// normal range.
-__device__ __forceinline__ double i64_times_pow2(long long v, int e)
+// The IEEE-754 pattern of the int64 v as a double, rounded to 53 bits (half
+// away from zero), from integer operations only and with no branch; 0 for
+// v = 0.  Its exponent field lies in [1023, 1087]; a caller scaling by 2^e adds
+// e << 52, which keeps the pattern normal for e in [-1022, 959].
+__device__ __forceinline__ unsigned long long i64_to_f64_bits(long long v)
 {
-    if (v == 0) return 0.0;
     const unsigned long long m = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-    const int lz = __clzll((long long)m);
-    const unsigned long long mn = m << lz;  // leading one at bit 63: 53 bits kept, 11 dropped
+    const int lz = __clzll((long long)m);  // 64 for m = 0
+    const unsigned long long mn = m << (lz & 63);
     const unsigned long long r = mn + 0x400ull;
-    int msb = 63 - lz;
-    unsigned long long frac = (r >> 11) & ((1ull << 52) - 1);
-    if (r < mn) {  // the rounding carried out of the top bit: 1.0 x 2^{msb + 1}
-        frac = 0;
-        ++msb;
-    }
-    const int be = msb + e + 1023;
-    if (be < 1 || be > 2046) return ldexp((double)v, e);
-    const unsigned long long bits = (v < 0 ? (1ull << 63) : 0ull) | ((unsigned long long)be << 52) | frac;
-    return __longlong_as_double((long long)bits);
+    const bool carry = r < mn;  // the rounding carried out of the top bit
+    const unsigned long long frac = carry ? 0ull : ((r >> 11) & ((1ull << 52) - 1));
+    const unsigned long long be = (unsigned long long)(1086 - lz + (carry ? 1 : 0));  // 63 - lz + 1023
+    const unsigned long long bits = (v < 0 ? (1ull << 63) : 0ull) | (be << 52) | frac;
+    return m == 0 ? 0ull : bits;
 }
+
+// x 2^e for the rare tiles whose scale leaves the range above (out of line).
+__device__ __noinline__ double f64_times_pow2_slow(double x, int e) { return ldexp(x, e); }
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
 {
@@ -66,14 +74,14 @@ __device__ __forceinline__ unsigned smem_u32(const void *p)
 constexpr int kTcM = 128;       // tile rows = TMEM lanes
 constexpr int kTcN = 64;        // tile columns = TMEM columns per accumulator
 constexpr int kTcKC = 32;       // k per stage: 64 bytes of a row = one swizzle span
-constexpr int kTcKBlk = 128;    // k between drains (exact FP32 sums)
+constexpr int kTcKBlk = 160;    // k between drains (exact FP32 sums)
 constexpr int kTcStages = 3;
 constexpr int kTcADigit = kTcM * kTcKC * 2;                        // 8 KB
 constexpr int kTcBDigit = kTcN * kTcKC * 2;                        // 4 KB
 constexpr int kTcAStage = kOzDigits * kTcADigit;                   // 48 KB
 constexpr int kTcStageBytes = kOzDigits * (kTcADigit + kTcBDigit);  // 72 KB
 constexpr int kTcTmemCols = 512;  // 6 x 64 accumulator columns, allocated as a power of two
-constexpr int kTcDrainWarps = 8;  // two per TMEM lane quarter, one per half of the columns
+constexpr int kTcDrainWarps = 16;  // four per TMEM lane quarter, one per 16 columns
 constexpr int kTcDrainCols = kTcN / (kTcDrainWarps / 4);
 constexpr int kTcProducerWarp = kTcDrainWarps, kTcMmaWarp = kTcDrainWarps + 1;
 constexpr int kTcThreads = 32 * (kTcDrainWarps + 2);
@@ -81,8 +89,7 @@ constexpr int kTcSmem = 1024 + kTcStages * kTcStageBytes + 128;  // alignment sl
 constexpr long long kTcWaitCycles = 1ll << 31;
 
 // instruction descriptor: D F32, A and B BF16, both K-major, M = 128; N (bits
-// 17-22, N / 8) is set per tile: 64, or the last column tile's width rounded up
-// to 16, so a ragged edge costs at most 15 padded columns
+// 17-22, N / 8) is set per MMA: 64 times the number of B digits it takes
 constexpr uint32_t kTcIdescBase = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcM >> 4) << 24);
 
 // The 21 digit pairs of one 16-k step as eight wide MMAs.  The B digits of a
@@ -189,16 +196,34 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar)
                  : "memory");
 }
 
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t *r)
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t *r)
 {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
+}
+
+// Transpose the 16 x 16 blocks held one row per lane in each half-warp
+// (v[j] = M[lane % 16][j]) into one column per lane (v[j] = M[j][lane % 16]):
+// four butterfly stages, each swapping the off-diagonal s x s sub-blocks of
+// every 2s x 2s block between lanes l and l ^ s.
+__device__ __forceinline__ void tc_transpose16(double (&v)[16], int lane)
+{
+#pragma unroll
+    for (int s = 8; s >= 1; s >>= 1) {
+        const bool up = (lane & s) != 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j & s) continue;
+            const double send = up ? v[j] : v[j + s];
+            const double recv = __shfl_xor_sync(0xffffffffu, send, s);
+            if (up) v[j] = recv;
+            else v[j + s] = recv;
+        }
+    }
 }
 
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -303,9 +328,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             uint32_t ph = 0;
             for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
                 const TcTile tl = tc_tile(t, per_item, TC, sym);
-                const int tn = tc_tile_n(n, tl.col0);
-                const bool full = tn == kTcN;  // full-width tile: the wide segments
-                const uint32_t idesc = kTcIdescBase | ((uint32_t)(tn >> 3) << 17);
                 for (int k0 = 0; k0 < Kp; k0 += kTcKC) {
                     const bool bfirst = (k0 % kTcKBlk) == 0;
                     const bool blast = ((k0 + kTcKC) % kTcKBlk) == 0 || k0 + kTcKC >= Kp;
@@ -320,36 +342,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     tc_fence_after();
                     const uint32_t sA = ring_s + (uint32_t)(stage * kTcStageBytes), sB = sA + kTcAStage;
                     const uint64_t a0 = tc_desc_sw64(sA), b0 = tc_desc_sw64(sB);
-                    if (full) {
 #pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {  // K = 16: 32 bytes further into the swizzle span
-                            if (kk == 1 && k0 + 16 >= n) break;  // that half of the chunk is zero padding
+                    for (int kk = 0; kk < 2; ++kk) {  // K = 16: 32 bytes further into the swizzle span
+                        if (kk == 1 && k0 + 16 >= n) break;  // that half of the chunk is zero padding
 #pragma unroll
-                            for (int g = 0; g < kTcSegs; ++g) {
-                                int p, q0, nq;
-                                tc_seg(g, p, q0, nq);
-                                nq = min(nq, dmax - p - q0 + 1);
-                                if (nq <= 0) continue;
-                                const uint64_t ad = a0 + (uint64_t)((p * kTcADigit + kk * 32) >> 4);
-                                const uint64_t bd = b0 + (uint64_t)((q0 * kTcBDigit + kk * 32) >> 4);
-                                tc_mma(tmem + (uint32_t)((p + q0) * kTcN), ad, bd,
-                                       kTcIdescBase | ((uint32_t)(nq * kTcN >> 3) << 17),
-                                       (bfirst && kk == 0 && p == 0) ? 0u : 1u);
-                            }
+                        for (int g = 0; g < kTcSegs; ++g) {
+                            int p, q0, nq;
+                            tc_seg(g, p, q0, nq);
+                            nq = min(nq, dmax - p - q0 + 1);
+                            if (nq <= 0) continue;
+                            const uint64_t ad = a0 + (uint64_t)((p * kTcADigit + kk * 32) >> 4);
+                            const uint64_t bd = b0 + (uint64_t)((q0 * kTcBDigit + kk * 32) >> 4);
+                            tc_mma(tmem + (uint32_t)((p + q0) * kTcN), ad, bd,
+                                   kTcIdescBase | ((uint32_t)(nq * kTcN >> 3) << 17),
+                                   (bfirst && kk == 0 && p == 0) ? 0u : 1u);
                         }
-                    } else {
-                        for (int d = 0; d <= dmax; ++d)
-                            for (int p = 0; p <= d; ++p) {
-                                const int q = d - p;
-#pragma unroll
-                                for (int kk = 0; kk < 2; ++kk) {
-                                    if (kk == 1 && k0 + 16 >= n) break;
-                                    const uint64_t ad = a0 + (uint64_t)((p * kTcADigit + kk * 32) >> 4);
-                                    const uint64_t bd = b0 + (uint64_t)((q * kTcBDigit + kk * 32) >> 4);
-                                    tc_mma(tmem + (uint32_t)(d * kTcN), ad, bd, idesc,
-                                           (bfirst && p == 0 && kk == 0) ? 0u : 1u);
-                                }
-                            }
                     }
                     tc_commit(empty_s + 8u * stage);
                     ++committed;
@@ -373,13 +380,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         __syncwarp();
     } else {
-        // ---- drain and epilogue: row (warp % 4) * 32 + lane of the tile, columns c0 .. c0 + 31
+        // ---- drain and epilogue: rows rbase .. + 31 of the tile (TMEM lane quarter
+        // warp % 4, one row per lane), columns c0 .. c0 + 15
+        static_assert(kTcDrainCols == 16, "the drain and its transpose take 16 columns per warp");
         int blk = 0;
-        const int row_in = (warp & 3) * 32 + lane, c0 = (warp >> 2) * kTcDrainCols;
+        const int c0 = (warp >> 2) * kTcDrainCols;
         const uint32_t tbase = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
         for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
             const TcTile tl = tc_tile(t, per_item, TC, sym);
             const bool live = c0 < tc_tile_n(n, tl.col0);  // this warp's columns hold results
+            const int rbase = tl.row0 + (warp & 3) * 32, cbase = tl.col0 + c0;
+            const bool work = live && rbase < n;  // warp-uniform
+            // the exponents of the row (this lane's) and of column cbase + lane % 16,
+            // loaded before the accumulators are ready; past n a valid column's
+            int er = 0, ecl = 0;
+            if (work) {
+                if (rbase + lane < n) er = ea_all[(size_t)(tl.b % a_mod) * n + rbase + lane];
+                const int cl = cbase + (lane & 15);
+                ecl = eb_all[(size_t)tl.b * n + (cl < n ? cl : cbase)];
+            }
             long long acc[kTcDrainCols];
 #pragma unroll
             for (int j = 0; j < kTcDrainCols; ++j) acc[j] = 0;
@@ -392,20 +411,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                 for (int d = 0; d < kOzDigits; d += 2) {  // two accumulators per round trip
                     if (d > dmax || !live) break;
-                    uint32_t r0[32], r1[32];
+                    uint32_t r0[kTcDrainCols], r1[kTcDrainCols];
                     const bool two = d + 1 <= dmax;
-                    tc_ld32(tbase + (uint32_t)(d * kTcN), r0);
-                    if (two) tc_ld32(tbase + (uint32_t)((d + 1) * kTcN), r1);
+                    tc_ld16(tbase + (uint32_t)(d * kTcN), r0);
+                    if (two) tc_ld16(tbase + (uint32_t)((d + 1) * kTcN), r1);
                     tc_wait_ld();
                     const int sh0 = 36 - 8 * d, sh1 = sh0 - 8;  // weight 2^{-8(d+2)+2} = 2^{sh-50}
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
+                    for (int j = 0; j < kTcDrainCols; ++j) {
                         const int v = __float2int_rn(__uint_as_float(r0[j]));
                         acc[j] += sh0 >= 0 ? ((long long)v << sh0) : (long long)(v >> -sh0);
                     }
                     if (two) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
+                        for (int j = 0; j < kTcDrainCols; ++j) {
                             const int v = __float2int_rn(__uint_as_float(r1[j]));
                             acc[j] += sh1 >= 0 ? ((long long)v << sh1) : (long long)(v >> -sh1);
                         }
@@ -415,19 +434,50 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 mbar_arrive(acce_s);  // the tensor core may overwrite the accumulators
             }
             if (failed) break;
-            const int r = tl.row0 + row_in;
-            if (r < n) {
-                const int *ea = ea_all + (size_t)(tl.b % a_mod) * n, *eb = eb_all + (size_t)tl.b * n;
-                double *C = C_all + (size_t)tl.b * n * n;
-                const int er = ea[r];
+            if (!work) continue;
+            // element (r, cbase + j) = acc[j] 2^{er + ec_j - 50}: first the integers as
+            // doubles of their own scale, then the exponents added to the fields
+            double *C = C_all + (size_t)tl.b * n * n;
+            const int r = rbase + lane;
+            double v[kTcDrainCols];
+            unsigned long long u[kTcDrainCols];
+#pragma unroll
+            for (int j = 0; j < kTcDrainCols; ++j) u[j] = i64_to_f64_bits(acc[j]);
+            int emin = ecl, emax = ecl;
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                emin = min(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+                emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+            }
+            if (__all_sync(0xffffffffu, er - 50 + emin >= -1022 && er - 50 + emax <= 959)) {
 #pragma unroll
                 for (int j = 0; j < kTcDrainCols; ++j) {
-                    const int c = tl.col0 + c0 + j;
-                    if (c >= n || (sym && c < r)) continue;
-                    const double v = i64_times_pow2(acc[j], er + eb[c] - 50);
-                    C[(size_t)r * n + c] = v;
-                    if (sym && c > r) C[(size_t)c * n + r] = v;
+                    const long long e = er + __shfl_sync(0xffffffffu, ecl, j) - 50;
+                    v[j] = __longlong_as_double(u[j] == 0 ? 0ll : (long long)(u[j] + ((unsigned long long)e << 52)));
                 }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kTcDrainCols; ++j) {
+                    const int e = er + __shfl_sync(0xffffffffu, ecl, j) - 50;
+                    v[j] = f64_times_pow2_slow(__longlong_as_double((long long)u[j]), e);
+                }
+            }
+            if (sym) {
+                // mirrored elements C[c][r], c > r: lanes run along r, coalesced
+#pragma unroll
+                for (int j = 0; j < kTcDrainCols; ++j) {
+                    const int c = cbase + j;
+                    if (c < n && r < n && c > r) C[(size_t)c * n + r] = v[j];
+                }
+            }
+            // lane l now takes column cbase + l % 16 of rows rg + j: each store
+            // writes two 128-byte row segments
+            tc_transpose16(v, lane);
+            const int c = cbase + (lane & 15), rg = rbase + (lane & 16);
+#pragma unroll
+            for (int j = 0; j < kTcDrainCols; ++j) {
+                const int rr = rg + j;
+                if (rr < n && c < n && (!sym || c >= rr)) C[(size_t)rr * n + c] = v[j];
             }
         }
         if (failed) *abort_flag = 1;
