@@ -116,11 +116,15 @@ enum {
  * path: two iterations leave phase errors below 1e-6 deg and cross-section
  * errors near 1e-6 mb; one iteration leaves phase errors up to ~6e-4 deg but
  * cross-section errors up to ~0.02 mb, outside the 0.01 mb bar, so it is only
- * an opt-in for callers that need the phases alone. */
+ * an opt-in for callers that need the phases alone.  WPCD_OPT_REFINE_DIGITS
+ * (4..6, default 6; tensor refinement engine): balanced 8-bit digits per operand
+ * of the refinement's digit products -- 6 gives FP64-accurate products (21 digit
+ * pairs), 5 and 4 about 39 and 31 bits (15 and 10 pairs), trading the refined
+ * accuracy for product time. */
 enum { WPCD_EXEC_BATCHED = 0, WPCD_EXEC_PLAIN = 1 };
 enum { WPCD_REFINE_TENSOR = 0, WPCD_REFINE_FP64 = 1 };
 enum { WPCD_OPT_EXEC = 1, WPCD_OPT_REFINE = 2, WPCD_OPT_AUTOTUNE = 3, WPCD_OPT_GRAPH = 4, WPCD_OPT_BIG_SLOTS = 5,
-       WPCD_OPT_ROTATE = 6, WPCD_OPT_REFINE_ITERS = 7 };
+       WPCD_OPT_ROTATE = 6, WPCD_OPT_REFINE_ITERS = 7, WPCD_OPT_REFINE_DIGITS = 8 };
 
 /* ---- context --------------------------------------------------------------------------------- */
 

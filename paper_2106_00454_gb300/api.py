@@ -19,7 +19,8 @@ PREC_FP64, PREC_MIXED = 0, 1
 AVG_FREE_BIN, AVG_SWP_INDEX, POINT = 0, 1, 2  # resolvent (wpcd_resolvent)
 EXEC_BATCHED, EXEC_PLAIN = 0, 1
 REFINE_TENSOR, REFINE_FP64 = 0, 1
-OPT_EXEC, OPT_REFINE, OPT_AUTOTUNE, OPT_GRAPH, OPT_BIG_SLOTS, OPT_ROTATE, OPT_REFINE_ITERS = 1, 2, 3, 4, 5, 6, 7
+OPT_EXEC, OPT_REFINE, OPT_AUTOTUNE, OPT_GRAPH, OPT_BIG_SLOTS, OPT_ROTATE, OPT_REFINE_ITERS, OPT_REFINE_DIGITS = \
+    1, 2, 3, 4, 5, 6, 7, 8
 
 
 class WpcdError(RuntimeError):
@@ -92,6 +93,10 @@ class Context:
     def set_refine_iters(self, iters: int):
         """FP64 refinement iterations of the mixed path (1..4, default 2)."""
         _ck(self.lib.wpcd_set_option(self.h, OPT_REFINE_ITERS, int(iters)), "wpcd_set_option")
+
+    def set_refine_digits(self, digits: int):
+        """Digits per operand of the mixed path's refinement products (4..6, default 6)."""
+        _ck(self.lib.wpcd_set_option(self.h, OPT_REFINE_DIGITS, int(digits)), "wpcd_set_option")
 
     def set_rotate(self, on: bool):
         """Mixed path: FP32 eigensolve in the mean-potential eigenbasis (default on)."""

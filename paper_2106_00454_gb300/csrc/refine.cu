@@ -214,8 +214,9 @@ size_t refine_scratch_per_item(int n, int engine)
 cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_samples, int sample0, int n,
                           int n_terms, const double *coeffs, void *scratch, double *eps_all, double *X_all,
                           int iters, int engine, cudaStream_t st, int *err, const __nv_bfloat16 *rot_s,
-                          const int *rot_e)
+                          const int *rot_e, int digits)
 {
+    if (digits < 4 || digits > kOzDigits) return cudaErrorInvalidValue;
     if (rot_s && engine != 0) return cudaErrorInvalidValue;
     (void)n_terms;
     (void)coeffs;
@@ -243,10 +244,10 @@ cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_s
     double *x = Xs, *xn = Y;
     if (engine == 0) CKR(launch_oz_split(n, items, false, H, sH, eH, st));  // rows of H, reused
     for (int it = 0; it < iters; ++it) {
-        // all 6 digits on every iteration: errors of S = X^T H X are divided by
-        // eigenvalue gaps (~1e-6 of ||H||) in E, so even the first iteration
-        // needs FP64-accurate products (4 digits cost 100x in phase accuracy)
-        const int dg = 6;
+        // digits per operand (6 by default, FP64-accurate products): errors of
+        // S = X^T H X are divided by eigenvalue gaps (~1e-6 of ||H||) in E, so
+        // the digit count sets the refined accuracy of every iteration
+        const int dg = digits;
         if (engine == 0) {
             CKR(launch_oz_split(n, items, true, x, sXc, eXc, st));                   // columns of X
             CKR(launch_oz_gemm_slices(n, items, sH, eH, sXc, eXc, xn, st, dg, false, err));       // Y = H X
@@ -278,7 +279,7 @@ cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_s
     if (rot_s) {
         // X = C0 X' (the same C0 for every sample of a channel: items run channel-fastest)
         CKR(launch_oz_split(n, items, true, x, sXc, eXc, st));
-        CKR(launch_oz_gemm_slices(n, items, rot_s, rot_e, sXc, eXc, xn, st, 6, false, err, nw));
+        CKR(launch_oz_gemm_slices(n, items, rot_s, rot_e, sXc, eXc, xn, st, digits, false, err, nw));
         xout = xn;
     }
 #undef CKR

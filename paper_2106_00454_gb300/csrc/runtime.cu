@@ -136,6 +136,7 @@ struct wpcd_ctx {
     int refine_engine = WPCD_REFINE_TENSOR;
     int rotate = 1;  // mixed path in the mean-potential eigenbasis (WPCD_OPT_ROTATE)
     int refine_iters = kRefineIters;  // WPCD_OPT_REFINE_ITERS
+    int refine_digits = 6;            // WPCD_OPT_REFINE_DIGITS
     int autotune = 1;
     int n_sm = 0;
     struct Tuned {
@@ -637,7 +638,7 @@ wpcd_status run_bucket_big(wpcd_ctx *c, Exec &X, VSetH &v, EigH &e, const double
         Launch L(c, X, WPCD_PHASE_REFINE);
         const VSetH::RotB *rb = e.rot ? &v.rotb.at(n) : nullptr;
         CK(launch_refine(e.cd_dev, work, nw, ns, smp0 + s0, n, v.n_terms, cf, base, e.eps, e.C, c->refine_iters,
-                         c->refine_engine, X.stream, X.err, rb ? rb->sC : nullptr, rb ? rb->eC : nullptr));
+                         c->refine_engine, X.stream, X.err, rb ? rb->sC : nullptr, rb ? rb->eC : nullptr, c->refine_digits));
     }
     return WPCD_OK;
 }
@@ -702,7 +703,7 @@ wpcd_status diag_body(wpcd_ctx *c, Exec &X, VSetH &v, const double *coeffs, int 
             Launch L(c, X, WPCD_PHASE_REFINE);
             const VSetH::RotB *rb = e.rot ? &v.rotb.at(n) : nullptr;
             CK(launch_refine(e.cd_dev, work, nw, ns, smp0 + s0, n, v.n_terms, cf, base, e.eps, e.C, c->refine_iters,
-                             c->refine_engine, X.stream, X.err, rb ? rb->sC : nullptr, rb ? rb->eC : nullptr));
+                             c->refine_engine, X.stream, X.err, rb ? rb->sC : nullptr, rb ? rb->eC : nullptr, c->refine_digits));
         }
         return WPCD_OK;
     };
@@ -887,6 +888,10 @@ wpcd_status wpcd_set_option(wpcd_ctx *c, int key, int value)
     }
     if (key == WPCD_OPT_REFINE_ITERS && value >= 1 && value <= 4) {
         c->refine_iters = value;
+        return WPCD_OK;
+    }
+    if (key == WPCD_OPT_REFINE_DIGITS && value >= 4 && value <= 6) {
+        c->refine_digits = value;
         return WPCD_OK;
     }
     if (key == WPCD_OPT_ROTATE && (value == 0 || value == 1)) {

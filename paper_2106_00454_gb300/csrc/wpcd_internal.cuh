@@ -287,7 +287,7 @@ size_t refine_scratch_per_item(int n, int engine);
 cudaError_t launch_refine(const ChanDev *chans, const int *work, int nw, int n_samples, int sample0, int n,
                           int n_terms, const double *coeffs, void *scratch, double *eps_all, double *X_all,
                           int iters, int engine, cudaStream_t st, int *err = nullptr,
-                          const __nv_bfloat16 *rot_s = nullptr, const int *rot_e = nullptr);
+                          const __nv_bfloat16 *rot_s = nullptr, const int *rot_e = nullptr, int digits = 6);
 cudaError_t launch_batched_dgemm(int n, int items, bool ta, const double *A, const double *B, double *C,
                                  void *scratch, int engine, cudaStream_t st, int *err = nullptr);
 size_t batched_dgemm_scratch(int n, int items);

@@ -172,3 +172,21 @@ def test_single_refinement_iteration_phases(ctx, orc):
     finally:
         ctx.set_refine_iters(2)
     _report("nwp150_one_iteration", compare_mixed(wl, gpu, oracle_run(orc, wl), tol_s=0.05))
+
+
+def test_refine_digits_option(ctx, orc):
+    """WPCD_OPT_REFINE_DIGITS = 5 (15 digit pairs per product instead of 21): the
+    N_WP = 150 workload stays within the mixed tolerances of the oracle (measured:
+    1.9e-7 deg, 3.0e-6 mb with the FP64 projection); out-of-range values are refused."""
+    from paper_2106_00454_gb300 import api
+    wl = W.workload_mixed(n_samples=2)
+    md = api.Model(ctx, wl)
+    ctx.set_refine_digits(5)
+    try:
+        worst = compare_mixed(wl, gpu_run(ctx, md, wl, prec=MIXED), oracle_run(orc, wl))
+    finally:
+        ctx.set_refine_digits(6)
+    _report("nwp150_refine_digits5", worst)
+    assert worst["sigma_mb"] < 1e-3 and worst["delta_deg"] < 1e-4, worst
+    with pytest.raises(api.WpcdError):
+        ctx.set_refine_digits(3)
