@@ -24,9 +24,10 @@
 //     an IEEE-754 pattern with integer operations (exponent added afterwards,
 //     so the 16 conversions of a thread are independent), and a butterfly of
 //     warp shuffles turns the warp's rows into 128-byte row segments for
-//     coalesced stores.  The drain is bound by the FP32 -> int conversions
-//     (6 x 64 x 128 per 160 k and tile) and is the part the MMAs wait for: the
-//     six accumulators take 384 of the 512 TMEM columns, too many to double.
+//     coalesced stores.  The drain (6 x 64 x 128 FP32 -> int conversions per
+//     160 k and tile) is the part the MMAs wait for: the six accumulators take
+//     384 of the 512 TMEM columns, too many to double; the warps hand the tensor
+//     memory back as soon as the last pair of accumulators is in registers.
 // Exactness: digit 0 lies in [-129, 129] and digits 1-5 in [-128, 127], so a
 // weight-d accumulator (at most six digit pairs, two of them with digit 0)
 // gains at most 2 * 129 * 128 + 4 * 128^2 = 99,560 per k; over 160 k that is
@@ -408,19 +409,28 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     break;
                 }
                 tc_fence_after();
+                // two accumulators per round trip; the arrival that hands the tensor memory
+                // back comes as soon as the last pair is in registers, so its conversion
+                // runs beside the next block's MMAs
 #pragma unroll
-                for (int d = 0; d < kOzDigits; d += 2) {  // two accumulators per round trip
-                    if (d > dmax || !live) break;
+                for (int d = 0; d < kOzDigits; d += 2) {
                     uint32_t r0[kTcDrainCols], r1[kTcDrainCols];
-                    const bool two = d + 1 <= dmax;
-                    tc_ld16(tbase + (uint32_t)(d * kTcN), r0);
+                    const bool any = live && d <= dmax, two = any && d + 1 <= dmax;  // warp-uniform
+                    if (any) tc_ld16(tbase + (uint32_t)(d * kTcN), r0);
                     if (two) tc_ld16(tbase + (uint32_t)((d + 1) * kTcN), r1);
-                    tc_wait_ld();
+                    if (any) tc_wait_ld();
+                    const bool last = !any || d + 2 > dmax;
+                    if (last) {
+                        tc_fence_before();
+                        mbar_arrive(acce_s);  // the tensor core may overwrite the accumulators
+                    }
                     const int sh0 = 36 - 8 * d, sh1 = sh0 - 8;  // weight 2^{-8(d+2)+2} = 2^{sh-50}
+                    if (any) {
 #pragma unroll
-                    for (int j = 0; j < kTcDrainCols; ++j) {
-                        const int v = __float2int_rn(__uint_as_float(r0[j]));
-                        acc[j] += sh0 >= 0 ? ((long long)v << sh0) : (long long)(v >> -sh0);
+                        for (int j = 0; j < kTcDrainCols; ++j) {
+                            const int v = __float2int_rn(__uint_as_float(r0[j]));
+                            acc[j] += sh0 >= 0 ? ((long long)v << sh0) : (long long)(v >> -sh0);
+                        }
                     }
                     if (two) {
 #pragma unroll
@@ -429,9 +439,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             acc[j] += sh1 >= 0 ? ((long long)v << sh1) : (long long)(v >> -sh1);
                         }
                     }
+                    if (last) break;
                 }
-                tc_fence_before();
-                mbar_arrive(acce_s);  // the tensor core may overwrite the accumulators
             }
             if (failed) break;
             if (!work) continue;
