@@ -55,7 +55,7 @@ L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 # capture of 152 solves of 3S1-3D1 at N_WP = 150 (profiles/k_jacobi_mixed_3s1d1_nwp150_152samples.md:
 # 12.3 MB + 265.1 MB over 152 x 300^2 elements); the traffic is the FP64 H and eigenvectors
 # handed to the refinement, so it scales with n^2
-JACOBI_MIXED_DRAM_BYTES_PER_N2 = (12.347392e6 + 265.13664e6) / (152 * 300 * 300)
+JACOBI_MIXED_DRAM_BYTES_PER_N2 = (15.507968e6 + 269.930496e6) / (152 * 300 * 300)
 SAT_P99_BOUND_MS = 250.0     # the saturation sweep's latency bound
 SERVE_MAX_QUEUE = 4096       # requests waiting at most (the server refuses beyond)
 
@@ -741,7 +741,7 @@ def run_wpcd(args, ws, rank, lrank):
             # DRAM bytes per launch: the capture's bytes per matrix element times the step's
             # sum of n^2 over its solves, over the step's Jacobi launches
             jac["traffic"] = JACOBI_MIXED_DRAM_BYTES_PER_N2 * S * sum(v * v for v in big) / jac["launches_per_step"]
-            jac["traffic_note"] = ("ncu capture of 152 solves at n = 300 (20.3 B of DRAM traffic per matrix element "
+            jac["traffic_note"] = ("ncu capture of 152 solves at n = 300 (20.8 B of DRAM traffic per matrix element "
                                    "per solve), scaled by the step's sum of n^2; bytes per launch")
 
         clocks = clk.summary()
