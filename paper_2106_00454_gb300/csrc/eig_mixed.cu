@@ -48,14 +48,14 @@ __host__ __device__ inline size_t mix_a_floats(int n)
     return (a + 3) & ~(size_t)3;  // the slot table after it is 16-byte aligned
 }
 
-// A float packed [npad] | slot table int4 [h] {p, q, base(p), base(q)} | rotations float2 [h] {c, s} |
+// A float packed [npad] | rotations float2 [h] {c, s} | slot table uint [h] {p | q << 16} |
 // a_pp', a_qq' float [h] each | flags int [8] | rank of each slot among the round's rotating
 // slots int [h] | rotating slots ushort [h, even] | slot pairs ushort [quads, even] | (16-byte aligned)
 // C float [n][ldc] (column-major) when it is kept in shared memory
 __host__ __device__ inline size_t mix_smem(int n, bool c_in_smem)
 {
     const int h = mpad(n) / 2;
-    size_t b = mix_a_floats(n) * 4 + (size_t)h * (16 + 8 + 8) + 8 * 4 + (size_t)h * 4 + (size_t)((h + 1) & ~1) * 2;
+    size_t b = mix_a_floats(n) * 4 + (size_t)h * (8 + 4 + 8) + 8 * 4 + (size_t)h * 4 + (size_t)((h + 1) & ~1) * 2;
     b += (size_t)((mquads(n) + 1) & ~1) * 2;
     b = (b + 15) & ~(size_t)15;
     if (c_in_smem) b += (size_t)n * mldc(n) * 4;
@@ -109,9 +109,11 @@ __global__ void __launch_bounds__(2 * kMixMaxThreads, 1) k_jacobi_mixed(const Ch
     extern __shared__ float4 smem_f4[];
     unsigned char *sb = reinterpret_cast<unsigned char *>(smem_f4);
     float *A = reinterpret_cast<float *>(sb);
-    int4 *sl = reinterpret_cast<int4 *>(A + mix_a_floats(n));
-    float2 *cs = reinterpret_cast<float2 *>(sl + h);
-    float *dpp = reinterpret_cast<float *>(cs + h), *dqq = dpp + h;
+    // the slot table holds p | q << 16 (one 4-byte word a slot: a warp reading 32 slots is one
+    // shared-memory wavefront); the packed bases p(p+1)/2 are recomputed where needed
+    float2 *cs = reinterpret_cast<float2 *>(A + mix_a_floats(n));
+    unsigned *slp = reinterpret_cast<unsigned *>(cs + h);
+    float *dpp = reinterpret_cast<float *>(slp + h), *dqq = dpp + h;
     // flags: [0] rotation in this sweep; [1..3] rotation in this round and [4..6] the
     // round's count of rotating slots, both cycled over three rounds
     int *flags = reinterpret_cast<int *>(dqq + h);
@@ -154,12 +156,14 @@ __global__ void __launch_bounds__(2 * kMixMaxThreads, 1) k_jacobi_mixed(const Ch
     // 2 x 2 block of A in rows of slot P and columns of slot P2 (P < P2): J_P^T B J_P2
     auto quad_update = [&](int P, int P2) {
         const float2 r1 = cs[P], r2 = cs[P2];
-        const int4 u = sl[P], v = sl[P2];
+        const unsigned u = slp[P], v = slp[P2];
+        const int up = (int)(u & 0xFFFFu), uq = (int)(u >> 16), vp = (int)(v & 0xFFFFu), vq = (int)(v >> 16);
+        const int ubp = up * (up + 1) >> 1, ubq = uq * (uq + 1) >> 1, vbp = vp * (vp + 1) >> 1, vbq = vq * (vq + 1) >> 1;
         // packed index of (x, y): base(max) + min
-        const int i00 = u.x <= v.x ? v.z + u.x : u.z + v.x;
-        const int i01 = u.x <= v.y ? v.w + u.x : u.z + v.y;
-        const int i10 = u.y <= v.x ? v.z + u.y : u.w + v.x;
-        const int i11 = u.y <= v.y ? v.w + u.y : u.w + v.y;
+        const int i00 = up <= vp ? vbp + up : ubp + vp;
+        const int i01 = up <= vq ? vbq + up : ubp + vq;
+        const int i10 = uq <= vp ? vbp + uq : ubq + vp;
+        const int i11 = uq <= vq ? vbq + uq : ubq + vq;
         const float b00 = A[i00], b01 = A[i01], b10 = A[i10], b11 = A[i11];
         const float c = r1.x, s = r1.y, c2 = r2.x, s2 = r2.y;
         const float x00 = c2 * b00 - s2 * b01, x01 = s2 * b00 + c2 * b01;
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(2 * kMixMaxThreads, 1) k_jacobi_mixed(const Ch
                 } else {
                     rank[k] = -1;
                 }
-                sl[k] = make_int4(p, q, pb, qb);
+                slp[k] = (unsigned)p | ((unsigned)q << 16);
                 cs[k] = make_float2(c, s);
                 dpp[k] = app;
                 dqq[k] = aqq;
@@ -255,10 +259,11 @@ __global__ void __launch_bounds__(2 * kMixMaxThreads, 1) k_jacobi_mixed(const Ch
                 }
                 for (int i = tid; i < na; i += nt) {
                     const int k = act[i];
-                    const int4 u = sl[k];
-                    A[u.z + u.x] = dpp[k];
-                    A[u.w + u.y] = dqq[k];
-                    A[u.w + u.x] = 0.0f;
+                    const int p = (int)(slp[k] & 0xFFFFu), q = (int)(slp[k] >> 16);
+                    const int pb = p * (p + 1) / 2, qb = q * (q + 1) / 2;
+                    A[pb + p] = dpp[k];
+                    A[qb + q] = dqq[k];
+                    A[qb + p] = 0.0f;
                 }
                 // C is column-major (column s contiguous, stride ldc): one warp per
                 // rotation, each lane four consecutive rows of the two columns
@@ -266,9 +271,8 @@ __global__ void __launch_bounds__(2 * kMixMaxThreads, 1) k_jacobi_mixed(const Ch
                 for (int i = warp; i < na; i += nwarps) {
                     const int k = act[i];
                     const float2 r1 = cs[k];
-                    const int4 u = sl[k];
-                    float4 *Cp = reinterpret_cast<float4 *>(C + (size_t)u.x * ldc);
-                    float4 *Cq = reinterpret_cast<float4 *>(C + (size_t)u.y * ldc);
+                    float4 *Cp = reinterpret_cast<float4 *>(C + (size_t)(slp[k] & 0xFFFFu) * ldc);
+                    float4 *Cq = reinterpret_cast<float4 *>(C + (size_t)(slp[k] >> 16) * ldc);
                     const float c = r1.x, s = r1.y;
                     if (!C_SMEM && nv <= 96) {
                         // columns in global memory (L2): every load of the two columns is
