@@ -53,9 +53,9 @@ FP32_PEAK_NOTE = ("builder-derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz;
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 # k_jacobi_mixed DRAM bytes (read + write) per solve per matrix element, from the ncu
 # capture of 152 solves of 3S1-3D1 at N_WP = 150 (profiles/k_jacobi_mixed_3s1d1_nwp150_152samples.md:
-# 12.3 MB + 265.1 MB over 152 x 300^2 elements); the traffic is the FP64 H and eigenvectors
+# 17.8 MB + 274.1 MB over 152 x 300^2 elements); the traffic is the FP64 H and eigenvectors
 # handed to the refinement, so it scales with n^2
-JACOBI_MIXED_DRAM_BYTES_PER_N2 = (15.507968e6 + 269.930496e6) / (152 * 300 * 300)
+JACOBI_MIXED_DRAM_BYTES_PER_N2 = (17.841408e6 + 274.119168e6) / (152 * 300 * 300)
 SAT_P99_BOUND_MS = 250.0     # the saturation sweep's latency bound
 SERVE_MAX_QUEUE = 4096       # requests waiting at most (the server refuses beyond)
 
@@ -737,11 +737,11 @@ def run_wpcd(args, ws, rank, lrank):
                 r["unit"] = "TFLOP/s"
                 r["frac"] = r["achieved"] / r["peak"]
                 r["traffic"] = None
-        if prec == api.PREC_MIXED and jac["launches_per_step"] > 0 and all(v <= 310 for v in big):
+        if prec == api.PREC_MIXED and jac["launches_per_step"] > 0 and all(v <= 304 for v in big):
             # DRAM bytes per launch: the capture's bytes per matrix element times the step's
             # sum of n^2 over its solves, over the step's Jacobi launches
             jac["traffic"] = JACOBI_MIXED_DRAM_BYTES_PER_N2 * S * sum(v * v for v in big) / jac["launches_per_step"]
-            jac["traffic_note"] = ("ncu capture of 152 solves at n = 300 (20.8 B of DRAM traffic per matrix element "
+            jac["traffic_note"] = ("ncu capture of 152 solves at n = 300 (21.3 B of DRAM traffic per matrix element "
                                    "per solve), scaled by the step's sum of n^2; bytes per launch")
 
         clocks = clk.summary()

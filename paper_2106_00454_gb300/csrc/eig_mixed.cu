@@ -30,11 +30,26 @@ constexpr float kMixThreshFrac = 0.1f;
 
 __host__ __device__ inline int mpad(int n) { return (n + 1) & ~1; }
 __host__ __device__ inline int mldc(int n) { return (n + 3) & ~3; }  // column stride of C: float4 rows
-__host__ __device__ inline size_t mpacked(int n) { return (size_t)n * (n + 1) / 2; }
+
+// A is stored as its upper triangle, column by column, with column y (rows
+// 0..y) starting at mcol(y) == y (mod 32): element (x, y), x <= y, then lies in
+// shared-memory bank (x + y) mod 32, whichever index is the larger.  A block
+// update reads, across a warp, the elements of one slot's index with the
+// indices of consecutive tournament slots, which run over consecutive values
+// (r + k + 1 upwards, r - k + 1 downwards), so the 32 lanes of one access fall
+// in 32 different banks, apart from a row change or a wrap of the tournament
+// inside the warp.  (Columns packed back to back at y (y + 1) / 2 put two or
+// more lanes in one bank on about half of those accesses.)  The padding is
+// (-y) mod 32 floats after column y: 15.5 floats a column on average.
+__host__ __device__ inline int mcol(int y)
+{
+    const int a = y >> 5, b = y & 31;
+    return y * (y + 1) / 2 + 496 * a + (b ? (b - 1) * (64 - b) / 2 : 0);
+}
 
 // Index pairs (P, P2), P < P2, of the rotation slots whose 2 x 2 blocks of A
-// one round updates: h (h - 1) / 2 of them, 8 bits each (h <= 256, which
-// every A that fits in shared memory satisfies).
+// one round updates: h (h - 1) / 2 of them in row order of P, 8 bits each
+// (h <= 256, which every A that fits in shared memory satisfies).
 __host__ __device__ inline int mquads(int n)
 {
     const int h = mpad(n) / 2;
@@ -43,19 +58,20 @@ __host__ __device__ inline int mquads(int n)
 
 __host__ __device__ inline size_t mix_a_floats(int n)
 {
-    size_t a = mpacked(mpad(n));  // the odd-n phantom row and column are kept (as zeros)
+    const int np = mpad(n);  // the odd-n phantom row and column are kept (as zeros)
+    size_t a = (size_t)mcol(np - 1) + np;
     if (a < (size_t)10 * n) a = (size_t)10 * n;
-    return (a + 3) & ~(size_t)3;  // the slot table after it is 16-byte aligned
+    return (a + 3) & ~(size_t)3;  // the slot records after it are 16-byte aligned
 }
 
-// A float packed [npad] | rotations float2 [h] {c, s} | slot table uint [h] {p | q << 16} |
-// a_pp', a_qq' float [h] each | flags int [8] | rank of each slot among the round's rotating
+// A float [mix_a_floats] | slot records uint4 [h] {c, s', a | b << 16, mcol(a) | mcol(b) << 16} |
+// a_aa', a_bb' float [h] each | flags int [8] | rank of each slot among the round's rotating
 // slots int [h] | rotating slots ushort [h, even] | slot pairs ushort [quads, even] | (16-byte aligned)
 // C float [n][ldc] (column-major) when it is kept in shared memory
 __host__ __device__ inline size_t mix_smem(int n, bool c_in_smem)
 {
     const int h = mpad(n) / 2;
-    size_t b = mix_a_floats(n) * 4 + (size_t)h * (8 + 4 + 8) + 8 * 4 + (size_t)h * 4 + (size_t)((h + 1) & ~1) * 2;
+    size_t b = mix_a_floats(n) * 4 + (size_t)h * (16 + 8) + 8 * 4 + (size_t)h * 4 + (size_t)((h + 1) & ~1) * 2;
     b += (size_t)((mquads(n) + 1) & ~1) * 2;
     b = (b + 15) & ~(size_t)15;
     if (c_in_smem) b += (size_t)n * mldc(n) * 4;
@@ -67,10 +83,14 @@ size_t jacobi_mixed_c_bytes(int n) { return (size_t)n * mldc(n) * 4; }
 
 // Rotation slot k of round r (0 <= r < M = npad - 1) of the round-robin
 // tournament: the same pairs as jac_pair_of, with the modulo reduced to one
-// conditional correction (r + k < 2M, r - k > -M).
-__device__ __forceinline__ void mix_pair(int r, int k, int M, int &p, int &q)
+// conditional correction (r + k < 2M, r - k > -M).  The pair comes in
+// tournament order (a = r + k + 1, b = r - k + 1, both mod M), not sorted: over
+// consecutive slots a counts up and b down, which the layout of A turns into
+// distinct banks.
+__device__ __forceinline__ void mix_pair(int r, int k, int M, int &a, int &b)
 {
-    int a = 0, b = 1 + r;
+    a = 0;
+    b = 1 + r;
     if (k != 0) {
         a = r + k;
         if (a >= M) a -= M;
@@ -79,8 +99,6 @@ __device__ __forceinline__ void mix_pair(int r, int k, int M, int &p, int &q)
         if (b < 0) b += M;
         ++b;
     }
-    p = a < b ? a : b;
-    q = a < b ? b : a;
 }
 
 // Launch bound 1024 threads, one CTA per SM (the shared memory holds one
@@ -109,14 +127,15 @@ __global__ void __launch_bounds__(2 * kMixMaxThreads, 1) k_jacobi_mixed(const Ch
     extern __shared__ float4 smem_f4[];
     unsigned char *sb = reinterpret_cast<unsigned char *>(smem_f4);
     float *A = reinterpret_cast<float *>(sb);
-    // the slot table holds p | q << 16 (one 4-byte word a slot: a warp reading 32 slots is one
-    // shared-memory wavefront); the packed bases p(p+1)/2 are recomputed where needed
-    float2 *cs = reinterpret_cast<float2 *>(A + mix_a_floats(n));
-    unsigned *slp = reinterpret_cast<unsigned *>(cs + h);
-    float *dpp = reinterpret_cast<float *>(slp + h), *dqq = dpp + h;
+    // one 16-byte record a slot (one shared-memory load): the rotation of the pair (a, b) in
+    // tournament order, J = [[c, s'], [-s', c]] on (a, b), s' = s when a < b and -s otherwise
+    // (the rotation of the sorted pair (p, q) seen with its indices swapped), then a | b << 16
+    // and the column starts mcol(a) | mcol(b) << 16 (A has fewer than 2^16 floats)
+    uint4 *rec = reinterpret_cast<uint4 *>(A + mix_a_floats(n));
+    float *daa = reinterpret_cast<float *>(rec + h), *dbb = daa + h;
     // flags: [0] rotation in this sweep; [1..3] rotation in this round and [4..6] the
     // round's count of rotating slots, both cycled over three rounds
-    int *flags = reinterpret_cast<int *>(dqq + h);
+    int *flags = reinterpret_cast<int *>(dbb + h);
     int *rank = flags + 8;                                            // [h]: index in act, or -1
     unsigned short *act = reinterpret_cast<unsigned short *>(rank + h);  // [h]: the rotating slots
     unsigned short *quad = act + ((h + 1) & ~1);
@@ -133,14 +152,14 @@ __global__ void __launch_bounds__(2 * kMixMaxThreads, 1) k_jacobi_mixed(const Ch
         double v = ch.V[e];
         for (int a = 1; a < n_terms; ++a) v = fma(cf[a - 1], ch.V[(size_t)a * n * n + e], v);
         if (i == j) v += ch.d0 ? ch.d0[i] : ch.h0[i % N];  // d0: the diagonal of a rotated basis
-        A[pk(i, j)] = (float)v;
+        A[mcol(j) + i] = (float)v;
         if (Hg) {
             Hg[e] = v;
             Hg[(size_t)j * n + i] = v;
         }
     }
     if (npad > n)  // odd n: the phantom index n pairs with a zero row and column, so its rotation is the identity
-        for (int i = tid; i <= n; i += nt) A[pk(i, n)] = 0.0f;
+        for (int i = tid; i <= n; i += nt) A[mcol(n) + i] = 0.0f;
     for (int e = tid; e < n * ldc; e += nt) {
         const int col = e / ldc, row = e - col * ldc;
         C[e] = (row == col) ? 1.0f : 0.0f;  // rows n .. ldc-1 stay zero
@@ -153,19 +172,19 @@ __global__ void __launch_bounds__(2 * kMixMaxThreads, 1) k_jacobi_mixed(const Ch
     __syncthreads();
     const int nwarps = nt >> 5, warp = tid >> 5;
 
-    // 2 x 2 block of A in rows of slot P and columns of slot P2 (P < P2): J_P^T B J_P2
-    auto quad_update = [&](int P, int P2) {
-        const float2 r1 = cs[P], r2 = cs[P2];
-        const unsigned u = slp[P], v = slp[P2];
-        const int up = (int)(u & 0xFFFFu), uq = (int)(u >> 16), vp = (int)(v & 0xFFFFu), vq = (int)(v >> 16);
-        const int ubp = up * (up + 1) >> 1, ubq = uq * (uq + 1) >> 1, vbp = vp * (vp + 1) >> 1, vbq = vq * (vq + 1) >> 1;
-        // packed index of (x, y): base(max) + min
-        const int i00 = up <= vp ? vbp + up : ubp + vp;
-        const int i01 = up <= vq ? vbq + up : ubp + vq;
-        const int i10 = uq <= vp ? vbp + uq : ubq + vp;
-        const int i11 = uq <= vq ? vbq + uq : ubq + vq;
+    // 2 x 2 block B of A in rows (a, b) of the slot of record r1 and columns (a, b) of the slot
+    // of record r2: J_1^T B J_2
+    auto quad_update = [&](const uint4 r1, const uint4 r2) {
+        const int ua = (int)(r1.z & 0xFFFFu), ub = (int)(r1.z >> 16), va = (int)(r2.z & 0xFFFFu), vb = (int)(r2.z >> 16);
+        const int sua = (int)(r1.w & 0xFFFFu), sub = (int)(r1.w >> 16), sva = (int)(r2.w & 0xFFFFu), svb = (int)(r2.w >> 16);
+        // element (x, y) at mcol(max) + min
+        const int i00 = ua <= va ? sva + ua : sua + va;
+        const int i01 = ua <= vb ? svb + ua : sua + vb;
+        const int i10 = ub <= va ? sva + ub : sub + va;
+        const int i11 = ub <= vb ? svb + ub : sub + vb;
         const float b00 = A[i00], b01 = A[i01], b10 = A[i10], b11 = A[i11];
-        const float c = r1.x, s = r1.y, c2 = r2.x, s2 = r2.y;
+        const float c = __uint_as_float(r1.x), s = __uint_as_float(r1.y);
+        const float c2 = __uint_as_float(r2.x), s2 = __uint_as_float(r2.y);
         const float x00 = c2 * b00 - s2 * b01, x01 = s2 * b00 + c2 * b01;
         const float x10 = c2 * b10 - s2 * b11, x11 = s2 * b10 + c2 * b11;
         A[i00] = c * x00 - s * x10;
@@ -183,16 +202,16 @@ __global__ void __launch_bounds__(2 * kMixMaxThreads, 1) k_jacobi_mixed(const Ch
         if (n >= kMixThreshN && sweeps < kMixThreshSweeps) {
             float o2 = 0.0f;  // columns j and n - 1 - j per thread: balanced lengths
             for (int j = tid; j < (n + 1) / 2; j += nt) {
-                const int jb = j * (j + 1) / 2, j2 = n - 1 - j, j2b = j2 * (j2 + 1) / 2;
+                const int jb = mcol(j), j2 = n - 1 - j, j2b = mcol(j2);
                 for (int i = 0; i < j; ++i) o2 = fmaf(A[jb + i], A[jb + i], o2);
                 if (j2 != j)
                     for (int i = 0; i < j2; ++i) o2 = fmaf(A[j2b + i], A[j2b + i], o2);
             }
             for (int o = 16; o > 0; o >>= 1) o2 += __shfl_xor_sync(0xffffffffu, o2, o);
-            if (lane == 0) dpp[tid >> 5] = o2;  // dpp is free until this sweep's first round
+            if (lane == 0) daa[tid >> 5] = o2;  // daa is free until this sweep's first round
             __syncthreads();
             float tot = 0.0f;
-            for (int w = 0; w < (nt >> 5); ++w) tot += dpp[w];
+            for (int w = 0; w < (nt >> 5); ++w) tot += daa[w];
             thr = kMixThreshFrac * sqrtf(tot) / (float)n;
             __syncthreads();
         }
@@ -204,9 +223,11 @@ __global__ void __launch_bounds__(2 * kMixMaxThreads, 1) k_jacobi_mixed(const Ch
                 flags[4 + nx3] = 0;
             }
             for (int k = tid; k < h; k += nt) {
-                int p, q;
-                mix_pair(r, k, M, p, q);
-                const int pb = p * (p + 1) / 2, qb = q * (q + 1) / 2;
+                int a, b;
+                mix_pair(r, k, M, a, b);
+                const bool ab = a < b;
+                const int p = ab ? a : b, q = ab ? b : a;
+                const int ca = mcol(a), cb = mcol(b), pb = ab ? ca : cb, qb = ab ? cb : ca;
                 float c = 1.0f, s = 0.0f, app = A[pb + p], aqq = A[qb + q];
                 const float apq = A[qb + p];
                 if (fabsf(apq) > kRelTol * sqrtf(fabsf(app) * fabsf(aqq)) && fabsf(apq) > thr) {
@@ -226,10 +247,10 @@ __global__ void __launch_bounds__(2 * kMixMaxThreads, 1) k_jacobi_mixed(const Ch
                 } else {
                     rank[k] = -1;
                 }
-                slp[k] = (unsigned)p | ((unsigned)q << 16);
-                cs[k] = make_float2(c, s);
-                dpp[k] = app;
-                dqq[k] = aqq;
+                rec[k] = make_uint4(__float_as_uint(c), __float_as_uint(ab ? s : -s), (unsigned)a | ((unsigned)b << 16),
+                                    (unsigned)ca | ((unsigned)cb << 16));
+                daa[k] = ab ? app : aqq;
+                dbb[k] = ab ? aqq : app;
             }
             __syncthreads();
             const int na = flags[4 + g3];  // rotating slots this round (the same value for every thread)
@@ -238,42 +259,46 @@ __global__ void __launch_bounds__(2 * kMixMaxThreads, 1) k_jacobi_mixed(const Ch
                     // most slots rotate: every slot pair from the table
                     for (int e = tid; e < nq; e += nt) {
                         const unsigned pr = quad[e];
-                        const int P = pr >> 8, P2 = pr & 0xFF;
-                        if (cs[P].y == 0.0f && cs[P2].y == 0.0f) continue;  // both rotations are the identity
-                        quad_update(P, P2);
+                        const uint4 r1 = rec[pr >> 8], r2 = rec[pr & 0xFF];
+                        // both rotations the identity (s' = +-0)
+                        if (__uint_as_float(r1.y) == 0.0f && __uint_as_float(r2.y) == 0.0f) continue;
+                        quad_update(r1, r2);
                     }
                 } else {
                     // few slots rotate (late sweeps, threshold sweeps): only the pairs that
-                    // hold a rotating slot, one warp per rotating slot, lanes over the
-                    // others; a pair of two rotating slots is done once, by the lower
-                    // one's warp.  Each pair keeps its orientation (lower slot's rows),
-                    // so the result does not depend on the order of the rotating list.
+                    // hold a rotating slot, one warp per rotating slot P, lanes over the
+                    // others, rows from P's pair; a pair of two rotating slots is done
+                    // once, by the lower one's warp.  A pair with a non-rotating slot
+                    // gives the same bits in either orientation (the identity's c = 1,
+                    // s' = +-0 leave its side exact), so the result does not depend on
+                    // the order of the rotating list.
                     for (int i = warp; i < na; i += nwarps) {
                         const int P = act[i];
+                        const uint4 r1 = rec[P];
                         for (int P2 = lane; P2 < h; P2 += 32) {
                             if (P2 == P || (P2 < P && rank[P2] >= 0)) continue;
-                            if (P < P2) quad_update(P, P2);
-                            else quad_update(P2, P);
+                            quad_update(r1, rec[P2]);
                         }
                     }
                 }
                 for (int i = tid; i < na; i += nt) {
                     const int k = act[i];
-                    const int p = (int)(slp[k] & 0xFFFFu), q = (int)(slp[k] >> 16);
-                    const int pb = p * (p + 1) / 2, qb = q * (q + 1) / 2;
-                    A[pb + p] = dpp[k];
-                    A[qb + q] = dqq[k];
-                    A[qb + p] = 0.0f;
+                    const uint4 rk = rec[k];
+                    const int a = (int)(rk.z & 0xFFFFu), b = (int)(rk.z >> 16);
+                    const int ca = (int)(rk.w & 0xFFFFu), cb = (int)(rk.w >> 16);
+                    A[ca + a] = daa[k];
+                    A[cb + b] = dbb[k];
+                    A[a < b ? cb + a : ca + b] = 0.0f;
                 }
                 // C is column-major (column s contiguous, stride ldc): one warp per
                 // rotation, each lane four consecutive rows of the two columns
                 const int nv = ldc >> 2;
                 for (int i = warp; i < na; i += nwarps) {
-                    const int k = act[i];
-                    const float2 r1 = cs[k];
-                    float4 *Cp = reinterpret_cast<float4 *>(C + (size_t)(slp[k] & 0xFFFFu) * ldc);
-                    float4 *Cq = reinterpret_cast<float4 *>(C + (size_t)(slp[k] >> 16) * ldc);
-                    const float c = r1.x, s = r1.y;
+                    // columns a and b of C: C_a <- c C_a - s' C_b, C_b <- s' C_a + c C_b
+                    const uint4 rk = rec[act[i]];
+                    float4 *Cp = reinterpret_cast<float4 *>(C + (size_t)(rk.z & 0xFFFFu) * ldc);
+                    float4 *Cq = reinterpret_cast<float4 *>(C + (size_t)(rk.z >> 16) * ldc);
+                    const float c = __uint_as_float(rk.x), s = __uint_as_float(rk.y);
                     if (!C_SMEM && nv <= 96) {
                         // columns in global memory (L2): every load of the two columns is
                         // issued before the first store, one L2 round trip per rotation
@@ -321,7 +346,7 @@ __global__ void __launch_bounds__(2 * kMixMaxThreads, 1) k_jacobi_mixed(const Ch
         const int col = e / n, row = e - col * n;
         X[(size_t)row * n + col] = (double)C[(size_t)col * ldc + row];
     }
-    for (int i = tid; i < n; i += nt) lam_s[(size_t)blockIdx.x * n + i] = (double)A[pk(i, i)];
+    for (int i = tid; i < n; i += nt) lam_s[(size_t)blockIdx.x * n + i] = (double)A[mcol(i) + i];
     if (tid == 0) {
         status_all[(size_t)smp * n_ch_total + cidx] = converged ? sweeps : -1;
         if (!converged) record_error(err, kDevNoConverge);
