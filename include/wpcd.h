@@ -227,7 +227,7 @@ wpcd_status wpcd_vset_get(wpcd_ctx *ctx, int vset_id, int channel, double *out_h
  * stay on the device under the returned eig handle.  prec: WPCD_PREC_FP64 or
  * WPCD_PREC_MIXED (see wpcd_precision).  Every size uses the parallel cyclic
  * Jacobi method (App. C): matrices that fit one CTA's shared memory (FP64 up to
- * n ~ 230, FP32 up to n ~ 310) are held there; larger ones, up to n = 1024, are
+ * n ~ 230, FP32 up to n = 304) are held there; larger ones, up to n = 1024, are
  * held in global memory (L2-resident while a CTA works on them).
  * Per-solve convergence status: wpcd_diag_status.
  * Errors: WPCD_ERR_ARG, WPCD_ERR_HANDLE, WPCD_ERR_NOMEM, WPCD_ERR_BUDGET, WPCD_ERR_CUDA. */

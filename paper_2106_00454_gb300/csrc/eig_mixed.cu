@@ -16,7 +16,12 @@ namespace wpcd {
 
 constexpr int kMixMaxThreads = 512;  // launch bound; the launch picks 64..512
 constexpr int kMixMaxSweeps = 40;
-constexpr size_t kMixSmemCap = 200 * 1024;
+// The eigenvectors C stay in shared memory while A, the tables and C fit in this
+// many bytes (n <= 149), else they live in global memory (L2): from n = 150 on,
+// the smaller CTAs without C run more solves per SM than their L2 round trips
+// cost (measured at n = 150: 11.3 us per solve with C in shared memory and one
+// 1024-thread CTA per SM, 8.2 us with C in L2 and 256-thread CTAs).
+constexpr size_t kMixSmemCap = 150 * 1024;
 constexpr float kRelTol = 1.1920929e-7f;  // 2^-23
 // Threshold Jacobi (Rutishauser) on large matrices: in the first sweeps a pair
 // rotates only if |a_pq| also exceeds kMixThreshFrac * off(A) / n, off(A) the
