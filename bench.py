@@ -51,11 +51,18 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP32_PEAK_NOTE = ("builder-derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz; "
                   "our FFMA probe measured 69-70 TFLOP/s")
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
-# k_jacobi_mixed DRAM bytes (read + write) per solve per matrix element, from the ncu
-# capture of 152 solves of 3S1-3D1 at N_WP = 150 (profiles/k_jacobi_mixed_3s1d1_nwp150_152samples.md:
-# 17.8 MB + 274.1 MB over 152 x 300^2 elements); the traffic is the FP64 H and eigenvectors
-# handed to the refinement, so it scales with n^2
-JACOBI_MIXED_DRAM_BYTES_PER_N2 = (17.841408e6 + 274.119168e6) / (152 * 300 * 300)
+# k_jacobi_mixed DRAM bytes (read + write) per solve per matrix element inside the headline
+# step, from the ncu capture of the workload's first 128 samples (profiles/
+# traffic_mixed_20ch_nwp150_128samples.md: 1.460 GB + 2.602 GB per solve pass over
+# 128 x (6 x 300^2 + 14 x 150^2) elements, L2 flushed between passes as in the timed steps):
+# the FP64 H and eigenvectors handed to the refinement (16 B an element), the potential
+# terms re-read after the flush and eigenvector columns evicted from the L2; it scales
+# with the samples and with n^2
+JACOBI_MIXED_DRAM_BYTES_PER_N2 = (1459650764.8 + 2601650176.0) / (128 * (6 * 300 * 300 + 14 * 150 * 150))
+# the refinement phase's kernels (digit splits, tcgen05 digit products, update, sort), same
+# capture: 39.52 GB + 22.56 GB per solve pass, against the algorithmic 24 B an element (H and
+# X read, X written, FP64)
+REFINE_DRAM_BYTES_PER_N2 = (39518831616.0 + 22560583270.4) / (128 * (6 * 300 * 300 + 14 * 150 * 150))
 SAT_P99_BOUND_MS = 250.0     # the saturation sweep's latency bound
 SERVE_MAX_QUEUE = 4096       # requests waiting at most (the server refuses beyond)
 
@@ -712,7 +719,7 @@ def run_wpcd(args, ws, rank, lrank):
             jac["executed"] = {"flops_per_step": ex, "achieved": ach, "frac": ach / jac["peak"],
                                "sweeps_mean": float(sw.mean()), "sweeps_max": int(sw.max()),
                                "note": f"upper bound: sweeps x 4 n^3 per solve, sweeps of the first {ks} samples"}
-        ref = None
+        ref, ref_traffic = None, None
         if ref_n:
             if ctx.refine_engine == api.REFINE_TENSOR:
                 # Ozaki products: 6 balanced 8-bit digits per operand, the 21 digit pairs of
@@ -731,18 +738,28 @@ def run_wpcd(args, ws, rank, lrank):
                        "peak": FP64_PEAK_TFLOPS, "peak_source": FP64_PEAK_NOTE}
             ref.update({"ms_per_step": ref_ms / kp, "launches_per_step": ref_n / kp,
                         "timing": "CUDA events around the whole phase (several kernels per launch)"})
+            if ctx.refine_engine == api.REFINE_TENSOR and args.workload == "config4" and all(v <= 304 for v in big):
+                ref_traffic = REFINE_DRAM_BYTES_PER_N2 * S * sum(v * v for v in big) / ref["launches_per_step"]
         for r in (jac, ref):
             if r:
                 r["achieved"] = r["flops_per_step"] / (r["ms_per_step"] * 1e-3) / 1e12
                 r["unit"] = "TFLOP/s"
                 r["frac"] = r["achieved"] / r["peak"]
                 r["traffic"] = None
-        if prec == api.PREC_MIXED and jac["launches_per_step"] > 0 and all(v <= 304 for v in big):
+        if ref_traffic is not None and prec == api.PREC_MIXED:
+            ref["traffic"] = ref_traffic
+            ref["traffic_note"] = ("ncu capture of the workload's first 128 samples (567 B of DRAM traffic per "
+                                   "matrix element per solve against the algorithmic 24 B: the BF16 digit slices of "
+                                   "every operand and the FP64 intermediates go through HBM), scaled by the step's "
+                                   "sum of n^2; bytes per phase launch")
+        if prec == api.PREC_MIXED and args.workload == "config4" and jac["launches_per_step"] > 0 \
+                and all(v <= 304 for v in big):
             # DRAM bytes per launch: the capture's bytes per matrix element times the step's
             # sum of n^2 over its solves, over the step's Jacobi launches
             jac["traffic"] = JACOBI_MIXED_DRAM_BYTES_PER_N2 * S * sum(v * v for v in big) / jac["launches_per_step"]
-            jac["traffic_note"] = ("ncu capture of 152 solves at n = 300 (21.3 B of DRAM traffic per matrix element "
-                                   "per solve), scaled by the step's sum of n^2; bytes per launch")
+            jac["traffic_note"] = ("ncu capture of the workload's first 128 samples (37.1 B of DRAM traffic per "
+                                   "matrix element per solve against the algorithmic 16 B), scaled by the step's "
+                                   "sum of n^2; bytes per launch")
 
         clocks = clk.summary()
         line = {
