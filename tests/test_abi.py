@@ -78,3 +78,15 @@ def test_null_context_is_rejected_without_device(lib):
             assert got == -1, (name, got)
         checked += 1
     assert checked >= 25
+
+
+def test_binding_refuses_to_run_without_the_library(monkeypatch, tmp_path):
+    """No fallback: with the compiled library absent the binding raises instead
+    of computing anything another way (the product path has no CPU route)."""
+    from paper_2106_00454_gb300 import _lib, api
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libwpcd.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        _lib.load()
+    with pytest.raises(RuntimeError, match="missing"):
+        api.Context(0)
